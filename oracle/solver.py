@@ -1,0 +1,226 @@
+"""Oracle, global level: assembly, Dirichlet elimination, Newton, load steps, objective,
+discrete adjoint, direct sensitivity and central finite differences.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+* Assembly K = A_e K^e, R = A_e R^e (Sec. 2.2.4); COO -> CSR summation is the library
+  step (scipy.sparse), standing in for the triplet assembly of App. E.
+* Dirichlet data: u[dof] = t * value is imposed on u before the first Newton iteration of a
+  step and the linear solves run on the free block of K (reading R12: the same converged u as
+  identity-row elimination, with a symmetric matrix).
+* Newton (Eq. Stiffness_mat): K(d^k) dd = -R(d^k) until ||R_free|| <= rtol * max(||R_free^0||, 1)
+  (reading R11); the linear solve is scipy's sparse direct solver.
+* Objective J = w sum_n ||u^n - u_gt^n||^2 over all dofs and steps (Sec. 2.3, reading R16).
+* Adjoint (Eq. dR_u, Eq. main_grad, Algorithm adjoint_ad) with the history written out:
+  states (u^n, h^n), R^n(u^n, h^{n-1}, theta) = 0, h^n = H(u^n, h^{n-1}, theta).  With
+  mu^N = 0, for n = N..1:  ubar = dJ^n/du^n + (dH/du^n)^T mu^n;  K^T lambda = -ubar (free
+  dofs);  mu^{n-1} = (dR^n/dh^{n-1})^T lambda + (dH/dh^{n-1})^T mu^n;
+  g += (dR^n/dtheta)^T lambda + (dH/dtheta)^T mu^n.
+* Direct sensitivity (forward mode of the same chain) and central FD (Algorithm
+  finite_difference) are the independent checks of the adjoint.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import element
+
+
+@dataclasses.dataclass
+class Problem:
+    X: np.ndarray
+    conn: np.ndarray
+    fixed_dof: np.ndarray
+    fixed_val: np.ndarray
+    theta: np.ndarray            # (11,) uniform or (n_el, 11) per element
+    hardening: str
+    Theta: np.ndarray | None = None
+    f_ext: np.ndarray | None = None   # nodal dead load at t = 1 (n_dof,), optional
+
+    @property
+    def n_dof(self):
+        return 3 * self.X.shape[0]
+
+    @property
+    def n_el(self):
+        return self.conn.shape[0]
+
+
+def from_inputs(mesh, bc, mat, theta=None):
+    th = mat.theta_vector() if theta is None else np.asarray(theta, dtype=np.float64)
+    return Problem(X=mesh.X, conn=mesh.conn.astype(np.int64), fixed_dof=bc.dof,
+                   fixed_val=bc.value, theta=th, hardening=mat.hardening,
+                   Theta=None if np.allclose(mat.Theta, np.eye(3)) else mat.Theta)
+
+
+def element_dofs(conn):
+    return (3 * conn[:, :, None] + np.arange(3)[None, None, :]).reshape(conn.shape[0], 24)
+
+
+def assemble_R(prob, Re):
+    R = np.zeros(prob.n_dof)
+    np.add.at(R, element_dofs(prob.conn), Re)
+    return R
+
+
+def assemble_K(prob, Ke):
+    ed = element_dofs(prob.conn)
+    rows = np.repeat(ed, 24, axis=1).ravel()
+    cols = np.tile(ed, (1, 24)).ravel()
+    return sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(prob.n_dof, prob.n_dof)).tocsr()
+
+
+def free_mask(prob):
+    m = np.ones(prob.n_dof, dtype=bool)
+    m[prob.fixed_dof] = False
+    return m
+
+
+def residual(prob, u, hist, t=1.0, jacobians="tangent"):
+    """R(u) = f_int(u; h_n) - t f_ext and, with jacobians, K = dR/du."""
+    es = element.element_sweep(prob.X, prob.conn, u, hist, prob.theta, prob.hardening,
+                               prob.Theta, jacobians=jacobians)
+    R = assemble_R(prob, es["Re"])
+    if prob.f_ext is not None:
+        R = R - t * prob.f_ext
+    K = assemble_K(prob, es["Ke"]) if jacobians is not None else None
+    return R, K, es
+
+
+def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0):
+    """Equilibrium at load factor t from the predictor u0 (Dirichlet values set here)."""
+    u = u0.copy()
+    u[prob.fixed_dof] = t * prob.fixed_val
+    free = free_mask(prob)
+    history = []
+    ref = None
+    for it in range(maxit + 1):
+        R, K, es = residual(prob, u, hist, t)
+        rn = float(np.linalg.norm(R[free]))
+        history.append(rn)
+        if ref is None:
+            ref = max(rn, atol_floor)
+        if rn <= rtol * ref:
+            return u, es, dict(iters=it, res=history, converged=True)
+        if it == maxit:
+            break
+        Kff = K[free][:, free]
+        du = spla.spsolve(Kff.tocsc(), -R[free])
+        u[free] += du
+    return u, es, dict(iters=maxit, res=history, converged=False)
+
+
+def forward(prob, t_steps, rtol=1e-10, maxit=30, hist0=None):
+    """Load-step loop; returns u^n (N, n_dof), h^n (N+1, n_el, 8, 7), per-step info."""
+    hist = np.zeros((prob.n_el, 8, 7)) if hist0 is None else hist0.copy()
+    u = np.zeros(prob.n_dof)
+    us, hs, infos = [], [hist.copy()], []
+    for t in t_steps:
+        u, es, info = newton_step(prob, u, hist, t, rtol=rtol, maxit=maxit)
+        hist = es["h_new"].copy()                  # commit h_n = H(u_n, h_{n-1}, theta)
+        us.append(u.copy())
+        hs.append(hist.copy())
+        info["plastic"] = int(es["gp"]["plastic"].sum())
+        info["sigma"] = es["gp"]["sigma"].reshape(prob.n_el, 8, 3, 3)
+        infos.append(info)
+    return np.array(us), np.array(hs), infos
+
+
+def objective(us, u_gt, w=1.0):
+    return float(w * np.sum((us - u_gt) ** 2))
+
+
+def _gp_cotangent_from_dofs(prob, es, lam):
+    """P-bar per Gauss point: w detJ0 sum_a lambda_a (x) g_a (shape (n_el, 8, 3, 3))."""
+    le = lam.reshape(-1, 3)[prob.conn]                 # (n_el, 8, 3)
+    return np.einsum("eg,eai,egaJ->egiJ", es["wdet"], le, es["g"])
+
+
+def _dofs_from_F_cotangent(prob, es, Fbar):
+    """u-bar = sum_gp sum_l Fbar_kl g_al, scattered to the dofs."""
+    ue = np.einsum("egkl,egal->eak", Fbar, es["g"]).reshape(prob.n_el, 24)
+    return assemble_R(prob, ue)
+
+
+def adjoint(prob, t_steps, us, hs, u_gt, w=1.0, per_element=False):
+    """dJ/dtheta by the discrete adjoint; (11,) for uniform theta, (n_el, 11) if per_element."""
+    free = free_mask(prob)
+    n_el = prob.n_el
+    N = len(t_steps)
+    mu = np.zeros((n_el, 8, 7))
+    gth = np.zeros((n_el, 11))
+    for n in range(N - 1, -1, -1):
+        R, K, es = residual(prob, us[n], hs[n], t_steps[n], jacobians="all")
+        gp = es["gp"]
+        mu_f = mu.reshape(-1, 7)
+        Fbar = np.einsum("bj,bjkl->bkl", mu_f, gp["dh_dF"]).reshape(n_el, 8, 3, 3)
+        ubar = 2.0 * w * (us[n] - u_gt[n]) + _dofs_from_F_cotangent(prob, es, Fbar)
+        lam = np.zeros(prob.n_dof)
+        Kff = K[free][:, free]
+        lam[free] = spla.spsolve(Kff.T.tocsc(), -ubar[free])
+        Pbar = _gp_cotangent_from_dofs(prob, es, lam).reshape(-1, 3, 3)
+        hbar = np.einsum("biJ,biJj->bj", Pbar, gp["dP_dh"]) + \
+            np.einsum("bj,bjk->bk", mu_f, gp["dh_dh"])
+        tbar = np.einsum("biJ,biJj->bj", Pbar, gp["dP_dtheta"]) + \
+            np.einsum("bj,bjk->bk", mu_f, gp["dh_dtheta"])
+        gth += tbar.reshape(n_el, 8, 11).sum(axis=1)
+        mu = hbar.reshape(n_el, 8, 7)
+    return gth if per_element else gth.sum(axis=0)
+
+
+def direct_sensitivity(prob, t_steps, us, hs, u_gt, dtheta, w=1.0):
+    """dJ/dtheta . dtheta by forward (tangent) propagation; dtheta (11,) or (n_el, 11)."""
+    free = free_mask(prob)
+    n_el = prob.n_el
+    dth = np.broadcast_to(np.asarray(dtheta, dtype=np.float64), (n_el, 11))
+    dth_gp = np.repeat(dth[:, None, :], 8, axis=1).reshape(-1, 11)
+    hdot = np.zeros((n_el * 8, 7))
+    dJ = 0.0
+    for n in range(len(t_steps)):
+        R, K, es = residual(prob, us[n], hs[n], t_steps[n], jacobians="all")
+        gp = es["gp"]
+        Pdot = np.einsum("biJj,bj->biJ", gp["dP_dtheta"], dth_gp) + \
+            np.einsum("biJj,bj->biJ", gp["dP_dh"], hdot)
+        Re_dot = np.einsum("eg,egiJ,egaJ->eai", es["wdet"], Pdot.reshape(n_el, 8, 3, 3),
+                           es["g"]).reshape(n_el, 24)
+        rhs = assemble_R(prob, Re_dot)
+        udot = np.zeros(prob.n_dof)
+        udot[free] = spla.spsolve(K[free][:, free].tocsc(), -rhs[free])
+        Fdot = np.einsum("eai,egaj->egij", udot.reshape(-1, 3)[prob.conn], es["g"]).reshape(-1, 3, 3)
+        hdot = np.einsum("bjkl,bkl->bj", gp["dh_dF"], Fdot) + \
+            np.einsum("bjk,bk->bj", gp["dh_dh"], hdot) + \
+            np.einsum("bjk,bk->bj", gp["dh_dtheta"], dth_gp)
+        dJ += float(2.0 * w * np.dot(us[n] - u_gt[n], udot))
+    return dJ
+
+
+def fd_gradient(prob, t_steps, u_gt, h_rel=1e-6, w=1.0, index=None, rtol=1e-13):
+    """Central differences (Algorithm finite_difference) with step h_rel * |theta_i|."""
+    th0 = np.asarray(prob.theta, dtype=np.float64)
+    idx = range(th0.shape[-1]) if index is None else index
+    g = {}
+    for i in idx:
+        h = h_rel * abs(th0[..., i]).max()
+        vals = []
+        for s in (+1, -1):
+            th = th0.copy()
+            th[..., i] += s * h
+            p = dataclasses.replace(prob, theta=th)
+            us, _, _ = forward(p, t_steps, rtol=rtol)
+            vals.append(objective(us, u_gt, w))
+        g[i] = (vals[0] - vals[1]) / (2 * h)
+    return g
+
+
+def fd_directional(prob, t_steps, u_gt, direction, h=1e-6, w=1.0, rtol=1e-13):
+    """Central difference of J along a parameter direction (same shape as theta)."""
+    vals = []
+    for s in (+1, -1):
+        p = dataclasses.replace(prob, theta=np.asarray(prob.theta) + s * h * np.asarray(direction))
+        us, _, _ = forward(p, t_steps, rtol=rtol)
+        vals.append(objective(us, u_gt, w))
+    return (vals[0] - vals[1]) / (2 * h)
