@@ -1,0 +1,209 @@
+/*
+ * hfe.h — C ABI of the B300 hex8 finite-strain Hill-48 plasticity library.
+ *
+ * The library computes, on one GPU, the per-Newton-iteration sweep over all hex8 Gauss
+ * points of a displacement-based finite element model in the additive logarithmic-strain
+ * formulation (paper Sec. 2.2.2: geometric pre-processor Eq. c_decomp, log-space elasticity
+ * Eq. T, Hill-48 effective stress Eq. Phi_hill with App. A.1, hardening Eq. Hard,
+ * associative flow Eq. ep_evol and the Kuhn-Tucker conditions Eq. KT, return mapping
+ * Eq. Tr_stress/Eq. local_cpp, geometric post-processor Eq. proj_lagrange/Eq. pk_stress),
+ * the element residual and consistent tangent (Sec. 2.2.4, Eq. Stiffness_mat), their
+ * assembly into a block-CSR matrix, the linear solve, the global Newton loop over load
+ * steps, and the discrete adjoint (Sec. 2.3, Eq. dR_u, Eq. main_grad, Algorithm
+ * adjoint_ad).
+ *
+ * Units are whatever the caller uses consistently (the tests use mm, N, MPa).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - hex8 node order C3D8: bottom face 0-1-2-3 counter-clockwise seen from +z, top 4-7;
+ *  - Gauss points: 2x2x2 at +-1/sqrt(3), unit weights, gp = i + 2j + 4k (xi fastest);
+ *    the global Gauss-point index is 8*element + gp;
+ *  - degrees of freedom are node-major: dof = 3*node + component;
+ *  - symmetric tensors are 6 tensor components in the order (11, 22, 33, 12, 23, 13);
+ *  - history is structure-of-arrays [7][n_gp]: eps_p (6 components), alpha;
+ *  - theta (material parameters) is [n_mat][11]: E, nu, F, G, H, L, M, N, h1, h2, h3
+ *    with (h1, h2, h3) = (K, eps0, n) for Swift sigma_y = K (eps0 + alpha)^n and
+ *    (sigma0, Q, b) for Voce sigma_y = sigma0 + Q (1 - exp(-b alpha)); the yield function
+ *    is f = sqrt(T:H:T) - sqrt(2/3) sigma_y(alpha) with alpha-rate sqrt(2/3) gamma-rate;
+ *  - Dirichlet data (dof[i], value[i]) prescribe u[dof] = t * value at load factor t;
+ *  - pointer arguments marked "host or device" may point to either; the library detects
+ *    which with cudaPointerGetAttributes and copies on its stream.  All other pointers
+ *    are host pointers.
+ *
+ * Ownership: the caller owns every buffer it passes.  hfe_create copies what it needs;
+ * the handle owns its device workspaces and frees them in hfe_destroy.
+ *
+ * Errors: every function returns an hfe_status; none aborts, exits or traps.  Device
+ * loops are bounded (local Newton, Krylov iterations) and report through a device status
+ * word that the host reads after each sweep and solve.  A non-zero status leaves the
+ * handle usable; hfe_last_error() gives a one-line description.
+ */
+#ifndef HFE_H
+#define HFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HFE_OK = 0,
+  HFE_EINVAL = -1,      /* invalid argument (sizes, indices, NULL where required) */
+  HFE_ENOMEM = -2,      /* device allocation failed */
+  HFE_ECUDA = -3,       /* CUDA runtime error (message in hfe_last_error) */
+  HFE_EDETJ = -4,       /* an element has det(dX/dxi) <= 0 or det F <= 0 */
+  HFE_ENEWTON = 1,      /* global Newton did not converge within newton_maxit */
+  HFE_ELOCAL = 2,       /* a local return mapping did not converge (count in stats) */
+  HFE_EPCG = 3,         /* Krylov solve did not reach pcg_rtol within pcg_maxit */
+  HFE_ENONFINITE = 4    /* a non-finite value appeared in a residual, stress or solve */
+} hfe_status;
+
+typedef struct hfe_handle hfe_handle;
+
+/* Mesh: X[n_nodes*3] reference coordinates, conn[n_el*8] node ids in C3D8 order. */
+typedef struct {
+  int64_t n_nodes;
+  int64_t n_el;
+  const double* X;
+  const int32_t* conn;
+} hfe_mesh;
+
+/* Boundary data (Eq. equilibrium): n_fixed Dirichlet entries (sorted or not, no duplicates),
+ * and an optional nodal dead load f_ext[n_dof] at t = 1 (NULL for none), scaled by t. */
+typedef struct {
+  int64_t n_fixed;
+  const int64_t* dof;
+  const double* value;
+  const double* f_ext;
+} hfe_bc;
+
+#define HFE_HARDENING_SWIFT 0
+#define HFE_HARDENING_VOCE 1
+
+/* Material: n_mat = 1 (uniform) or n_el (per element); theta[n_mat*11] as above;
+ * Theta NULL (material axes = global axes) or [n_mat*9] row-major 3x3 whose columns are the
+ * material axes in global coordinates (App. A.1: H_g = Theta Theta : H_l : Theta^T Theta^T). */
+typedef struct {
+  int hardening;
+  int64_t n_mat;
+  const double* theta;
+  const double* Theta;
+} hfe_material;
+
+#define HFE_PRECISION_FP64 0
+#define HFE_PRECISION_MIXED 1
+#define HFE_PRECOND_JACOBI 0
+#define HFE_PRECOND_BLOCK3 1
+
+/* Options (hfe_default_options fills the defaults). */
+typedef struct {
+  int precision;          /* HFE_PRECISION_FP64 or HFE_PRECISION_MIXED */
+  double newton_rtol;     /* ||R_free|| <= newton_rtol * max(||R_free^0||, newton_atol) */
+  double newton_atol;
+  int newton_maxit;
+  double newton_stag_tol; /* mixed only: stagnation accepted below this relative norm */
+  double pcg_rtol;        /* ||r|| <= pcg_rtol * ||b|| */
+  int pcg_maxit;
+  int pcg_check_every;    /* iterations per convergence read-back (one CUDA graph) */
+  int precond;            /* HFE_PRECOND_JACOBI or HFE_PRECOND_BLOCK3 */
+  int local_maxit;        /* bound of the local return-mapping Newton */
+  double local_tol;       /* relative tolerance of the local yield residual */
+  int ckpt_every;         /* adjoint: store the history every k steps, recompute between */
+  int predictor;          /* 1 (default): each step starts from the tangent predictor
+                             u = u_{n-1} + du_D + dK^-1 (-(R + K du_D)) built on the converged
+                             start-of-step state, where K is positive definite; 0: from u_{n-1}
+                             with the new Dirichlet values only */
+} hfe_options;
+
+/* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */
+typedef struct {
+  int64_t newton_iters;   /* total over steps */
+  int64_t pcg_iters;      /* total over solves */
+  int64_t sweeps;         /* Gauss-point sweeps launched */
+  int64_t plastic_gps;    /* plastic Gauss points in the last sweep */
+  int64_t local_fail;     /* local return mappings that hit local_maxit (last sweep) */
+  int32_t max_local_iters;/* largest local Newton iteration count (last sweep) */
+  int32_t steps_done;     /* load steps completed */
+  double last_residual;   /* ||R_free|| at the last Newton check */
+  double sweep_ms;        /* device time in the sweep kernels */
+  double solve_ms;        /* device time in the Krylov solves */
+  double total_ms;        /* wall time of the call */
+} hfe_stats;
+
+/* Sizes of the internal data (for tests and benchmarks). */
+typedef struct {
+  int64_t n_nodes, n_el, n_dof, n_gp, n_blocks, n_fixed;
+  int32_t n_colors;
+  int32_t precision;
+  int64_t device_bytes;
+} hfe_info;
+
+/* Fill *opt with defaults for the given precision. */
+void hfe_default_options(hfe_options* opt, int precision);
+
+/* Build the handle: copies the mesh, boundary data and material to the device, builds the
+ * block-CSR pattern of K (3x3 blocks, one block per node pair sharing an element), the
+ * element-to-block slot map, and a conflict-free element colouring (Sec. 2.2.5 "GPU-
+ * accelerated global sparse matrix assembly" describes the assembly it replaces).
+ * stream: a cudaStream_t the library orders its work after and before (NULL = legacy
+ * default stream).  Returns HFE_EINVAL for out-of-range node ids, HFE_EDETJ for an
+ * element with det(dX/dxi) <= 0 at a Gauss point. */
+hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat,
+                      const hfe_options* opt, void* stream, hfe_handle** out);
+void hfe_destroy(hfe_handle* h);
+const char* hfe_last_error(const hfe_handle* h);
+hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info);
+
+/* Replace the material parameters (same hardening law and n_mat); used by inverse loops. */
+hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat);
+
+/* State: displacement u[n_dof] and history [7][n_gp] at t_n (host or device).  hist may be
+ * NULL in set_state to mean zero history. */
+hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist);
+hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist);
+
+#define HFE_SWEEP_RESIDUAL 0   /* R and trial history only */
+#define HFE_SWEEP_TANGENT 1    /* R, trial history and K (into the internal BSR values) */
+
+/* One Gauss-point sweep at displacement u (host or device, [n_dof]) against the stored
+ * history h_n: R_out[n_dof] (host or device, may be NULL) receives the internal force
+ * minus t*f_ext with t = load (Dirichlet rows included, no elimination);
+ * hist_trial_out [7][n_gp] (host or device, may be NULL) the updated history; in tangent
+ * mode K is assembled into the handle (read it with hfe_get_bsr).  stats may be NULL. */
+hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, double* R_out,
+                        double* hist_trial_out, hfe_stats* stats);
+
+/* Export the block-CSR pattern (rowptr[n_nodes+1], cols[n_blocks]) and the values of the
+ * last assembled K as float64 [n_blocks*9] (row-major 3x3 blocks); any pointer may be NULL;
+ * host pointers. */
+hfe_status hfe_get_bsr(hfe_handle* h, int64_t* rowptr, int32_t* cols, double* vals);
+
+/* y = Kt x for the last assembled K with symmetric Dirichlet elimination (rows and columns
+ * of fixed dofs zeroed, unit diagonal); x, y [n_dof] host or device, float64. */
+hfe_status hfe_spmv(hfe_handle* h, const double* x, double* y);
+
+/* Solve Kt x = b (Dirichlet components of b ignored, x_fixed = 0) with Jacobi or 3x3
+ * block-Jacobi preconditioned CG; b, x [n_dof] host or device, float64. */
+hfe_status hfe_solve(hfe_handle* h, const double* b, double* x, hfe_stats* stats);
+
+/* Load-step loop with global Newton (Eq. Stiffness_mat) from the stored state.  t[n_steps]
+ * load factors.  u_out [n_steps*n_dof] (all steps), sigma_out [n_gp*6] Cauchy stress
+ * sigma = P F^T / J at the final step, hist_out [7][n_gp] at the final step; each host or
+ * device or NULL.  On success the stored state is the final one. */
+hfe_status hfe_forward(hfe_handle* h, int n_steps, const double* t, double* u_out,
+                       double* sigma_out, double* hist_out, hfe_stats* stats);
+
+/* Misfit J = w sum_n ||u^n - u_target^n||^2 of a forward run from zero state over t, and its
+ * gradient by the discrete adjoint (Eq. dR_u, Eq. main_grad) with the per-Gauss-point
+ * implicit-function derivative of the return mapping (App. D).  u_target [n_steps*n_dof]
+ * host or device; grad_out [n_mat*11] host or device (same layout as theta); J_out host.
+ * The forward runs in the handle's precision; the adjoint in FP64. */
+hfe_status hfe_adjoint(hfe_handle* h, int n_steps, const double* t, const double* u_target,
+                       double w, double* J_out, double* grad_out, hfe_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFE_H */

@@ -8,8 +8,11 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 * Dirichlet data: u[dof] = t * value is imposed on u before the first Newton iteration of a
   step and the linear solves run on the free block of K (reading R12: the same converged u as
   identity-row elimination, with a symmetric matrix).
-* Newton (Eq. Stiffness_mat): K(d^k) dd = -R(d^k) until ||R_free|| <= rtol * max(||R_free^0||, 1)
-  (reading R11); the linear solve is scipy's sparse direct solver.
+* Newton (Eq. Stiffness_mat): K(d^k) dd = -R(d^k) until ||R_free|| <= rtol * max(ref, 1)
+  (reading R11) with ref the norm of the predictor's right-hand side; the linear solve is
+  scipy's sparse direct solver.  Each step starts from the linearised Dirichlet increment on
+  the converged start-of-step state (reading R14; a step that starts from u_{n-1} with only
+  the new boundary values can land on an indefinite tangent and diverge on perforated plates).
 * Objective J = w sum_n ||u^n - u_gt^n||^2 over all dofs and steps (Sec. 2.3, reading R16).
 * Adjoint (Eq. dR_u, Eq. main_grad, Algorithm adjoint_ad) with the history written out:
   states (u^n, h^n), R^n(u^n, h^{n-1}, theta) = 0, h^n = H(u^n, h^{n-1}, theta).  With
@@ -91,13 +94,30 @@ def residual(prob, u, hist, t=1.0, jacobians="tangent"):
     return R, K, es
 
 
-def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0):
-    """Equilibrium at load factor t from the predictor u0 (Dirichlet values set here)."""
-    u = u0.copy()
-    u[prob.fixed_dof] = t * prob.fixed_val
+def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0, t_prev=None):
+    """Equilibrium at load factor t from the converged start-of-step state u0 (at t_prev).
+
+    Predictor (reading R14): the Dirichlet increment du_D is linearised at the start-of-step
+    state, u = u0 + du_D + K_ff^{-1} (-(R(u0) + K du_D - dt f_ext))_f, with K the tangent at
+    (u0, h_{n-1}).  The Newton iterations that follow are Eq. Stiffness_mat; the predictor
+    changes the iteration count only.  Without t_prev: u = u0 with the new Dirichlet values.
+    """
     free = free_mask(prob)
-    history = []
+    u = u0.copy()
     ref = None
+    if t_prev is not None:
+        R0, K0, _ = residual(prob, u, hist, t_prev)
+        duD = np.zeros(prob.n_dof)
+        duD[prob.fixed_dof] = (t - t_prev) * prob.fixed_val
+        b = -(R0 + K0 @ duD)
+        if prob.f_ext is not None:
+            b = b + (t - t_prev) * prob.f_ext
+        ref = max(float(np.linalg.norm(b[free])), atol_floor)
+        u = u + duD
+        if np.any(b[free] != 0.0):
+            u[free] += spla.spsolve(K0[free][:, free].tocsc(), b[free])
+    u[prob.fixed_dof] = t * prob.fixed_val
+    history = []
     for it in range(maxit + 1):
         R, K, es = residual(prob, u, hist, t)
         rn = float(np.linalg.norm(R[free]))
@@ -114,13 +134,23 @@ def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0):
     return u, es, dict(iters=maxit, res=history, converged=False)
 
 
-def forward(prob, t_steps, rtol=1e-10, maxit=30, hist0=None):
-    """Load-step loop; returns u^n (N, n_dof), h^n (N+1, n_el, 8, 7), per-step info."""
+class NewtonDivergence(RuntimeError):
+    pass
+
+
+def forward(prob, t_steps, rtol=1e-10, maxit=30, hist0=None, predictor=True):
+    """Load-step loop; returns u^n (N, n_dof), h^n (N+1, n_el, 8, 7), per-step info.
+    Raises NewtonDivergence if a step does not converge."""
     hist = np.zeros((prob.n_el, 8, 7)) if hist0 is None else hist0.copy()
     u = np.zeros(prob.n_dof)
     us, hs, infos = [], [hist.copy()], []
+    t_prev = 0.0
     for t in t_steps:
-        u, es, info = newton_step(prob, u, hist, t, rtol=rtol, maxit=maxit)
+        u, es, info = newton_step(prob, u, hist, t, rtol=rtol, maxit=maxit,
+                                  t_prev=t_prev if predictor else None)
+        if not info["converged"]:
+            raise NewtonDivergence(f"step t={t}: residual history {info['res'][-3:]}")
+        t_prev = t
         hist = es["h_new"].copy()                  # commit h_n = H(u_n, h_{n-1}, theta)
         us.append(u.copy())
         hs.append(hist.copy())

@@ -1,0 +1,659 @@
+// C ABI of the library (include/hfe.h): handle set-up, state transfer, the Gauss-point
+// sweep, the Krylov solve and the load-step Newton driver (paper Eq. Stiffness_mat and the
+// load-step loop of Algorithm adjoint_ad's forward pass).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+
+using namespace hfe;
+
+namespace hfe {
+
+hfe_status fail(hfe_handle* h, hfe_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+hfe_status cuda_check(hfe_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HFE_OK;
+  return fail(h, HFE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+hfe_status dalloc(hfe_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, HFE_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  h->allocs.push_back(q);
+  h->device_bytes += count * sizeof(T);
+  *p = reinterpret_cast<T*>(q);
+  return HFE_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// copy `bytes` from a host or device source into device memory on the handle's stream
+hfe_status copy_in(hfe_handle* h, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return HFE_OK;
+  cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  return cuda_check(h, cudaMemcpyAsync(dst, src, bytes, k, h->s), "copy in");
+}
+
+// copy device memory out to a host or device destination; host copies complete on return
+hfe_status copy_out(hfe_handle* h, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0 || dst == nullptr) return HFE_OK;
+  bool dev = is_device_ptr(dst);
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s),
+                     "copy out"));
+  if (!dev) HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));
+  return HFE_OK;
+}
+
+hfe_status upload_material(hfe_handle* h, const hfe_material* m) {
+  if (m == nullptr || m->theta == nullptr) return fail(h, HFE_EINVAL, "material: theta is NULL");
+  if (!(m->n_mat == 1 || m->n_mat == h->n_el)) return fail(h, HFE_EINVAL, "material: n_mat must be 1 or n_el");
+  if (m->hardening != HFE_HARDENING_SWIFT && m->hardening != HFE_HARDENING_VOCE)
+    return fail(h, HFE_EINVAL, "material: unknown hardening law");
+  if (h->mat64 != nullptr && m->n_mat != h->n_mat) return fail(h, HFE_EINVAL, "material: n_mat changed");
+  if (h->mat64 != nullptr && m->hardening != h->hardening) return fail(h, HFE_EINVAL, "material: hardening changed");
+  h->n_mat = m->n_mat;
+  h->hardening = m->hardening;
+  if (h->mat64 == nullptr) {
+    HFE_TRY(dalloc(h, &h->theta, (size_t)h->n_mat * 11));
+    HFE_TRY(dalloc(h, &h->mat64, (size_t)h->n_mat));
+    HFE_TRY(dalloc(h, &h->matf, (size_t)h->n_mat));
+  }
+  HFE_TRY(copy_in(h, h->theta, m->theta, sizeof(double) * h->n_mat * 11));
+  if (m->Theta != nullptr) {
+    if (h->Theta == nullptr) HFE_TRY(dalloc(h, &h->Theta, (size_t)h->n_mat * 9));
+    HFE_TRY(copy_in(h, h->Theta, m->Theta, sizeof(double) * h->n_mat * 9));
+  } else if (h->Theta != nullptr) {
+    h->Theta = nullptr;   // buffer stays in allocs; identity axes from now on
+  }
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
+  launch_material_setup(h->theta, h->Theta, h->n_mat, h->mat64, h->matf, h->bad, h->s);
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
+  HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "material set-up"));
+  if (*h->h_bad != 0) return fail(h, HFE_EINVAL, "material: " + std::to_string(*h->h_bad) +
+                                                     " record(s) with non-positive Hill eigenvalue or elastic modulus");
+  return HFE_OK;
+}
+
+hfe_status read_status(hfe_handle* h) {
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_status, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->s),
+                     "status"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_sc, h->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, h->s), "scalars"));
+  HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "kernels"));
+  return cuda_check(h, cudaGetLastError(), "kernel launch");
+}
+
+// one sweep on the internal stream; u may be any device pointer; R into Rdst (device)
+hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev) {
+  SweepArgs a;
+  a.X = h->X;
+  a.conn = h->conn;
+  a.u = u_dev;
+  a.hist = h->hist;
+  a.hist_trial = h->hist_trial;
+  a.mat = h->fp64 ? (const void*)h->mat64 : (const void*)h->matf;
+  a.mat_per_element = h->n_mat > 1 ? 1 : 0;
+  a.hardening = h->hardening;
+  a.elems = h->elems;
+  a.slot = h->slot;
+  a.K = h->K;
+  a.R = Rdst;
+  a.f_ext = h->f_ext;
+  a.load = load;
+  a.sigma = sigma_dev;
+  a.status = h->status;
+  a.n_gp = h->n_gp;
+  a.local_maxit = h->opt.local_maxit;
+  a.local_tol = h->opt.local_tol;
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->s), "memset"));
+  launch_gp_sweep(a, h->fp64 != 0, mode, h->P.color_off, h->s);
+  return HFE_OK;
+}
+
+hfe_status check_sweep_status(hfe_handle* h) {
+  const DevStatus& st = *h->h_status;
+  if (st.detj > 0) return fail(h, HFE_EDETJ, std::to_string(st.detj) + " Gauss point(s) with det J <= 0");
+  if (st.nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite internal force");
+  if (st.local_fail > 0)
+    return fail(h, HFE_ELOCAL, std::to_string(st.local_fail) + " local return mapping(s) hit local_maxit");
+  return HFE_OK;
+}
+
+template <typename R>
+PcgVecs<R> vecs(hfe_handle* h) {
+  PcgVecs<R> v;
+  v.x = (R*)h->vx; v.r = (R*)h->vr; v.z = (R*)h->vz; v.p = (R*)h->vp; v.q = (R*)h->vq; v.minv = (R*)h->vminv;
+  return v;
+}
+
+template <typename R>
+hfe_status build_pcg_graph(hfe_handle* h, int len) {
+  if (h->pcg_graph != nullptr && h->pcg_graph_len == len) return HFE_OK;
+  if (h->pcg_graph != nullptr) {
+    cudaGraphExecDestroy(h->pcg_graph);
+    h->pcg_graph = nullptr;
+  }
+  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  PcgVecs<R> v = vecs<R>(h);
+  const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
+  cudaGraph_t g;
+  HFE_TRY(cuda_check(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal), "capture"));
+  for (int i = 0; i < len; ++i) pcg_iteration<R>(K, (const R*)h->K, h->freem, v, block3, h->sc, h->part, h->s);
+  HFE_TRY(cuda_check(h, cudaStreamEndCapture(h->s, &g), "end capture"));
+  cudaError_t e = cudaGraphInstantiate(&h->pcg_graph, g, 0);
+  cudaGraphDestroy(g);
+  HFE_TRY(cuda_check(h, e, "graph instantiate"));
+  h->pcg_graph_len = len;
+  return HFE_OK;
+}
+
+// Solve Kt x = bscale * b with PCG (b device FP64 [n_dof]); x left in h->vx (precision R).
+template <typename R>
+hfe_status pcg_solve(hfe_handle* h, const double* b, double bscale, int64_t* iters_out) {
+  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  PcgVecs<R> v = vecs<R>(h);
+  const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
+  precond_setup<R>(K, (const R*)h->K, h->diag_slot, h->freem, v.minv, block3, h->bad, h->s);
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
+  {
+    const double rt2 = h->opt.pcg_rtol * h->opt.pcg_rtol;
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(&h->sc->target, &rt2, sizeof(double), cudaMemcpyHostToDevice, h->s),
+                       "copy"));
+    HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));   // rt2 lives on this stack frame
+  }
+  pcg_init<R>(b, bscale, h->freem, v, block3, h->n_nodes, h->sc, h->part, h->s);
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
+  HFE_TRY(read_status(h));
+  if (*h->h_bad != 0) return fail(h, HFE_EPCG, "preconditioner: non-positive diagonal (block)");
+  const double rr0 = h->h_sc->rr0;
+  if (!std::isfinite(rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
+  int64_t it = 0;
+  if (rr0 > 0.0) {
+    const double target = h->opt.pcg_rtol * h->opt.pcg_rtol * rr0;
+    const int m = std::max(1, h->opt.pcg_check_every);
+    HFE_TRY(build_pcg_graph<R>(h, m));
+    bool done = false;
+    while (it < h->opt.pcg_maxit) {
+      HFE_TRY(cuda_check(h, cudaGraphLaunch(h->pcg_graph, h->s), "graph launch"));
+      it += m;
+      HFE_TRY(read_status(h));
+      if (h->h_sc->done || h->h_sc->rr <= target) { done = true; break; }
+      if (h->h_sc->breakdown) return fail(h, HFE_EPCG, "CG breakdown (p.Ap <= 0 or non-finite)");
+    }
+    if (!done) {
+      if (iters_out) *iters_out = it;
+      return fail(h, HFE_EPCG, "CG did not converge: |r|/|b| = " + std::to_string(std::sqrt(h->h_sc->rr / rr0)));
+    }
+  } else {
+    HFE_TRY(cuda_check(h, cudaMemsetAsync(v.x, 0, sizeof(R) * h->n_dof, h->s), "memset"));
+  }
+  if (iters_out) *iters_out = it;
+  return HFE_OK;
+}
+
+hfe_status solve_any(hfe_handle* h, const double* b, double bscale, int64_t* iters) {
+  return h->fp64 ? pcg_solve<double>(h, b, bscale, iters) : pcg_solve<float>(h, b, bscale, iters);
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace hfe
+
+extern "C" {
+
+void hfe_default_options(hfe_options* o, int precision) {
+  std::memset(o, 0, sizeof(*o));
+  o->precision = precision;
+  o->newton_rtol = precision == HFE_PRECISION_FP64 ? 1e-10 : 1e-6;
+  o->newton_atol = 1.0;
+  o->newton_maxit = 25;
+  o->newton_stag_tol = 1e-4;
+  o->pcg_rtol = precision == HFE_PRECISION_FP64 ? 1e-12 : 1e-6;
+  o->pcg_maxit = 20000;
+  o->pcg_check_every = 16;
+  o->precond = HFE_PRECOND_BLOCK3;
+  o->local_maxit = 50;
+  o->local_tol = 1e-14;
+  o->ckpt_every = 1;
+  o->predictor = 1;
+}
+
+hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
+                      void* stream, hfe_handle** out) {
+  if (out == nullptr) return HFE_EINVAL;
+  *out = nullptr;
+  if (mesh == nullptr || mesh->X == nullptr || mesh->conn == nullptr || mesh->n_nodes <= 0 || mesh->n_el <= 0)
+    return HFE_EINVAL;
+  hfe_handle* h = new (std::nothrow) hfe_handle();
+  if (h == nullptr) return HFE_ENOMEM;
+  *out = h;
+  if (opt) h->opt = *opt;
+  else hfe_default_options(&h->opt, HFE_PRECISION_FP64);
+  if (h->opt.precision != HFE_PRECISION_FP64 && h->opt.precision != HFE_PRECISION_MIXED)
+    return fail(h, HFE_EINVAL, "options: unknown precision");
+  h->fp64 = h->opt.precision == HFE_PRECISION_FP64;
+  h->user = reinterpret_cast<cudaStream_t>(stream);
+  HFE_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"));
+  HFE_TRY(cuda_check(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "event"));
+  HFE_TRY(cuda_check(h, cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "event"));
+  HFE_TRY(cuda_check(h, cudaEventCreate(&h->t0), "event"));
+  HFE_TRY(cuda_check(h, cudaEventCreate(&h->t1), "event"));
+  h->n_nodes = mesh->n_nodes;
+  h->n_el = mesh->n_el;
+  h->n_dof = 3 * h->n_nodes;
+  h->n_gp = 8 * h->n_el;
+  // host copies of the mesh (pageable or device input)
+  std::vector<int32_t> conn_h(h->n_el * 8);
+  if (is_device_ptr(mesh->conn)) {
+    if (cudaMemcpy(conn_h.data(), mesh->conn, conn_h.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(h, HFE_ECUDA, "copy conn");
+  } else {
+    std::memcpy(conn_h.data(), mesh->conn, conn_h.size() * 4);
+  }
+  std::string perr;
+  if (!build_pattern(h->n_nodes, h->n_el, conn_h.data(), h->P, perr)) return fail(h, HFE_EINVAL, "mesh: " + perr);
+  StreamScope scope(h);
+  // device allocations
+  const bool f64 = h->fp64 != 0;
+  const size_t rsz = f64 ? 8 : 4;
+  HFE_TRY(dalloc(h, &h->X, h->n_dof));
+  HFE_TRY(dalloc(h, &h->conn, h->n_el * 8));
+  HFE_TRY(dalloc(h, &h->u, h->n_dof));
+  HFE_TRY(dalloc(h, &h->hist, 8 * h->n_gp));
+  HFE_TRY(dalloc(h, &h->hist_trial, 8 * h->n_gp));
+  HFE_TRY(dalloc(h, &h->rowptr, h->n_nodes + 1));
+  HFE_TRY(dalloc(h, &h->cols, h->P.n_blocks));
+  HFE_TRY(dalloc(h, &h->diag_slot, h->n_nodes));
+  HFE_TRY(dalloc(h, &h->slot, h->n_el * 64));
+  HFE_TRY(dalloc(h, &h->elems, h->n_el));
+  {
+    unsigned char* k = nullptr;
+    HFE_TRY(dalloc(h, &k, rsz * 9 * h->P.n_blocks));
+    h->K = k;
+  }
+  HFE_TRY(dalloc(h, &h->R, h->n_dof));
+  HFE_TRY(dalloc(h, &h->freem, h->n_dof));
+  HFE_TRY(dalloc(h, &h->status, 1));
+  HFE_TRY(dalloc(h, &h->sc, 1));
+  HFE_TRY(dalloc(h, &h->part, partial_slots()));
+  HFE_TRY(dalloc(h, &h->bad, 1));
+  HFE_TRY(dalloc(h, &h->tmp64, h->n_dof));
+  HFE_TRY(dalloc(h, &h->b64, h->n_dof));
+  {
+    unsigned char* b = nullptr;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vx = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vr = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vz = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vp = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vq = b;
+    HFE_TRY(dalloc(h, &b, rsz * 9 * h->n_nodes)); h->vminv = b;
+  }
+  if (cudaMallocHost(&h->h_sc, sizeof(PcgScalars)) != cudaSuccess ||
+      cudaMallocHost(&h->h_status, sizeof(DevStatus)) != cudaSuccess || cudaMallocHost(&h->h_bad, sizeof(int)) != cudaSuccess)
+    return fail(h, HFE_ENOMEM, "pinned host allocation failed");
+  HFE_TRY(copy_in(h, h->X, mesh->X, sizeof(double) * h->n_dof));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->conn, conn_h.data(), conn_h.size() * 4, cudaMemcpyHostToDevice, h->s), "copy"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->rowptr, h->P.rowptr.data(), 8 * (h->n_nodes + 1), cudaMemcpyHostToDevice, h->s),
+                     "copy"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->cols, h->P.cols.data(), 4 * h->P.n_blocks, cudaMemcpyHostToDevice, h->s), "copy"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->diag_slot, h->P.diag_slot.data(), 8 * h->n_nodes, cudaMemcpyHostToDevice, h->s),
+                     "copy"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->slot, h->P.slot.data(), 4 * h->P.slot.size(), cudaMemcpyHostToDevice, h->s),
+                     "copy"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->elems, h->P.elems.data(), 4 * h->n_el, cudaMemcpyHostToDevice, h->s), "copy"));
+  // boundary data
+  std::vector<uint8_t> freem(h->n_dof, 1);
+  std::vector<int64_t> fdof;
+  std::vector<double> fval;
+  if (bc != nullptr && bc->n_fixed > 0) {
+    if (bc->dof == nullptr || bc->value == nullptr) return fail(h, HFE_EINVAL, "bc: dof/value NULL");
+    fdof.resize(bc->n_fixed);
+    fval.resize(bc->n_fixed);
+    if (is_device_ptr(bc->dof)) {
+      cudaMemcpy(fdof.data(), bc->dof, 8 * bc->n_fixed, cudaMemcpyDeviceToHost);
+      cudaMemcpy(fval.data(), bc->value, 8 * bc->n_fixed, cudaMemcpyDeviceToHost);
+    } else {
+      std::memcpy(fdof.data(), bc->dof, 8 * bc->n_fixed);
+      std::memcpy(fval.data(), bc->value, 8 * bc->n_fixed);
+    }
+    for (int64_t i = 0; i < bc->n_fixed; ++i) {
+      if (fdof[i] < 0 || fdof[i] >= h->n_dof) return fail(h, HFE_EINVAL, "bc: dof out of range");
+      if (!freem[fdof[i]]) return fail(h, HFE_EINVAL, "bc: duplicate dof");
+      freem[fdof[i]] = 0;
+    }
+  }
+  h->n_fixed = (int64_t)fdof.size();
+  HFE_TRY(dalloc(h, &h->fixed_dof, h->n_fixed));
+  HFE_TRY(dalloc(h, &h->fixed_val, h->n_fixed));
+  if (h->n_fixed) {
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->fixed_dof, fdof.data(), 8 * h->n_fixed, cudaMemcpyHostToDevice, h->s), "copy"));
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->fixed_val, fval.data(), 8 * h->n_fixed, cudaMemcpyHostToDevice, h->s), "copy"));
+  }
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->freem, freem.data(), h->n_dof, cudaMemcpyHostToDevice, h->s), "copy"));
+  if (bc != nullptr && bc->f_ext != nullptr) {
+    HFE_TRY(dalloc(h, &h->f_ext, h->n_dof));
+    HFE_TRY(copy_in(h, h->f_ext, bc->f_ext, sizeof(double) * h->n_dof));
+  }
+  HFE_TRY(upload_material(h, mat));
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, sizeof(double) * h->n_dof, h->s), "memset"));
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->hist, 0, sizeof(double) * 8 * h->n_gp, h->s), "memset"));
+  launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+  HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "create"));
+  return cuda_check(h, cudaGetLastError(), "create kernels");
+}
+
+void hfe_destroy(hfe_handle* h) {
+  if (h == nullptr) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  adjoint_free(h->adj);
+  if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->sigma) cudaFree(h->sigma);
+  if (h->h_sc) cudaFreeHost(h->h_sc);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_bad) cudaFreeHost(h->h_bad);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->t0) cudaEventDestroy(h->t0);
+  if (h->t1) cudaEventDestroy(h->t1);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+}
+
+const char* hfe_last_error(const hfe_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info) {
+  if (h == nullptr || info == nullptr) return HFE_EINVAL;
+  info->n_nodes = h->n_nodes;
+  info->n_el = h->n_el;
+  info->n_dof = h->n_dof;
+  info->n_gp = h->n_gp;
+  info->n_blocks = h->P.n_blocks;
+  info->n_fixed = h->n_fixed;
+  info->n_colors = h->P.n_colors;
+  info->precision = h->opt.precision;
+  info->device_bytes = (int64_t)h->device_bytes;
+  return HFE_OK;
+}
+
+hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat) {
+  if (h == nullptr) return HFE_EINVAL;
+  StreamScope scope(h);
+  HFE_TRY(upload_material(h, mat));
+  launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+  return cuda_check(h, cudaStreamSynchronize(h->s), "set material");
+}
+
+hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist) {
+  if (h == nullptr) return HFE_EINVAL;
+  StreamScope scope(h);
+  if (u) HFE_TRY(copy_in(h, h->u, u, sizeof(double) * h->n_dof));
+  else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, sizeof(double) * h->n_dof, h->s), "memset"));
+  if (hist) HFE_TRY(copy_in(h, h->hist, hist, sizeof(double) * 7 * h->n_gp));
+  else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->hist, 0, sizeof(double) * 7 * h->n_gp, h->s), "memset"));
+  launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+  h->t_state = 0.0;
+  return cuda_check(h, cudaStreamSynchronize(h->s), "set state");
+}
+
+hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist) {
+  if (h == nullptr) return HFE_EINVAL;
+  StreamScope scope(h);
+  HFE_TRY(copy_out(h, u, h->u, sizeof(double) * h->n_dof));
+  HFE_TRY(copy_out(h, hist, h->hist, sizeof(double) * 7 * h->n_gp));
+  return cuda_check(h, cudaStreamSynchronize(h->s), "get state");
+}
+
+hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, double* R_out, double* hist_trial_out,
+                        hfe_stats* stats) {
+  if (h == nullptr || u == nullptr) return HFE_EINVAL;
+  if (mode != HFE_SWEEP_RESIDUAL && mode != HFE_SWEEP_TANGENT) return fail(h, HFE_EINVAL, "sweep: unknown mode");
+  auto w0 = std::chrono::steady_clock::now();
+  StreamScope scope(h);
+  const double* ud = u;
+  if (!is_device_ptr(u)) {
+    HFE_TRY(copy_in(h, h->tmp64, u, sizeof(double) * h->n_dof));
+    ud = h->tmp64;
+  }
+  double* Rd = (R_out != nullptr && is_device_ptr(R_out)) ? R_out : h->R;
+  cudaEventRecord(h->t0, h->s);
+  HFE_TRY(sweep(h, ud, load, mode, Rd, nullptr));
+  cudaEventRecord(h->t1, h->s);
+  if (R_out != nullptr && Rd != R_out) HFE_TRY(copy_out(h, R_out, Rd, sizeof(double) * h->n_dof));
+  if (hist_trial_out) HFE_TRY(copy_out(h, hist_trial_out, h->hist_trial, sizeof(double) * 7 * h->n_gp));
+  if (stats != nullptr) {
+    HFE_TRY(read_status(h));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->sweeps = 1;
+    stats->plastic_gps = h->h_status->plastic;
+    stats->local_fail = h->h_status->local_fail;
+    stats->max_local_iters = h->h_status->max_local_iters;
+    stats->sweep_ms = elapsed(h->t0, h->t1);
+    stats->total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+    return check_sweep_status(h);
+  }
+  return cuda_check(h, cudaGetLastError(), "sweep launch");
+}
+
+hfe_status hfe_get_bsr(hfe_handle* h, int64_t* rowptr, int32_t* cols, double* vals) {
+  if (h == nullptr) return HFE_EINVAL;
+  if (rowptr) std::memcpy(rowptr, h->P.rowptr.data(), 8 * (h->n_nodes + 1));
+  if (cols) std::memcpy(cols, h->P.cols.data(), 4 * h->P.n_blocks);
+  if (vals) {
+    StreamScope scope(h);
+    const size_t n = 9 * (size_t)h->P.n_blocks;
+    if (h->fp64) {
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(vals, h->K, 8 * n, cudaMemcpyDeviceToHost, h->s), "copy"));
+    } else {
+      std::vector<float> tmp(n);
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(tmp.data(), h->K, 4 * n, cudaMemcpyDeviceToHost, h->s), "copy"));
+      HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));
+      for (size_t i = 0; i < n; ++i) vals[i] = tmp[i];
+    }
+    HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));
+  }
+  return HFE_OK;
+}
+
+hfe_status hfe_spmv(hfe_handle* h, const double* x, double* y) {
+  if (h == nullptr || x == nullptr || y == nullptr) return HFE_EINVAL;
+  StreamScope scope(h);
+  HFE_TRY(copy_in(h, h->tmp64, x, sizeof(double) * h->n_dof));
+  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  if (h->fp64) {
+    spmv<double>(K, (const double*)h->K, h->freem, h->tmp64, (double*)h->vq, nullptr, nullptr, h->s);
+    HFE_TRY(copy_out(h, y, h->vq, sizeof(double) * h->n_dof));
+  } else {
+    to_float(h->tmp64, (float*)h->vp, h->n_dof, h->s);
+    spmv<float>(K, (const float*)h->K, h->freem, (const float*)h->vp, (float*)h->vq, nullptr, nullptr, h->s);
+    to_double((const float*)h->vq, h->tmp64, h->n_dof, h->s);
+    HFE_TRY(copy_out(h, y, h->tmp64, sizeof(double) * h->n_dof));
+  }
+  return cuda_check(h, cudaStreamSynchronize(h->s), "spmv");
+}
+
+hfe_status hfe_solve(hfe_handle* h, const double* b, double* x, hfe_stats* stats) {
+  if (h == nullptr || b == nullptr || x == nullptr) return HFE_EINVAL;
+  StreamScope scope(h);
+  HFE_TRY(copy_in(h, h->tmp64, b, sizeof(double) * h->n_dof));
+  int64_t it = 0;
+  cudaEventRecord(h->t0, h->s);
+  hfe_status st = solve_any(h, h->tmp64, 1.0, &it);
+  cudaEventRecord(h->t1, h->s);
+  if (st != HFE_OK) return st;
+  if (h->fp64) HFE_TRY(copy_out(h, x, h->vx, sizeof(double) * h->n_dof));
+  else {
+    to_double((const float*)h->vx, h->tmp64, h->n_dof, h->s);
+    HFE_TRY(copy_out(h, x, h->tmp64, sizeof(double) * h->n_dof));
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    cudaStreamSynchronize(h->s);
+    stats->pcg_iters = h->h_sc->iters;
+    stats->solve_ms = elapsed(h->t0, h->t1);
+  }
+  return cuda_check(h, cudaStreamSynchronize(h->s), "solve");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Newton driver (shared with the adjoint's forward pass).
+hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double* u_out_dev_or_host,
+                            double* sigma_out, double* hist_out, hfe_stats* st, StepHook* hook) {
+  auto w0 = std::chrono::steady_clock::now();
+  hfe_stats loc;
+  std::memset(&loc, 0, sizeof(loc));
+  const bool u_out_dev = is_device_ptr(u_out_dev_or_host);
+  for (int n = 0; n < n_steps; ++n) {
+    double ref = -1.0, prev = 0.0;
+    const double t_prev = h->t_state;
+    if (h->opt.predictor) {
+      // tangent predictor on the converged start-of-step state (u_{n-1}, h_{n-1}):
+      // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment
+      HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
+      HFE_TRY(read_status(h));
+      loc.sweeps++;
+      HFE_TRY(check_sweep_status(h));
+      HFE_TRY(cuda_check(h, cudaMemsetAsync(h->tmp64, 0, sizeof(double) * h->n_dof, h->s), "memset"));
+      set_dirichlet(h->tmp64, h->fixed_dof, h->fixed_val, t[n] - t_prev, h->n_fixed, h->s);
+      Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+      if (h->fp64) {
+        spmv_rows<double>(K, (const double*)h->K, h->freem, h->tmp64, (double*)h->vq, h->s);
+        predictor_rhs<double>(h->R, (const double*)h->vq, h->f_ext, t[n] - t_prev, h->freem, h->b64, h->n_dof, h->s);
+      } else {
+        to_float(h->tmp64, (float*)h->vp, h->n_dof, h->s);
+        spmv_rows<float>(K, (const float*)h->K, h->freem, (const float*)h->vp, (float*)h->vq, h->s);
+        predictor_rhs<float>(h->R, (const float*)h->vq, h->f_ext, t[n] - t_prev, h->freem, h->b64, h->n_dof, h->s);
+      }
+      free_norm(h->b64, h->freem, h->n_dof, h->sc, h->part, h->s);
+      HFE_TRY(read_status(h));
+      ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
+      set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
+      if (h->h_sc->norm2 > 0.0) {
+        cudaEventRecord(h->t0, h->s);
+        HFE_TRY(solve_any(h, h->b64, 1.0, nullptr));
+        cudaEventRecord(h->t1, h->s);
+        cudaEventSynchronize(h->t1);
+        loc.solve_ms += elapsed(h->t0, h->t1);
+        loc.pcg_iters += h->h_sc->iters;
+        if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
+        else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
+      }
+    } else {
+      set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
+    }
+    int stall = 0;
+    bool conv = false;
+    for (int it = 0; it <= h->opt.newton_maxit; ++it) {
+      cudaEventRecord(h->t0, h->s);
+      HFE_TRY(sweep(h, h->u, t[n], HFE_SWEEP_TANGENT, h->R, nullptr));
+      cudaEventRecord(h->t1, h->s);
+      free_norm(h->R, h->freem, h->n_dof, h->sc, h->part, h->s);
+      HFE_TRY(read_status(h));
+      loc.sweeps++;
+      loc.sweep_ms += elapsed(h->t0, h->t1);
+      HFE_TRY(check_sweep_status(h));
+      loc.plastic_gps = h->h_status->plastic;
+      loc.max_local_iters = std::max<int32_t>(loc.max_local_iters, (int32_t)h->h_status->max_local_iters);
+      if (h->h_sc->nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite residual");
+      const double nrm = std::sqrt(h->h_sc->norm2);
+      loc.last_residual = nrm;
+      if (ref < 0.0) ref = std::max(nrm, h->opt.newton_atol);
+      if (nrm <= h->opt.newton_rtol * ref) { conv = true; break; }
+      if (!h->fp64 && it >= 2) {   // mixed: accept a stagnated residual below newton_stag_tol
+        stall = (nrm > 0.5 * prev) ? stall + 1 : 0;
+        if (stall >= 2 && nrm <= h->opt.newton_stag_tol * ref) { conv = true; break; }
+      }
+      prev = nrm;
+      if (it == h->opt.newton_maxit) break;
+      int64_t pit = 0;
+      cudaEventRecord(h->t0, h->s);
+      HFE_TRY(solve_any(h, h->R, -1.0, &pit));
+      cudaEventRecord(h->t1, h->s);
+      cudaEventSynchronize(h->t1);
+      loc.solve_ms += elapsed(h->t0, h->t1);
+      loc.pcg_iters += h->h_sc->iters;
+      (void)pit;
+      if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
+      else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
+      loc.newton_iters++;
+    }
+    if (!conv) {
+      if (st) *st = loc;
+      return fail(h, HFE_ENEWTON, "Newton did not converge at step " + std::to_string(n) + ", |R| = " +
+                                      std::to_string(loc.last_residual));
+    }
+    if (hook) HFE_TRY(hook->before_commit(h, n));
+    if (sigma_out != nullptr && n == n_steps - 1) {
+      if (h->sigma == nullptr) {
+        if (cudaMalloc(&h->sigma, sizeof(double) * 6 * h->n_gp) != cudaSuccess) return fail(h, HFE_ENOMEM, "sigma");
+      }
+      HFE_TRY(sweep(h, h->u, t[n], HFE_SWEEP_RESIDUAL, h->R, h->sigma));
+      HFE_TRY(read_status(h));
+      HFE_TRY(copy_out(h, sigma_out, h->sigma, sizeof(double) * 6 * h->n_gp));
+    }
+    std::swap(h->hist, h->hist_trial);   // commit h_n = H(u_n, h_{n-1})
+    if (!h->fp64) launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+    if (u_out_dev_or_host != nullptr) {
+      double* dst = u_out_dev_or_host + (size_t)n * h->n_dof;
+      if (u_out_dev) HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, h->u, 8 * h->n_dof, cudaMemcpyDeviceToDevice, h->s), "copy"));
+      else HFE_TRY(copy_out(h, dst, h->u, sizeof(double) * h->n_dof));
+    }
+    h->t_state = t[n];
+    if (hook) HFE_TRY(hook->after_commit(h, n));
+    loc.steps_done = n + 1;
+  }
+  if (hist_out) HFE_TRY(copy_out(h, hist_out, h->hist, sizeof(double) * 7 * h->n_gp));
+  HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "forward"));
+  loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+  if (st) *st = loc;
+  return HFE_OK;
+}
+
+extern "C" hfe_status hfe_forward(hfe_handle* h, int n_steps, const double* t, double* u_out, double* sigma_out,
+                                  double* hist_out, hfe_stats* stats) {
+  if (h == nullptr || t == nullptr || n_steps <= 0) return HFE_EINVAL;
+  StreamScope scope(h);
+  std::vector<double> th(n_steps);
+  std::memcpy(th.data(), t, sizeof(double) * n_steps);
+  return newton_steps(h, n_steps, th.data(), u_out, sigma_out, hist_out, stats, nullptr);
+}
+
+extern "C" hfe_status hfe_adjoint(hfe_handle* h, int n_steps, const double* t, const double* u_target, double w,
+                                  double* J_out, double* grad_out, hfe_stats* stats) {
+  if (h == nullptr || t == nullptr || n_steps <= 0 || u_target == nullptr) return HFE_EINVAL;
+  StreamScope scope(h);
+  return adjoint_run(h, n_steps, t, u_target, w, J_out, grad_out, stats);
+}

@@ -1,0 +1,126 @@
+// Library handle and host helpers shared by the translation units (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "hfe_internal.h"
+#include "pattern.h"
+#include "solver.h"
+
+namespace hfe {
+struct AdjointWork;
+struct StepHook;
+}  // namespace hfe
+
+using hfe::DevStatus;
+using hfe::MatRec;
+using hfe::MatRecF;
+using hfe::Pattern;
+using hfe::PcgScalars;
+
+struct hfe_handle {
+  hfe_options opt;
+  int fp64 = 1;
+  cudaStream_t user = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  int64_t n_nodes = 0, n_el = 0, n_dof = 0, n_gp = 0, n_fixed = 0, n_mat = 1;
+  int hardening = 0;
+  Pattern P;
+  // device buffers
+  double* X = nullptr;
+  int32_t* conn = nullptr;
+  double* u = nullptr;
+  double* hist = nullptr;
+  double* hist_trial = nullptr;
+  int64_t* rowptr = nullptr;
+  int32_t* cols = nullptr;
+  int64_t* diag_slot = nullptr;
+  int32_t* slot = nullptr;
+  int32_t* elems = nullptr;
+  void* K = nullptr;
+  double* R = nullptr;
+  double* f_ext = nullptr;
+  int64_t* fixed_dof = nullptr;
+  double* fixed_val = nullptr;
+  uint8_t* freem = nullptr;
+  double* theta = nullptr;
+  double* Theta = nullptr;
+  MatRec* mat64 = nullptr;
+  MatRecF* matf = nullptr;
+  DevStatus* status = nullptr;
+  PcgScalars* sc = nullptr;
+  double* part = nullptr;
+  int* bad = nullptr;
+  void* vx = nullptr; void* vr = nullptr; void* vz = nullptr; void* vp = nullptr; void* vq = nullptr;
+  void* vminv = nullptr;
+  double* tmp64 = nullptr;     // n_dof doubles
+  double* b64 = nullptr;       // n_dof doubles (predictor right-hand side)
+  double t_state = 0.0;        // load factor of the stored state
+  double* sigma = nullptr;     // n_gp * 6, allocated on demand
+  // pinned host mirrors of the device scalars
+  PcgScalars* h_sc = nullptr;
+  DevStatus* h_status = nullptr;
+  int* h_bad = nullptr;
+  // CUDA graph of pcg_check_every CG iterations
+  cudaGraphExec_t pcg_graph = nullptr;
+  int pcg_graph_len = 0;
+  size_t device_bytes = 0;
+  std::string err;
+  std::vector<void*> allocs;
+  hfe::AdjointWork* adj = nullptr;
+};
+
+
+namespace hfe {
+
+#define HFE_TRY(expr)              \
+  do {                             \
+    hfe_status _st = (expr);       \
+    if (_st != HFE_OK) return _st; \
+  } while (0)
+
+// Called by the Newton driver around each commit (used by the adjoint's forward pass).
+struct StepHook {
+  virtual ~StepHook() {}
+  virtual hfe_status before_commit(hfe_handle* h, int step) = 0;
+  virtual hfe_status after_commit(hfe_handle* h, int step) = 0;
+};
+
+// order the internal stream after the caller's stream, and the caller's after ours on exit
+struct StreamScope {
+  hfe_handle* h;
+  explicit StreamScope(hfe_handle* hh) : h(hh) {
+    cudaEventRecord(h->ev_in, h->user);
+    cudaStreamWaitEvent(h->s, h->ev_in, 0);
+  }
+  ~StreamScope() {
+    cudaEventRecord(h->ev_out, h->s);
+    cudaStreamWaitEvent(h->user, h->ev_out, 0);
+  }
+};
+
+hfe_status fail(hfe_handle* h, hfe_status st, const std::string& msg);
+hfe_status cuda_check(hfe_handle* h, cudaError_t e, const char* what);
+template <typename T>
+hfe_status dalloc(hfe_handle* h, T** p, size_t count);
+bool is_device_ptr(const void* p);
+hfe_status copy_in(hfe_handle* h, void* dst, const void* src, size_t bytes);
+hfe_status copy_out(hfe_handle* h, void* dst, const void* src, size_t bytes);
+hfe_status read_status(hfe_handle* h);
+hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev);
+hfe_status check_sweep_status(hfe_handle* h);
+hfe_status solve_any(hfe_handle* h, const double* b, double bscale, int64_t* iters);
+float elapsed(cudaEvent_t a, cudaEvent_t b);
+hfe_status newton_steps(hfe_handle* h, int n_steps, const double* t, double* u_out, double* sigma_out,
+                        double* hist_out, hfe_stats* st, StepHook* hook);
+
+// adjoint.cu
+hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t, const double* u_target, double w,
+                       double* J_out, double* grad_out, hfe_stats* stats);
+void adjoint_free(AdjointWork* w);
+
+}  // namespace hfe

@@ -1,0 +1,83 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hfe.h"
+
+namespace hfe {
+
+// Per-material record (FP64).  The Hill tensor is held in Mandel notation
+// (t = (T11, T22, T33, sqrt2 T12, sqrt2 T23, sqrt2 T13)) through its eigen-decomposition
+// H_M = QH diag(h) QH^T; column 0 of QH is the hydrostatic direction (1,1,1,0,0,0)/sqrt3
+// with h[0] = 0 (the Hill tensor is pressure-insensitive), so the isotropic elasticity is
+// diagonal in the same basis with eigenvalues kap3 = 3 lambda + 2 mu (column 0) and 2 mu.
+struct MatRec {
+  double lam, mu, kap3;
+  double h[6];
+  double hmin;        // smallest deviatoric eigenvalue of H_M
+  double QH[36];      // QH[i*6 + j]: component i of eigenvector j
+  double hard[3];     // hardening parameters (h1, h2, h3)
+  double pad;
+};
+
+// Mixed-precision record: FP32 copies for the FP32 arithmetic, plus the FP64 values the
+// FP64 steps of the return mapping need.
+struct MatRecF {
+  double h64[6];
+  double mu64;
+  double hard64[3];
+  float lam, mu, kap3;
+  float h[6];
+  float hmin;
+  float QH[36];
+  float hard[3];
+  float pad;
+};
+
+// Device status counters written by the kernels (read back by the host after each call).
+struct DevStatus {
+  int local_fail;      // return mappings that hit the iteration bound
+  int nonfinite;       // non-finite values met
+  int detj;            // det(dX/dxi) <= 0 or det F <= 0 or stretch <= 0
+  int max_local_iters;
+  int plastic;         // plastic Gauss points in the sweep
+  int krylov_breakdown;
+  int pad[2];
+};
+
+struct SweepArgs {
+  const double* X;         // [n_nodes*3]
+  const int32_t* conn;     // [n_el*8]
+  const double* u;         // [n_dof]
+  const double* hist;      // [8][n_gp]  eps_p(6), alpha, sigma_y(alpha) cache
+  double* hist_trial;      // [8][n_gp]
+  const void* mat;         // MatRec* or MatRecF*
+  int mat_per_element;
+  int hardening;
+  const int32_t* elems;    // colour-sorted element ids
+  const int32_t* slot;     // [n_el*64] block index | store flag (bit 31)
+  void* K;                 // [n_blocks*9] float or double
+  double* R;               // [n_dof]
+  const double* f_ext;     // [n_dof] or nullptr
+  double load;
+  double* sigma;           // [n_gp*6] Cauchy stress output or nullptr
+  DevStatus* status;
+  int64_t n_gp;
+  int local_maxit;
+  double local_tol;
+};
+
+void launch_material_setup(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,
+                           MatRecF* outf, int* bad, cudaStream_t s);
+// mode: HFE_SWEEP_RESIDUAL / HFE_SWEEP_TANGENT; fp64 selects the plain FP64 kernel.
+void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
+                     cudaStream_t s);
+void launch_sigma_cache(double* hist, const void* mat, int mat_per_element, int hardening,
+                        int64_t n_gp, cudaStream_t s);
+
+}  // namespace hfe

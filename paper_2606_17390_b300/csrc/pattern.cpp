@@ -1,0 +1,154 @@
+// Host-side set-up of the assembly data: the block-CSR pattern of K (one 3x3 block per pair
+// of nodes that share an element), a conflict-free element colouring, and the element-to-
+// block slot map that replaces the paper's triplet -> COO -> CSR assembly (App. E,
+// Algorithm gpu_chunked_assembly): slot[e][a][b] is the index of block (conn[e][a],
+// conn[e][b]); bit 31 marks the first colour (in launch order) that writes the block, which
+// stores instead of adding, so K needs no clearing pass.
+#include "pattern.h"
+
+#include <algorithm>
+#include <cstring>
+#include <thread>
+
+namespace hfe {
+
+static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& f) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 4096 || nt == 1) {
+    f(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
+    if (b >= e) break;
+    th.emplace_back(f, b, e);
+  }
+  for (auto& x : th) x.join();
+}
+
+bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, Pattern& P, std::string& err) {
+  for (int64_t i = 0; i < n_el * 8; ++i) {
+    if (conn[i] < 0 || conn[i] >= n_nodes) {
+      err = "conn[" + std::to_string(i) + "] out of range";
+      return false;
+    }
+  }
+  for (int64_t e = 0; e < n_el; ++e)
+    for (int a = 0; a < 8; ++a)
+      for (int b = a + 1; b < 8; ++b)
+        if (conn[e * 8 + a] == conn[e * 8 + b]) {
+          err = "element " + std::to_string(e) + " repeats a node";
+          return false;
+        }
+  // node -> elements incidence
+  std::vector<int64_t> nptr(n_nodes + 1, 0);
+  for (int64_t i = 0; i < n_el * 8; ++i) nptr[conn[i] + 1]++;
+  for (int64_t n = 0; n < n_nodes; ++n) nptr[n + 1] += nptr[n];
+  for (int64_t n = 0; n < n_nodes; ++n) {
+    if (nptr[n + 1] == nptr[n]) {
+      err = "node " + std::to_string(n) + " belongs to no element";
+      return false;
+    }
+  }
+  std::vector<int32_t> nel(n_el * 8);
+  {
+    std::vector<int64_t> fill(nptr.begin(), nptr.end() - 1);
+    for (int64_t e = 0; e < n_el; ++e)
+      for (int a = 0; a < 8; ++a) nel[fill[conn[e * 8 + a]]++] = (int32_t)e;
+  }
+  // rows: sorted unique neighbour nodes
+  std::vector<int64_t> cnt(n_nodes, 0);
+  std::vector<std::vector<int32_t>> rows(n_nodes);
+  parallel_for(n_nodes, [&](int64_t b, int64_t e) {
+    std::vector<int32_t> buf;
+    for (int64_t n = b; n < e; ++n) {
+      buf.clear();
+      for (int64_t k = nptr[n]; k < nptr[n + 1]; ++k) {
+        const int32_t* c = conn + (int64_t)nel[k] * 8;
+        buf.insert(buf.end(), c, c + 8);
+      }
+      std::sort(buf.begin(), buf.end());
+      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+      rows[n] = buf;
+    }
+  });
+  P.rowptr.assign(n_nodes + 1, 0);
+  for (int64_t n = 0; n < n_nodes; ++n) P.rowptr[n + 1] = P.rowptr[n] + (int64_t)rows[n].size();
+  P.n_blocks = P.rowptr[n_nodes];
+  if (P.n_blocks >= (int64_t)0x7fffffff) {
+    err = "more than 2^31 - 1 blocks";
+    return false;
+  }
+  P.cols.resize(P.n_blocks);
+  P.diag_slot.resize(n_nodes);
+  parallel_for(n_nodes, [&](int64_t b, int64_t e) {
+    for (int64_t n = b; n < e; ++n) {
+      std::copy(rows[n].begin(), rows[n].end(), P.cols.begin() + P.rowptr[n]);
+      auto it = std::lower_bound(rows[n].begin(), rows[n].end(), (int32_t)n);
+      P.diag_slot[n] = P.rowptr[n] + (it - rows[n].begin());
+      std::vector<int32_t>().swap(rows[n]);
+    }
+  });
+  // greedy colouring: the smallest colour not used by an element sharing a node
+  std::vector<int8_t> color(n_el, -1);
+  int ncol = 0;
+  for (int64_t e = 0; e < n_el; ++e) {
+    uint64_t used = 0;
+    for (int a = 0; a < 8; ++a) {
+      int32_t n = conn[e * 8 + a];
+      for (int64_t k = nptr[n]; k < nptr[n + 1]; ++k) {
+        int8_t c = color[nel[k]];
+        if (c >= 0) used |= (1ull << c);
+      }
+    }
+    int c = 0;
+    while (c < 64 && (used >> c & 1ull)) ++c;
+    if (c >= 64) {
+      err = "element colouring needs more than 64 colours";
+      return false;
+    }
+    color[e] = (int8_t)c;
+    ncol = std::max(ncol, c + 1);
+  }
+  P.n_colors = ncol;
+  P.color_off.assign(ncol + 1, 0);
+  for (int64_t e = 0; e < n_el; ++e) P.color_off[color[e] + 1]++;
+  for (int c = 0; c < ncol; ++c) P.color_off[c + 1] += P.color_off[c];
+  P.elems.resize(n_el);
+  {
+    std::vector<int64_t> fill(P.color_off.begin(), P.color_off.end() - 1);
+    for (int64_t e = 0; e < n_el; ++e) P.elems[fill[color[e]]++] = (int32_t)e;
+  }
+  // slot map
+  P.slot.resize(n_el * 64);
+  parallel_for(n_el, [&](int64_t b, int64_t e_end) {
+    for (int64_t e = b; e < e_end; ++e) {
+      for (int a = 0; a < 8; ++a) {
+        int32_t r = conn[e * 8 + a];
+        const int32_t* c0 = P.cols.data() + P.rowptr[r];
+        const int32_t* c1 = P.cols.data() + P.rowptr[r + 1];
+        for (int bb = 0; bb < 8; ++bb) {
+          const int32_t* it = std::lower_bound(c0, c1, conn[e * 8 + bb]);
+          P.slot[e * 64 + a * 8 + bb] = (int32_t)(P.rowptr[r] + (it - c0));
+        }
+      }
+    }
+  });
+  // first-writer flags in launch order (colours in order; one writer per block per colour)
+  std::vector<uint8_t> seen(P.n_blocks, 0);
+  for (int64_t i = 0; i < n_el; ++i) {
+    int64_t e = P.elems[i];
+    for (int k = 0; k < 64; ++k) {
+      int32_t s = P.slot[e * 64 + k];
+      if (!seen[s]) {
+        seen[s] = 1;
+        P.slot[e * 64 + k] = (int32_t)((uint32_t)s | 0x80000000u);
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace hfe

@@ -1,0 +1,434 @@
+// Linear-algebra kernels of the Newton step: block-CSR SpMV with symmetric Dirichlet
+// elimination, Jacobi / 3x3 block-Jacobi preconditioned conjugate gradients, the free-dof
+// residual norm and the displacement update (paper Eq. Stiffness_mat; the paper's
+// identity-row elimination of App. E is made symmetric here: rows and columns of fixed dofs
+// are dropped, the diagonal set to one).
+//
+// Reductions are deterministic: every CTA writes a partial sum, and the last CTA to finish
+// (ticket counter, no waiting) adds the partials in index order and derives the scalars
+// (alpha, beta) that the next kernel reads from device memory, so a CG iteration needs no
+// host round trip and can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "solver.h"
+
+namespace hfe {
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of up to two doubles; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (w == 0) {
+    a = (l < nw) ? sa[l] : 0.0;
+    b = (l < nw) ? sb[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+}
+
+// Last-CTA reduction of the partials; returns true in every thread of the last CTA, which
+// then holds the totals in t0 / t1 (thread 0 only).
+__device__ __forceinline__ bool last_block_reduce(double pa, double pb, double* part, unsigned* ticket,
+                                                  double& t0, double& t1) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = pa;
+    part[2 * blockIdx.x + 1] = pb;
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  // fixed-order reduction: thread k sums partials k, k + blockDim, ... then a block reduction
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+    a += __ldcg(part + 2 * k);
+    b += __ldcg(part + 2 * k + 1);
+  }
+  block_sum2(a, b);
+  t0 = a;
+  t1 = b;
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// y = Kt x with Kt the matrix whose fixed rows/columns are dropped and whose fixed diagonal is 1.
+// One warp per block row; the lanes walk the row's values contiguously (coalesced), each
+// value v of the row belongs to block v/9, row (v%9)/3, column v%3.  Optionally
+// accumulates x.y (FP64) into a last-CTA reduction that sets alpha = rz / (p.Ap).
+template <typename R, bool COLMASK>
+__global__ void __launch_bounds__(kBlock) spmv_kernel(const int64_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ cols,
+                                                      const R* __restrict__ vals,
+                                                      const uint8_t* __restrict__ freem,
+                                                      const R* __restrict__ x, R* __restrict__ y,
+                                                      int64_t n_nodes, PcgScalars* sc, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * (kBlock / 32);
+  double dot = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); row < n_nodes; row += wstride) {
+    const int64_t b0 = rowptr[row];
+    const int nv = (int)(rowptr[row + 1] - b0) * 9;
+    const R* v = vals + b0 * 9;
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+    for (int k = lane; k < nv; k += 32) {
+      const int blk = k / 9;
+      const int rr = k - blk * 9;
+      const int i = rr / 3;
+      const int c = rr - i * 3;
+      const int64_t col = cols[b0 + blk];
+      const int64_t d = 3 * col + c;
+      const R xv = (!COLMASK || freem[d]) ? x[d] : R(0);
+      const R p = v[k] * xv;
+      a0 += (i == 0) ? p : R(0);
+      a1 += (i == 1) ? p : R(0);
+      a2 += (i == 2) ? p : R(0);
+    }
+    a0 = warp_sum_r(a0);
+    a1 = warp_sum_r(a1);
+    a2 = warp_sum_r(a2);
+    if (lane == 0) {
+      const int64_t d = 3 * row;
+      R o[3] = {a0, a1, a2};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        R out = freem[d + i] ? o[i] : (COLMASK ? x[d + i] : R(0));
+        y[d + i] = out;
+        dot += (double)x[d + i] * (double)out;
+      }
+    }
+  }
+  if (sc == nullptr) return;
+  double dummy = 0.0;
+  block_sum2(dot, dummy);
+  double tot, t1;
+  if (last_block_reduce(dot, 0.0, part, &sc->ticket, tot, t1) && threadIdx.x == 0) {
+    sc->pq = tot;
+    const bool ok = (tot > 0.0) && isfinite(tot) && isfinite(sc->rz);
+    sc->alpha = (ok && !sc->done) ? sc->rz / tot : 0.0;
+    if (!ok && !sc->done && sc->rz > 0.0) sc->breakdown = 1;
+  }
+}
+
+// x += alpha p; r -= alpha q; z = M^-1 r; partial (r.z, r.r); last CTA: beta = rz_new / rz.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) pcg_update_kernel(R* __restrict__ x, R* __restrict__ r, R* __restrict__ z,
+                                                            const R* __restrict__ p, const R* __restrict__ q,
+                                                            const R* __restrict__ minv, int block3,
+                                                            int64_t n_nodes, PcgScalars* sc, double* part) {
+  double rz = 0.0, rr = 0.0;
+  const R al = (R)sc->alpha;
+  for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < n_nodes; n += (int64_t)gridDim.x * kBlock) {
+    R rv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t d = 3 * n + i;
+      x[d] += al * p[d];
+      rv[i] = r[d] - al * q[d];
+      r[d] = rv[i];
+    }
+    R zv[3];
+    if (block3) {
+      const R* M = minv + 9 * n;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) zv[i] = M[3 * i] * rv[0] + M[3 * i + 1] * rv[1] + M[3 * i + 2] * rv[2];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) zv[i] = minv[3 * n + i] * rv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      z[3 * n + i] = zv[i];
+      rz += (double)rv[i] * (double)zv[i];
+      rr += (double)rv[i] * (double)rv[i];
+    }
+  }
+  block_sum2(rz, rr);
+  double trz, trr;
+  if (last_block_reduce(rz, rr, part, &sc->ticket, trz, trr) && threadIdx.x == 0) {
+    if (!sc->done) {
+      const double old = sc->rz;
+      sc->beta = (old > 0.0) ? trz / old : 0.0;
+      sc->rz = trz;
+      sc->rr = trr;
+      sc->iters += 1;
+      if (!isfinite(trz) || !isfinite(trr)) sc->breakdown = 1;
+      if (trr <= sc->target) sc->done = 1;
+    }
+  }
+}
+
+// p = z + beta p
+template <typename R>
+__global__ void __launch_bounds__(kBlock) pcg_p_kernel(R* __restrict__ p, const R* __restrict__ z, int64_t n_dof,
+                                                       const PcgScalars* sc) {
+  const int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (d < n_dof) p[d] = z[d] + (R)sc->beta * p[d];
+}
+
+// r = b (fixed components zeroed), x = 0, z = M^-1 r, p = z; rz = r.z, rr = r.r.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) pcg_init_kernel(const double* __restrict__ b, const uint8_t* __restrict__ freem,
+                                                          double bscale, R* __restrict__ x, R* __restrict__ r,
+                                                          R* __restrict__ z, R* __restrict__ p,
+                                                          const R* __restrict__ minv, int block3, int64_t n_nodes,
+                                                          PcgScalars* sc, double* part) {
+  double rz = 0.0, rr = 0.0;
+  for (int64_t n = (int64_t)blockIdx.x * kBlock + threadIdx.x; n < n_nodes; n += (int64_t)gridDim.x * kBlock) {
+    R rv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t d = 3 * n + i;
+      rv[i] = freem[d] ? (R)(bscale * b[d]) : R(0);
+      r[d] = rv[i];
+      x[d] = R(0);
+    }
+    R zv[3];
+    if (block3) {
+      const R* M = minv + 9 * n;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) zv[i] = M[3 * i] * rv[0] + M[3 * i + 1] * rv[1] + M[3 * i + 2] * rv[2];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) zv[i] = minv[3 * n + i] * rv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      z[3 * n + i] = zv[i];
+      p[3 * n + i] = zv[i];
+      rz += (double)rv[i] * (double)zv[i];
+      rr += (double)rv[i] * (double)rv[i];
+    }
+  }
+  block_sum2(rz, rr);
+  double trz, trr;
+  if (last_block_reduce(rz, rr, part, &sc->ticket, trz, trr) && threadIdx.x == 0) {
+    sc->rz = trz;
+    sc->rr = trr;
+    sc->rr0 = trr;
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->iters = 0;
+    sc->breakdown = (isfinite(trz) && isfinite(trr)) ? 0 : 1;
+    sc->target = sc->target * trr;     // the host stores rtol^2 here before the init kernel
+    sc->done = (trr <= sc->target) ? 1 : 0;
+  }
+}
+
+// Preconditioner from the diagonal blocks of Kt (fixed rows/columns dropped, unit diagonal):
+// Jacobi = 1 / diag, block3 = inverse of the 3x3 diagonal block (cofactors, FP64).
+template <typename R>
+__global__ void precond_kernel(const R* __restrict__ vals, const int64_t* __restrict__ diag_slot,
+                               const uint8_t* __restrict__ freem, R* __restrict__ minv, int block3,
+                               int64_t n_nodes, int* bad) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  const R* B = vals + 9 * diag_slot[n];
+  double M[3][3];
+  bool f[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) f[i] = freem[3 * n + i] != 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[i][j] = (f[i] && f[j]) ? (double)B[3 * i + j] : (i == j ? 1.0 : 0.0);
+  if (!block3) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (!(M[i][i] > 0.0)) atomicAdd(bad, 1);
+      minv[3 * n + i] = (R)(1.0 / M[i][i]);
+    }
+    return;
+  }
+  double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+  double c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+  double c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+  double det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
+  if (!(det > 0.0)) atomicAdd(bad, 1);
+  double id = 1.0 / det;
+  double I[3][3];
+  I[0][0] = c00 * id;
+  I[1][0] = c01 * id;
+  I[2][0] = c02 * id;
+  I[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) * id;
+  I[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) * id;
+  I[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) * id;
+  I[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) * id;
+  I[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) * id;
+  I[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) * id;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) minv[9 * n + 3 * i + j] = (R)I[i][j];
+}
+
+// ||R_free||^2 (FP64, deterministic) into sc->rr via the last-CTA reduction.
+__global__ void __launch_bounds__(kBlock) free_norm_kernel(const double* __restrict__ R_, const uint8_t* __restrict__ freem,
+                                                           int64_t n_dof, PcgScalars* sc, double* part) {
+  const int64_t d0 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  double s = 0.0, nf = 0.0;
+  for (int64_t d = d0; d < n_dof; d += (int64_t)gridDim.x * kBlock) {
+    double v = freem[d] ? R_[d] : 0.0;
+    s += v * v;
+    if (!isfinite(v)) nf += 1.0;
+  }
+  block_sum2(s, nf);
+  double ts, tn;
+  if (last_block_reduce(s, nf, part, &sc->ticket, ts, tn) && threadIdx.x == 0) {
+    sc->norm2 = ts;
+    sc->nonfinite = tn;
+  }
+}
+
+template <typename R>
+__global__ void add_update_kernel(double* __restrict__ u, const R* __restrict__ x, const uint8_t* __restrict__ freem,
+                                  int64_t n_dof) {
+  const int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (d < n_dof && freem[d]) u[d] += (double)x[d];
+}
+
+__global__ void set_dirichlet_kernel(double* __restrict__ u, const int64_t* __restrict__ dof,
+                                     const double* __restrict__ val, double t, int64_t n_fixed) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n_fixed) u[dof[i]] = t * val[i];
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (i < n) b[i] = (B)a[i];
+}
+
+// b = -(R + K du_D - dt f_ext) on free dofs, 0 on fixed dofs (tangent predictor right-hand side)
+template <typename R>
+__global__ void predictor_rhs_kernel(const double* __restrict__ R_, const R* __restrict__ Kd, const double* __restrict__ f_ext,
+                                     double dt, const uint8_t* __restrict__ freem, double* __restrict__ b, int64_t n_dof) {
+  const int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (d >= n_dof) return;
+  double v = R_[d] + (double)Kd[d] - (f_ext ? dt * f_ext[d] : 0.0);
+  b[d] = freem[d] ? -v : 0.0;
+}
+
+inline unsigned nblk(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+inline unsigned rblk(int64_t n, int per) {   // grid of a reducing (grid-stride) kernel
+  int64_t b = (n + per - 1) / per;
+  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+template <typename R>
+void spmv(const Csr& K, const R* vals, const uint8_t* freem, const R* x, R* y, PcgScalars* sc, double* part,
+          cudaStream_t s) {
+  spmv_kernel<R, true><<<rblk(K.n_nodes, kBlock / 32), kBlock, 0, s>>>(K.rowptr, K.cols, vals, freem, x, y, K.n_nodes,
+                                                                 sc, part);
+}
+
+template <typename R>
+void spmv_rows(const Csr& K, const R* vals, const uint8_t* freem, const R* x, R* y, cudaStream_t s) {
+  spmv_kernel<R, false><<<rblk(K.n_nodes, kBlock / 32), kBlock, 0, s>>>(K.rowptr, K.cols, vals, freem, x, y,
+                                                                         K.n_nodes, nullptr, nullptr);
+}
+
+template <typename R>
+void predictor_rhs(const double* R_, const R* Kd, const double* f_ext, double dt, const uint8_t* freem, double* b,
+                   int64_t n_dof, cudaStream_t s) {
+  predictor_rhs_kernel<R><<<nblk(n_dof, kBlock), kBlock, 0, s>>>(R_, Kd, f_ext, dt, freem, b, n_dof);
+}
+
+template <typename R>
+void pcg_init(const double* b, double bscale, const uint8_t* freem, PcgVecs<R>& v, int block3, int64_t n_nodes,
+              PcgScalars* sc, double* part, cudaStream_t s) {
+  pcg_init_kernel<R><<<rblk(n_nodes, kBlock), kBlock, 0, s>>>(b, freem, bscale, v.x, v.r, v.z, v.p, v.minv,
+                                                              block3, n_nodes, sc, part);
+}
+
+template <typename R>
+void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3, PcgScalars* sc,
+                   double* part, cudaStream_t s) {
+  spmv_kernel<R, true><<<rblk(K.n_nodes, kBlock / 32), kBlock, 0, s>>>(K.rowptr, K.cols, vals, freem, v.p, v.q,
+                                                                 K.n_nodes, sc, part);
+  pcg_update_kernel<R><<<rblk(K.n_nodes, kBlock), kBlock, 0, s>>>(v.x, v.r, v.z, v.p, v.q, v.minv, block3,
+                                                                  K.n_nodes, sc, part);
+  pcg_p_kernel<R><<<nblk(3 * K.n_nodes, kBlock), kBlock, 0, s>>>(v.p, v.z, 3 * K.n_nodes, sc);
+}
+
+template <typename R>
+void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
+                   int block3, int* bad, cudaStream_t s) {
+  precond_kernel<R><<<nblk(K.n_nodes, 128), 128, 0, s>>>(vals, diag_slot, freem, minv, block3, K.n_nodes, bad);
+}
+
+void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,
+               cudaStream_t s) {
+  free_norm_kernel<<<rblk(n_dof, kBlock), kBlock, 0, s>>>(R_, freem, n_dof, sc, part);
+}
+
+template <typename R>
+void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s) {
+  add_update_kernel<R><<<nblk(n_dof, kBlock), kBlock, 0, s>>>(u, x, freem, n_dof);
+}
+
+void set_dirichlet(double* u, const int64_t* dof, const double* val, double t, int64_t n_fixed, cudaStream_t s) {
+  if (n_fixed > 0) set_dirichlet_kernel<<<nblk(n_fixed, kBlock), kBlock, 0, s>>>(u, dof, val, t, n_fixed);
+}
+
+void to_double(const float* a, double* b, int64_t n, cudaStream_t s) {
+  convert_kernel<float, double><<<nblk(n, kBlock), kBlock, 0, s>>>(a, b, n);
+}
+void to_float(const double* a, float* b, int64_t n, cudaStream_t s) {
+  convert_kernel<double, float><<<nblk(n, kBlock), kBlock, 0, s>>>(a, b, n);
+}
+
+template void spmv<float>(const Csr&, const float*, const uint8_t*, const float*, float*, PcgScalars*, double*,
+                          cudaStream_t);
+template void spmv<double>(const Csr&, const double*, const uint8_t*, const double*, double*, PcgScalars*, double*,
+                           cudaStream_t);
+template void spmv_rows<float>(const Csr&, const float*, const uint8_t*, const float*, float*, cudaStream_t);
+template void spmv_rows<double>(const Csr&, const double*, const uint8_t*, const double*, double*, cudaStream_t);
+template void predictor_rhs<float>(const double*, const float*, const double*, double, const uint8_t*, double*,
+                                   int64_t, cudaStream_t);
+template void predictor_rhs<double>(const double*, const double*, const double*, double, const uint8_t*, double*,
+                                    int64_t, cudaStream_t);
+template void pcg_init<float>(const double*, double, const uint8_t*, PcgVecs<float>&, int, int64_t, PcgScalars*,
+                              double*, cudaStream_t);
+template void pcg_init<double>(const double*, double, const uint8_t*, PcgVecs<double>&, int, int64_t, PcgScalars*,
+                               double*, cudaStream_t);
+template void pcg_iteration<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int, PcgScalars*,
+                                   double*, cudaStream_t);
+template void pcg_iteration<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int, PcgScalars*,
+                                    double*, cudaStream_t);
+template void precond_setup<float>(const Csr&, const float*, const int64_t*, const uint8_t*, float*, int, int*,
+                                   cudaStream_t);
+template void precond_setup<double>(const Csr&, const double*, const int64_t*, const uint8_t*, double*, int, int*,
+                                    cudaStream_t);
+template void add_update<float>(double*, const float*, const uint8_t*, int64_t, cudaStream_t);
+template void add_update<double>(double*, const double*, const uint8_t*, int64_t, cudaStream_t);
+
+}  // namespace hfe

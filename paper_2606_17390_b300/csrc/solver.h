@@ -1,0 +1,60 @@
+// Solver kernels of the Newton step (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hfe {
+
+constexpr int kMaxRedBlocks = 148 * 16;   // grid cap of the reducing kernels (grid-stride)
+
+struct Csr {            // block-CSR pattern of K over node pairs (3x3 blocks)
+  const int64_t* rowptr;
+  const int32_t* cols;
+  int64_t n_nodes;
+  int64_t n_blocks;
+};
+
+struct PcgScalars {     // device-resident CG scalars
+  double rz, rr, rr0, pq, alpha, beta, norm2, nonfinite;
+  double target;        // rr at which the solve has converged (set by the host)
+  unsigned ticket;
+  int breakdown;
+  int iters;
+  int done;             // set once rr <= target: later iterations leave x unchanged
+};
+
+template <typename R>
+struct PcgVecs {
+  R *x, *r, *z, *p, *q, *minv;
+};
+
+inline int64_t partial_slots() { return 2 * (int64_t)kMaxRedBlocks; }
+
+template <typename R>
+void spmv(const Csr& K, const R* vals, const uint8_t* freem, const R* x, R* y, PcgScalars* sc, double* part,
+          cudaStream_t s);
+// y = K x over all columns (no Dirichlet elimination), fixed rows set to 0
+template <typename R>
+void spmv_rows(const Csr& K, const R* vals, const uint8_t* freem, const R* x, R* y, cudaStream_t s);
+template <typename R>
+void predictor_rhs(const double* R_, const R* Kd, const double* f_ext, double dt, const uint8_t* freem, double* b,
+                   int64_t n_dof, cudaStream_t s);
+template <typename R>
+void pcg_init(const double* b, double bscale, const uint8_t* freem, PcgVecs<R>& v, int block3, int64_t n_nodes,
+              PcgScalars* sc, double* part, cudaStream_t s);
+template <typename R>
+void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3, PcgScalars* sc,
+                   double* part, cudaStream_t s);
+template <typename R>
+void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
+                   int block3, int* bad, cudaStream_t s);
+void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,
+               cudaStream_t s);
+template <typename R>
+void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s);
+void set_dirichlet(double* u, const int64_t* dof, const double* val, double t, int64_t n_fixed, cudaStream_t s);
+void to_double(const float* a, double* b, int64_t n, cudaStream_t s);
+void to_float(const double* a, float* b, int64_t n, cudaStream_t s);
+
+}  // namespace hfe

@@ -1,0 +1,1071 @@
+// Gauss-point sweep: kinematics, log strain, Hill-48 return mapping, consistent tangent,
+// geometric post-processing, hex8 element contraction and conflict-free block-CSR scatter.
+//
+// Paper references: geometric pre-processor Eq. c_decomp; log-space elasticity Eq. T;
+// Hill-48 Eq. Phi_hill with App. A.1; hardening Eq. Hard; flow rule Eq. ep_evol and the
+// Kuhn-Tucker conditions Eq. KT; elastic predictor Eq. Tr_stress; closest-point projection
+// Eq. local_cpp (solved here in its scalar form, see return_map_*); implicit-function
+// tangent App. D; post-processor Eq. proj_lagrange / Eq. pk_stress with P_L and L_L applied
+// through first and second divided differences (Sec. 2.2.5); element residual and stiffness
+// Sec. 2.2.4 / Eq. Stiffness_mat.
+//
+// Thread layout: a CTA of 128 threads holds 16 elements x 8 Gauss points.  Phase 1: one
+// thread per Gauss point runs the constitutive update and stages the per-point tangent
+// A = dP/dF (rotated into the eigenbasis of C), the rotated shape-function gradients and the
+// rotated first Piola-Kirchhoff stress in shared memory.  Phase 2: one thread per
+// (element, node row a) contracts the eight Gauss points into the 3x24 row block of K^e
+// and the 3 entries of R^e, and scatters them through the element-to-block slot map.
+// Elements of one launch share no node (colouring), so the scatter needs no atomics; the
+// first colour that touches a block stores, later colours add (bit 31 of the slot).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hfe_internal.h"
+
+namespace hfe {
+namespace {
+
+constexpr double kSq23 = 0.81649658092772603273;   // sqrt(2/3)
+constexpr double kSq2 = 1.41421356237309504880;
+constexpr double kISq2 = 0.70710678118654752440;
+constexpr int kElemsPerCta = 16;
+constexpr int kThreads = 128;
+constexpr int kGpStride = 120;   // shared floats per Gauss point: A 84 (81 used), g 24, P 12 (9 used)
+
+// Mandel pair index helpers: p -> (i, j) and (i, j) -> p for the order 11,22,33,12,23,13.
+__host__ __device__ constexpr int pI(int p) { return p < 3 ? p : (p == 4 ? 1 : 0); }
+__host__ __device__ constexpr int pJ(int p) { return p < 3 ? p : (p == 3 ? 1 : 2); }
+__host__ __device__ constexpr int pidx(int i, int j) {
+  return i == j ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5));
+}
+
+template <typename R> struct Num;
+template <> struct Num<float> {
+  static constexpr float jac_eps2 = 1e-14f;   // Jacobi stop: off^2 <= eps2 * diag^2
+  static constexpr float dd1_series = 1e-3f;  // |x| below which log1p(x)/x uses its series
+  static constexpr float dd2_tau = 1e-2f;     // relative spread below which f2 uses f''(m)/2
+  __device__ static float log1p_(float x) { return log1pf(x); }
+  __device__ static float sqrt_(float x) { return sqrtf(x); }
+  __device__ static float rsqrt_(float x) { return rsqrtf(x); }
+};
+template <> struct Num<double> {
+  static constexpr double jac_eps2 = 1e-30;
+  static constexpr double dd1_series = 1e-4;
+  static constexpr double dd2_tau = 1e-5;
+  __device__ static double log1p_(double x) { return log1p(x); }
+  __device__ static double sqrt_(double x) { return sqrt(x); }
+  __device__ static double rsqrt_(double x) { return rsqrt(x); }
+};
+
+// ----------------------------------------------------------------------------------------
+// Symmetric 3x3 eigen-decomposition by the cyclic Jacobi method (Jacobi 1846, in the
+// rotation form of Rutishauser): each rotation annihilates one off-diagonal entry; the
+// off-diagonal norm falls quadratically.  Bounded to 10 sweeps.  Columns of V = eigenvectors.
+template <typename R>
+__device__ __forceinline__ void jacobi3(R A[3][3], R w[3], R V[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? R(1) : R(0);
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    R off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    R dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= Num<R>::jac_eps2 * dia || off == R(0)) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = (pq == 2) ? 1 : 0;
+      const int q = (pq == 0) ? 1 : 2;
+      const int r = 3 - p - q;
+      R apq = A[p][q];
+      if (apq != R(0)) {
+        R theta = (A[q][q] - A[p][p]) / (R(2) * apq);
+        R at = fabs(theta);
+        R t = (at > R(1e15)) ? R(0.5) / theta
+                             : (theta >= R(0) ? R(1) : R(-1)) / (at + Num<R>::sqrt_(theta * theta + R(1)));
+        R c = Num<R>::rsqrt_(t * t + R(1));
+        R s = t * c;
+        A[p][p] -= t * apq;
+        A[q][q] += t * apq;
+        A[p][q] = A[q][p] = R(0);
+        R arp = A[r][p], arq = A[r][q];
+        A[r][p] = A[p][r] = c * arp - s * arq;
+        A[r][q] = A[q][r] = s * arp + c * arq;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          R vp = V[k][p], vq = V[k][q];
+          V[k][p] = c * vp - s * vq;
+          V[k][q] = s * vp + c * vq;
+        }
+      }
+    }
+  }
+  w[0] = A[0][0];
+  w[1] = A[1][1];
+  w[2] = A[2][2];
+}
+
+template <typename R>
+__device__ __forceinline__ void swap_pair(R w[3], R V[3][3], int a, int b) {
+  if (w[b] < w[a]) {
+    R t = w[a]; w[a] = w[b]; w[b] = t;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { R v = V[k][a]; V[k][a] = V[k][b]; V[k][b] = v; }
+  }
+}
+
+// Mandel rotation: for a symmetric X, (Q^T X Q)_M = Rm X_M with Mandel vectors
+// (X11, X22, X33, sqrt2 X12, sqrt2 X23, sqrt2 X13).  Rm is orthogonal.
+template <typename R>
+__device__ __forceinline__ void mandel_rotation(const R Q[3][3], R Rm[6][6]) {
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const int a = pI(p), b = pJ(p);
+    const R so = (a != b) ? R(kSq2) : R(1);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int i = pI(q), j = pJ(q);
+      if (i == j) Rm[p][q] = so * Q[i][a] * Q[i][b];
+      else Rm[p][q] = so * R(kISq2) * (Q[i][a] * Q[j][b] + Q[j][a] * Q[i][b]);
+    }
+  }
+}
+
+// First divided difference of f(l) = 1/2 ln l at l_a = 1 + 2 e_a, l_b = 1 + 2 e_b, written as
+// log1p(x) / (2 l_b x) with x = (l_a - l_b) / l_b, which has no cancellation; the limit is
+// f'(l) = 1 / (2 l).
+template <typename R>
+__device__ __forceinline__ R dd1(R ea, R eb) {
+  R lb = R(1) + R(2) * eb;
+  R x = (R(2) * (ea - eb)) / lb;
+  R L;
+  if (fabs(x) < Num<R>::dd1_series) L = R(1) + x * (R(-0.5) + x * (R(1) / R(3) + x * R(-0.25)));
+  else L = Num<R>::log1p_(x) / x;
+  return L / (R(2) * lb);
+}
+
+// Second divided difference of f(l) = 1/2 ln l on the sorted multiset l_i <= l_j <= l_k:
+// (f[l_k, l_j] - f[l_j, l_i]) / (l_k - l_i); when the spread is below tau * l_j the value at
+// the mean m, f''(m)/2 = -1/(4 m^2), which is exact to second order in the spread.
+template <typename R>
+__device__ __forceinline__ R dd2(R ei, R ej, R ek, R f_kj, R f_ji) {
+  R li = R(1) + R(2) * ei, lj = R(1) + R(2) * ej;
+  R den = R(2) * (ek - ei);
+  if (den > Num<R>::dd2_tau * lj) return (f_kj - f_ji) / den;
+  R m = lj + (R(2) / R(3)) * (ei + ek - R(2) * ej);
+  (void)li;
+  return R(-0.25) / (m * m);
+}
+
+// ----------------------------------------------------------------------------------------
+// Hardening.  Plain FP64 evaluation (library pow / exp).
+__device__ __forceinline__ void sigy64(int type, const double* hp, double a, double& sy, double& dsy) {
+  if (type == HFE_HARDENING_SWIFT) {
+    double z = hp[1] + a;
+    sy = hp[0] * pow(z, hp[2]);
+    dsy = hp[2] * sy / z;
+  } else {
+    double e = exp(-hp[2] * a);
+    sy = hp[0] + hp[1] * (1.0 - e);
+    dsy = hp[1] * hp[2] * e;
+  }
+}
+
+// Mixed path: sigma_y(alpha_n + da) = sigma_y(alpha_n) + inc(da) with the FP64 cache
+// sigma_y(alpha_n) and the increment in FP32 (relative error ~1e-7 of the increment only).
+// Swift: inc = sy_n (exp(n log1p(da / (eps0 + alpha_n))) - 1); Voce: inc = A (1 - exp(-b da))
+// with A = sigma0 + Q - sy_n = Q exp(-b alpha_n).
+struct HardInc {
+  int type;
+  float p2, z_or_A, syn;   // Swift: n, eps0 + alpha_n, sy_n ; Voce: b, A, sy_n
+  __device__ __forceinline__ void eval(float da, float& inc, float& dsy) const {
+    if (type == HFE_HARDENING_SWIFT) {
+      float g = expm1f(p2 * log1pf(da / z_or_A));
+      inc = syn * g;
+      dsy = p2 * (syn + inc) / (z_or_A + da);
+    } else {
+      float em = expm1f(-p2 * da);
+      inc = -z_or_A * em;
+      dsy = p2 * z_or_A * (1.0f + em);
+    }
+  }
+};
+
+// FP64 reciprocal from the correctly rounded FP32 reciprocal and one Newton-Raphson step
+// for 1/d (x <- x (2 - d x)), relative error ~ (2^-24)^2.
+__device__ __forceinline__ double rcp64(double d) {
+  double r0 = (double)__frcp_rn((float)d);
+  double e = fma(-d, r0, 1.0);
+  return fma(r0, e, r0);
+}
+
+// Scalar form of the closest-point projection.  With isotropic E and a deviatoric Hill
+// tensor, E : H = 2 mu H, so the first row of Eq. local_cpp at the solution reads
+// (I + (2 mu dgamma / phi_y) H) : T = T_tr with phi(T) = phi_y = sqrt(2/3) sigma_y(alpha_n+1);
+// in the eigenbasis of H this is T_i = t_i / (1 + s h_i), s = 2 mu dgamma / phi_y, and the
+// remaining unknown dgamma solves r(dgamma) = sqrt(sum h_i T_i^2) - phi_y(dgamma) = 0, which
+// is strictly decreasing from r(0) = f_tr > 0; its root lies in (0, f_tr / (2 mu h_min)].
+// Safeguarded Newton: a step that leaves the bracket is replaced by bisection.
+struct RM {
+  double dgamma;   // plastic multiplier
+  double syn1;     // sigma_y(alpha_{n+1})
+  float dsy;       // d sigma_y / d alpha at alpha_{n+1}
+  int iters;
+  bool ok;
+};
+
+// Plain FP64 form (every operation in FP64).
+__device__ RM return_map_fp64(const double t[6], const double h[6], double mu, double hmin,
+                              int type, const double* hp, double alpn, double ftr, int maxit,
+                              double tol) {
+  RM out;
+  double dg = 0.0, lo = 0.0, hi = ftr / (2.0 * mu * hmin);
+  double sy = 0.0, dsy = 0.0;
+  int k = 0;
+  bool ok = false;
+  for (; k < maxit; ++k) {
+    sigy64(type, hp, alpn + kSq23 * dg, sy, dsy);
+    double phy = kSq23 * sy, dphy = (2.0 / 3.0) * dsy;
+    double s = 2.0 * mu * dg / phy;
+    double ds = 2.0 * mu * (phy - dg * dphy) / (phy * phy);
+    double phi2 = 0.0, acc = 0.0;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+      double d = 1.0 + s * h[i];
+      double Ti = t[i] / d;
+      double hT = h[i] * Ti;
+      phi2 += hT * Ti;
+      acc += hT * hT / d;
+    }
+    double phi = sqrt(phi2);
+    double r = phi - phy;
+    if (fabs(r) <= tol * phy) { ok = true; break; }
+    double dr = -(acc / phi) * ds - dphy;
+    if (r > 0.0) lo = dg; else hi = dg;
+    double dgn = dg - r / dr;
+    if (!(dgn > lo && dgn < hi)) dgn = 0.5 * (lo + hi);
+    if (fabs(dgn - dg) <= 1e-15 * dg) { dg = dgn; ok = true; break; }
+    dg = dgn;
+  }
+  sigy64(type, hp, alpn + kSq23 * dg, sy, dsy);
+  out.dgamma = dg;
+  out.syn1 = sy;
+  out.dsy = (float)dsy;
+  out.iters = k + 1;
+  out.ok = ok;
+  return out;
+}
+
+// Mixed form: the Newton iterations in FP32 to ~1e-6, then one FP64 Newton step on the yield
+// residual (written as phi^2 - phi_y^2 to avoid a square root) with FP64 reciprocals.
+__device__ RM return_map_mixed(const float t[6], const double* h, const float* hf, float mu,
+                               float hmin, const HardInc& inc, double syn64, float ftr, int maxit) {
+  RM out;
+  const float sq23 = (float)kSq23;
+  float dg = 0.0f, lo = 0.0f, hi = ftr / (2.0f * mu * hmin);
+  float dr = -1.0f;
+  int k = 0;
+  bool ok = false;
+  for (; k < maxit; ++k) {
+    float incv, dsy;
+    inc.eval(sq23 * dg, incv, dsy);
+    float phy = sq23 * (inc.syn + incv), dphy = (2.0f / 3.0f) * dsy;
+    float s = 2.0f * mu * dg / phy;
+    float ds = 2.0f * mu * (phy - dg * dphy) / (phy * phy);
+    float phi2 = 0.0f, acc = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+      float d = 1.0f + s * hf[i];
+      float Ti = t[i] / d;
+      float hT = hf[i] * Ti;
+      phi2 += hT * Ti;
+      acc += hT * hT / d;
+    }
+    float phi = sqrtf(phi2);
+    float r = phi - phy;
+    dr = -(acc / phi) * ds - dphy;
+    if (fabsf(r) <= 1e-6f * phy) { ok = true; break; }
+    if (r > 0.0f) lo = dg; else hi = dg;
+    float dgn = dg - r / dr;
+    if (!(dgn > lo && dgn < hi)) dgn = 0.5f * (lo + hi);
+    if (fabsf(dgn - dg) <= 1e-7f * dg) { dg = dgn; ok = true; break; }
+    dg = dgn;
+  }
+  // FP64 polish: one Newton step on rt(dgamma) = phi^2 - phi_y^2 (derivative 2 phi_y r').
+  double dg64 = (double)dg;
+  float incv, dsy;
+  inc.eval(sq23 * dg, incv, dsy);
+  double sy64 = syn64 + (double)incv;
+  double phy = kSq23 * sy64;
+  double s = 2.0 * (double)mu * dg64 * rcp64(phy);
+  double phi2 = 0.0;
+#pragma unroll
+  for (int i = 1; i < 6; ++i) {
+    double c = rcp64(fma(s, h[i], 1.0));
+    double Ti = (double)t[i] * c;
+    phi2 = fma(h[i] * Ti, Ti, phi2);
+  }
+  double rt = phi2 - phy * phy;
+  float corr = (float)rt / (2.0f * (float)phy * dr);
+  dg64 -= (double)corr;
+  if (dg64 < 0.0) dg64 = 0.0;
+  inc.eval(sq23 * (float)dg64, incv, dsy);
+  out.dgamma = dg64;
+  out.syn1 = syn64 + (double)incv;
+  out.dsy = dsy;
+  out.iters = k + 1;
+  out.ok = ok;
+  return out;
+}
+
+template <typename R> struct MatOf;
+template <> struct MatOf<float> { using T = MatRecF; };
+template <> struct MatOf<double> { using T = MatRec; };
+
+// ----------------------------------------------------------------------------------------
+template <typename R, bool TANGENT>
+__global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t cbeg, int64_t ccount) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sNode = reinterpret_cast<R*>(smem_raw);                     // [16][8][6]: dX(3), du(3)
+  R* sGp = sNode + kElemsPerCta * 8 * 6;                           // [128][kGpStride]
+
+  const int tid = threadIdx.x;
+  const int le = tid >> 3;
+  const int g = tid & 7;
+  const int64_t li = (int64_t)blockIdx.x * kElemsPerCta + le;
+  const bool valid = li < ccount;
+  const int e = valid ? a.elems[cbeg + li] : 0;
+  const unsigned lane = tid & 31;
+  const unsigned gmask = 0xffu << (lane & 24);
+
+  using MR = typename MatOf<R>::T;
+  const MatRec* mat64 = reinterpret_cast<const MatRec*>(a.mat);   // FP64 records (FP64 path)
+  const MR* matR = reinterpret_cast<const MR*>(a.mat);
+  const int mi = a.mat_per_element ? e : 0;
+
+  // ---- S1 gather: node g of element e; coordinates and displacements relative to node 0
+  // (differences taken in FP64, then rounded to R)
+  {
+    int node = valid ? a.conn[(int64_t)e * 8 + g] : 0;
+    double x0 = a.X[3 * (int64_t)node], x1 = a.X[3 * (int64_t)node + 1], x2 = a.X[3 * (int64_t)node + 2];
+    double u0 = a.u[3 * (int64_t)node], u1 = a.u[3 * (int64_t)node + 1], u2 = a.u[3 * (int64_t)node + 2];
+    const int src = lane & 24;
+    double bx0 = __shfl_sync(gmask, x0, src), bx1 = __shfl_sync(gmask, x1, src), bx2 = __shfl_sync(gmask, x2, src);
+    double bu0 = __shfl_sync(gmask, u0, src), bu1 = __shfl_sync(gmask, u1, src), bu2 = __shfl_sync(gmask, u2, src);
+    R* dst = sNode + (le * 8 + g) * 6;
+    dst[0] = (R)(x0 - bx0); dst[1] = (R)(x1 - bx1); dst[2] = (R)(x2 - bx2);
+    dst[3] = (R)(u0 - bu0); dst[4] = (R)(u1 - bu1); dst[5] = (R)(u2 - bu2);
+  }
+  __syncwarp(gmask);
+
+  const int64_t gpi = (int64_t)e * 8 + g;   // global Gauss-point index
+  int flag_detj = 0, flag_local = 0, flag_plastic = 0, local_iters = 0;
+
+  if (valid) {
+    const R* nd = sNode + le * 8 * 6;
+    // ---- S2 kinematics: dN/dxi at Gauss point g, J0 = dX/dxi, g_a = J0^{-T} dN_a
+    const R c3 = R(0.57735026918962576451);
+    const R xg = (g & 1) ? c3 : -c3, yg = (g & 2) ? c3 : -c3, zg = (g & 4) ? c3 : -c3;
+    R dN[8][3];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      const R xa = (n == 1 || n == 2 || n == 5 || n == 6) ? R(1) : R(-1);
+      const R ya = (n == 2 || n == 3 || n == 6 || n == 7) ? R(1) : R(-1);
+      const R za = (n >= 4) ? R(1) : R(-1);
+      const R fx = R(1) + xa * xg, fy = R(1) + ya * yg, fz = R(1) + za * zg;
+      dN[n][0] = R(0.125) * xa * fy * fz;
+      dN[n][1] = R(0.125) * ya * fx * fz;
+      dN[n][2] = R(0.125) * za * fx * fy;
+    }
+    R J0[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        R s = R(0);
+#pragma unroll
+        for (int n = 1; n < 8; ++n) s += nd[n * 6 + i] * dN[n][j];
+        J0[i][j] = s;
+      }
+    R c00 = J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1];
+    R c01 = J0[1][2] * J0[2][0] - J0[1][0] * J0[2][2];
+    R c02 = J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0];
+    R det0 = J0[0][0] * c00 + J0[0][1] * c01 + J0[0][2] * c02;
+    if (!(det0 > R(0))) flag_detj = 1;
+    R id = R(1) / det0;
+    R Ji[3][3];   // inverse of J0: Ji[j][k] = d xi_j / d X_k
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J0[0][2] * J0[2][1] - J0[0][1] * J0[2][2]) * id;
+    Ji[1][1] = (J0[0][0] * J0[2][2] - J0[0][2] * J0[2][0]) * id;
+    Ji[2][1] = (J0[0][1] * J0[2][0] - J0[0][0] * J0[2][1]) * id;
+    Ji[0][2] = (J0[0][1] * J0[1][2] - J0[0][2] * J0[1][1]) * id;
+    Ji[1][2] = (J0[0][2] * J0[1][0] - J0[0][0] * J0[1][2]) * id;
+    Ji[2][2] = (J0[0][0] * J0[1][1] - J0[0][1] * J0[1][0]) * id;
+    R gN[8][3];
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gN[n][k] = dN[n][0] * Ji[0][k] + dN[n][1] * Ji[1][k] + dN[n][2] * Ji[2][k];
+    // H = grad u = sum_a du_a (x) g_a ; F = I + H ; E = (H + H^T + H^T H) / 2
+    R H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        R s = R(0);
+#pragma unroll
+        for (int n = 1; n < 8; ++n) s += nd[n * 6 + 3 + i] * gN[n][j];
+        H[i][j] = s;
+      }
+    R F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? R(1) : R(0));
+    R Em[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        R s = H[i][j] + H[j][i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) s += H[k][i] * H[k][j];
+        Em[i][j] = Em[j][i] = R(0.5) * s;
+      }
+    R detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+             F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+    if (!(detF > R(0))) flag_detj = 1;
+
+    // ---- S3 log strain: E = Q diag(e) Q^T, C = I + 2E, eps = sum_a 1/2 log1p(2 e_a) n_a (x) n_a
+    R ev[3], Q[3][3];
+    jacobi3<R>(Em, ev, Q);
+    swap_pair<R>(ev, Q, 0, 1);
+    swap_pair<R>(ev, Q, 1, 2);
+    swap_pair<R>(ev, Q, 0, 1);
+    if (!(R(1) + R(2) * ev[0] > R(0))) flag_detj = 1;
+    R epa[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) epa[k] = R(0.5) * Num<R>::log1p_(R(2) * ev[k]);
+    R epsM[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const int i = pI(p), j = pJ(p);
+      R s = Q[i][0] * epa[0] * Q[j][0] + Q[i][1] * epa[1] * Q[j][1] + Q[i][2] * epa[2] * Q[j][2];
+      epsM[p] = (i == j) ? s : R(kSq2) * s;
+    }
+
+    // ---- S4 elastic predictor (Eq. Tr_stress) and return mapping in the Hill eigenbasis
+    const double* hist = a.hist;
+    const int64_t ng = a.n_gp;
+    double epn[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) epn[c] = hist[c * ng + gpi];
+    const double alpn = hist[6 * ng + gpi];
+    const MR& m = matR[mi];
+    const R lam = m.lam, mu = m.mu;
+    R ee[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) ee[p] = epsM[p] - (R)(p < 3 ? epn[p] : kSq2 * epn[p]);
+    R tre = ee[0] + ee[1] + ee[2];
+    R Ttr[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) Ttr[p] = R(2) * mu * ee[p] + (p < 3 ? lam * tre : R(0));
+    R t[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      R s = R(0);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) s += m.QH[i * 6 + j] * Ttr[i];
+      t[j] = s;
+    }
+    bool plastic = false;
+    RM rm;
+    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0;
+    double syn64;
+    if constexpr (sizeof(R) == 8) {
+      const MatRec& m64 = mat64[mi];
+      double dsy0;
+      sigy64(a.hardening, m64.hard, alpn, syn64, dsy0);
+      double phi2 = 0.0;
+#pragma unroll
+      for (int i = 1; i < 6; ++i) phi2 += m64.h[i] * (double)t[i] * (double)t[i];
+      double ftr = sqrt(phi2) - kSq23 * syn64;
+      if (ftr > 0.0) {
+        plastic = true;
+        double td[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) td[i] = (double)t[i];
+        rm = return_map_fp64(td, m64.h, m64.mu, m64.hmin, a.hardening, m64.hard, alpn, ftr, a.local_maxit,
+                             a.local_tol);
+      } else {
+        rm.syn1 = syn64;
+        rm.dsy = (float)dsy0;
+      }
+    } else {
+      syn64 = hist[7 * ng + gpi];
+      const MatRecF& mf = reinterpret_cast<const MatRecF*>(a.mat)[mi];
+      float phi2 = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 6; ++i) phi2 += mf.h[i] * (float)t[i] * (float)t[i];
+      float phyn2 = (float)((2.0 / 3.0) * syn64 * syn64);
+      bool pl;
+      if (phi2 > phyn2 * 1.00001f) pl = true;
+      else if (phi2 < phyn2 * 0.99999f) pl = false;
+      else {   // near the yield surface: decide in FP64
+        double p2 = 0.0;
+#pragma unroll
+        for (int i = 1; i < 6; ++i) p2 += mf.h64[i] * (double)t[i] * (double)t[i];
+        pl = p2 > (2.0 / 3.0) * syn64 * syn64;
+      }
+      HardInc inc;
+      inc.type = a.hardening;
+      inc.p2 = (float)mf.hard64[2];
+      inc.syn = (float)syn64;
+      if (a.hardening == HFE_HARDENING_SWIFT) inc.z_or_A = (float)(mf.hard64[1] + alpn);
+      else inc.z_or_A = (float)(mf.hard64[0] + mf.hard64[1] - syn64);
+      if (pl) {
+        plastic = true;
+        float ftr = sqrtf(phi2) - (float)kSq23 * inc.syn;
+        if (!(ftr > 0.0f)) ftr = 1e-30f;
+        float tf[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tf[i] = (float)t[i];
+        rm = return_map_mixed(tf, mf.h64, mf.h, mf.mu, mf.hmin, inc, syn64, ftr, a.local_maxit);
+      } else {
+        float incv, dsy;
+        inc.eval(0.0f, incv, dsy);
+        rm.syn1 = syn64;
+        rm.dsy = dsy;
+      }
+    }
+    flag_plastic = plastic ? 1 : 0;
+    flag_local = rm.ok ? 0 : 1;
+    local_iters = rm.iters;
+
+    // stress T and plastic update in the Hill eigenbasis, then back to Mandel components
+    R Teig[6];
+    R s_pl = R(0), phy = R(1);
+    if (plastic) {
+      phy = (R)(kSq23 * rm.syn1);
+      s_pl = R(2) * mu * (R)rm.dgamma / phy;
+    }
+    Teig[0] = t[0];
+#pragma unroll
+    for (int i = 1; i < 6; ++i) Teig[i] = plastic ? t[i] / (R(1) + s_pl * (R)m.h[i]) : t[i];
+    R TM[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      R s = R(0);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) s += m.QH[i * 6 + j] * Teig[j];
+      TM[i] = s;
+    }
+    {
+      double* ht = a.hist_trial;
+      if (plastic) {
+        R neig[6];
+        neig[0] = R(0);
+#pragma unroll
+        for (int i = 1; i < 6; ++i) neig[i] = (R)m.h[i] * Teig[i] / phy;
+        const R dgR = (R)rm.dgamma;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          R s = R(0);
+#pragma unroll
+          for (int j = 1; j < 6; ++j) s += m.QH[p * 6 + j] * neig[j];
+          double inc_t = (double)(dgR * s) * (p < 3 ? 1.0 : kISq2);
+          ht[p * ng + gpi] = epn[p] + inc_t;
+        }
+        ht[6 * ng + gpi] = alpn + kSq23 * rm.dgamma;
+      } else {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) ht[p * ng + gpi] = epn[p];
+        ht[6 * ng + gpi] = alpn;
+      }
+      ht[7 * ng + gpi] = rm.syn1;
+    }
+
+    // ---- S6 post-processor in the eigenbasis of C: That = Q^T T Q, Shat_ab = 2 f1_ab That_ab
+    R Tt[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int p = pidx(i, j);
+        Tt[i][j] = (i == j) ? TM[p] : R(kISq2) * TM[p];
+      }
+    R That[3][3];
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+      for (int bb = aa; bb < 3; ++bb) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          R qi = Q[i][aa];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) s += qi * Tt[i][j] * Q[j][bb];
+        }
+        That[aa][bb] = That[bb][aa] = s;
+      }
+    R f1[3][3];
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+      for (int bb = aa; bb < 3; ++bb) {
+        R v = (aa == bb) ? R(0.5) / (R(1) + R(2) * ev[aa]) : dd1<R>(ev[bb], ev[aa]);
+        f1[aa][bb] = f1[bb][aa] = v;
+      }
+    R Sh[3][3];
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) Sh[aa][bb] = R(2) * f1[aa][bb] * That[aa][bb];
+    // Ftilde = F Q ; Ptilde = Ftilde Shat ; gtilde_a = Q^T g_a ; weight w det J0 (w = 1)
+    R Ft[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Ft[i][j] = F[i][0] * Q[0][j] + F[i][1] * Q[1][j] + F[i][2] * Q[2][j];
+    R* gp = sGp + (size_t)tid * kGpStride;
+    const R wd = det0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gp[84 + n * 3 + j] = gN[n][0] * Q[0][j] + gN[n][1] * Q[1][j] + gN[n][2] * Q[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        gp[108 + i * 3 + j] = wd * (Ft[i][0] * Sh[0][j] + Ft[i][1] * Sh[1][j] + Ft[i][2] * Sh[2][j]);
+    if (a.sigma != nullptr) {   // Cauchy stress sigma = P F^T / J, P = Ftilde Shat Q^T
+      R P[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          R s = R(0);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) s += (Ft[i][0] * Sh[0][j] + Ft[i][1] * Sh[1][j] + Ft[i][2] * Sh[2][j]) * Q[k][j];
+          P[i][k] = s;
+        }
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const int i = pI(p), j = pJ(p);
+        R s = P[i][0] * F[j][0] + P[i][1] * F[j][1] + P[i][2] * F[j][2];
+        a.sigma[gpi * 6 + p] = (double)(s / detF);
+      }
+    }
+
+    if constexpr (TANGENT) {
+      // ---- S5 algorithmic tangent D = dT/deps (Mandel), rotated into the eigenbasis of C
+      R Dh[6][6];
+      R Rq[6][6];
+      mandel_rotation<R>(Q, Rq);
+      if (!plastic) {
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) Dh[p][q] = (p == q ? R(2) * mu : R(0)) + (p < 3 && q < 3 ? lam : R(0));
+      } else {
+        // implicit function theorem on Eq. local_cpp (App. D) in the Hill eigenbasis:
+        // Xi^-1 = E^-1 + dgamma (H - N (x) N) / phi, D = Xi - (Xi N)(Xi N)^T / (N Xi N + 2/3 H')
+        const R dgR = (R)rm.dgamma;
+        const R cph = dgR / phy;
+        R nv[6], Dd[6], pv[6];
+        R npn = R(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const R hi = (R)m.h[i];
+          nv[i] = (i == 0) ? R(0) : hi * Teig[i] / phy;
+          const R ei = (i == 0) ? (R)m.kap3 : R(2) * mu;
+          Dd[i] = R(1) / ei + cph * hi;
+          pv[i] = nv[i] / Dd[i];
+          npn += nv[i] * pv[i];
+        }
+        const R kap = cph / (R(1) - cph * npn);
+        const R qf = R(1) + kap * npn;
+        R qv[6];
+        R nqn = R(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { qv[i] = pv[i] * qf; nqn += nv[i] * qv[i]; }
+        const R beta = nqn + (R(2) / R(3)) * (R)rm.dsy;
+        // W = Rq QH ; Dh = W diag(1/Dd) W^T + kap (W p)(W p)^T - (W q)(W q)^T / beta
+        R W[6][6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            R s = R(0);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) s += Rq[p][i] * m.QH[i * 6 + j];
+            W[p][j] = s;
+          }
+        R Wp[6], Wq[6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          R s1 = R(0), s2 = R(0);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) { s1 += W[p][j] * pv[j]; s2 += W[p][j] * qv[j]; }
+          Wp[p] = s1;
+          Wq[p] = s2;
+        }
+        const R ib = R(1) / beta;
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+#pragma unroll
+          for (int q = p; q < 6; ++q) {
+            R s = R(0);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) s += W[p][j] * W[q][j] / Dd[j];
+            s += kap * Wp[p] * Wp[q] - ib * Wq[p] * Wq[q];
+            Dh[p][q] = Dh[q][p] = s;
+          }
+      }
+      // material tangent in the eigenbasis: Chat = 4 diag(f1) Dh diag(f1) + 4 D^2eps[That, .]
+      R f1M[6];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) f1M[p] = f1[pI(p)][pJ(p)];
+      // second divided differences on the sorted eigenvalues (10 distinct values)
+      R f2[3][3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j)
+#pragma unroll
+          for (int k = j; k < 3; ++k) {
+            R v = dd2<R>(ev[i], ev[j], ev[k], f1[k][j], f1[j][i]);
+            f2[i][j][k] = f2[i][k][j] = f2[j][i][k] = f2[j][k][i] = f2[k][i][j] = f2[k][j][i] = v;
+          }
+      R Ct[6][6];   // tensor-component matrix of Chat (no Mandel factors)
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const int aa = pI(p), bb = pJ(p);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const int cc = pI(q), dd = pJ(q);
+          // G(Y)_ab = 4 sum_k f2(a,k,b) (That_ak Y_kb + Y_ak That_kb) for the Mandel unit Y_q
+          R gsum = R(0);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            R ykb = ((k == cc && bb == dd) || (k == dd && bb == cc)) ? R(1) : R(0);
+            R yak = ((aa == cc && k == dd) || (aa == dd && k == cc)) ? R(1) : R(0);
+            if (cc != dd) { ykb *= R(kISq2); yak *= R(kISq2); }
+            gsum += f2[aa][k][bb] * (That[aa][k] * ykb + yak * That[k][bb]);
+          }
+          R cm = R(4) * f1M[p] * Dh[p][q] * f1M[q] + R(4) * gsum * (aa == bb ? R(1) : R(kSq2));
+          Ct[p][q] = cm * (aa == bb ? R(1) : R(kISq2)) * (cc == dd ? R(1) : R(kISq2));
+        }
+      }
+      // A_iJkL = delta_ik Shat_JL + sum_IK Ft_iI Chat_IJKL Ft_kK, scaled by w det J0
+      R Xt[3][3][6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J)
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            Xt[i][J][q] = Ft[i][0] * Ct[pidx(0, J)][q] + Ft[i][1] * Ct[pidx(1, J)][q] + Ft[i][2] * Ct[pidx(2, J)][q];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int J = 0; J < 3; ++J)
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int L = 0; L < 3; ++L) {
+              R s = Xt[i][J][pidx(0, L)] * Ft[k][0] + Xt[i][J][pidx(1, L)] * Ft[k][1] + Xt[i][J][pidx(2, L)] * Ft[k][2];
+              if (i == k) s += Sh[J][L];
+              gp[(i * 3 + J) * 9 + k * 3 + L] = wd * s;
+            }
+    }
+  }
+
+  // ---- status counters (one atomic per warp and counter)
+  {
+    const unsigned full = 0xffffffffu;
+    unsigned bd = __ballot_sync(full, flag_detj), bl = __ballot_sync(full, flag_local);
+    unsigned bp = __ballot_sync(full, flag_plastic);
+    int mx = local_iters;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(full, mx, o));
+    if (lane == 0) {
+      if (bd) atomicAdd(&a.status->detj, __popc(bd));
+      if (bl) atomicAdd(&a.status->local_fail, __popc(bl));
+      if (bp) atomicAdd(&a.status->plastic, __popc(bp));
+      if (mx > 0) atomicMax(&a.status->max_local_iters, mx);
+    }
+  }
+  __syncthreads();
+
+  // ---- S7/S8 phase 2: thread (element le, node row a = g)
+  if (!valid) return;
+  const R* G = sGp + (size_t)(le * 8) * kGpStride;
+  R Ra[3] = {R(0), R(0), R(0)};
+  const int arow = g;
+  if constexpr (TANGENT) {
+    R Kr[8][9];
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) Kr[b][c] = R(0);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const R* A = G + q * kGpStride;
+      const R* gt = A + 84;
+      const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
+      R U[3][3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int L = 0; L < 3; ++L)
+            U[i][k][L] = ga0 * A[(i * 3 + 0) * 9 + k * 3 + L] + ga1 * A[(i * 3 + 1) * 9 + k * 3 + L] +
+                         ga2 * A[(i * 3 + 2) * 9 + k * 3 + L];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const R gb0 = gt[b * 3], gb1 = gt[b * 3 + 1], gb2 = gt[b * 3 + 2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Kr[b][i * 3 + k] += U[i][k][0] * gb0 + U[i][k][1] * gb1 + U[i][k][2] * gb2;
+      }
+      const R* P = A + 108;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
+    }
+    R* Kv = reinterpret_cast<R*>(a.K);
+    const int32_t* sl = a.slot + (int64_t)e * 64 + arow * 8;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int32_t sv = sl[b];
+      const bool store = sv < 0;
+      R* dst = Kv + (int64_t)(sv & 0x7fffffff) * 9;
+      if (store) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) dst[c] = Kr[b][c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) dst[c] += Kr[b][c];
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const R* A = G + q * kGpStride;
+      const R* gt = A + 84;
+      const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
+      const R* P = A + 108;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
+    }
+  }
+  {
+    const int node = a.conn[(int64_t)e * 8 + arow];
+    const bool store = a.slot[(int64_t)e * 64 + arow * 9] < 0;   // diagonal block (a, a)
+    double* Rg = a.R + 3 * (int64_t)node;
+    if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
+      atomicAdd(&a.status->nonfinite, 1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double v = (double)Ra[i];
+      if (store) Rg[i] = v - (a.f_ext ? a.load * a.f_ext[3 * (int64_t)node + i] : 0.0);
+      else Rg[i] += v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Material set-up (one thread per material): Lame constants, the Hill tensor in Mandel
+// notation from (F, G, H, L, M, N) — phi^2 = (2/3)[F (T22-T33)^2 + G (T33-T11)^2 +
+// H (T11-T22)^2 + 2L T23^2 + 2M T13^2 + 2N T12^2] in the material frame (App. A.1 written in
+// the Hill constants) — rotated by Theta (X -> Theta^T X Theta), and its eigen-decomposition
+// by cyclic Jacobi in FP64.  The hydrostatic direction is pinned as eigenvector 0.
+__global__ void material_setup_kernel(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,
+                                      MatRecF* outf, int* bad) {
+  int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n_mat) return;
+  const double* th = theta + id * 11;
+  const double E = th[0], nu = th[1];
+  const double Fh = th[2], Gh = th[3], Hh = th[4], Lh = th[5], Mh = th[6], Nh = th[7];
+  MatRec r;
+  r.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  r.mu = E / (2.0 * (1.0 + nu));
+  r.kap3 = 3.0 * r.lam + 2.0 * r.mu;
+  r.hard[0] = th[8];
+  r.hard[1] = th[9];
+  r.hard[2] = th[10];
+  r.pad = 0.0;
+  double Hl[6][6] = {};
+  const double c = 2.0 / 3.0;
+  Hl[0][0] = c * (Gh + Hh); Hl[1][1] = c * (Fh + Hh); Hl[2][2] = c * (Fh + Gh);
+  Hl[0][1] = Hl[1][0] = -c * Hh;
+  Hl[1][2] = Hl[2][1] = -c * Fh;
+  Hl[0][2] = Hl[2][0] = -c * Gh;
+  Hl[3][3] = c * Nh; Hl[4][4] = c * Lh; Hl[5][5] = c * Mh;
+  double Hg[6][6];
+  if (Theta != nullptr) {
+    double Th[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Th[i][j] = Theta[id * 9 + i * 3 + j];
+    double Rt[6][6];
+    mandel_rotation<double>(Th, Rt);   // local Mandel = Rt * global Mandel
+    double tmp[6][6];
+    for (int p = 0; p < 6; ++p)
+      for (int q = 0; q < 6; ++q) {
+        double s = 0.0;
+        for (int k = 0; k < 6; ++k) s += Hl[p][k] * Rt[k][q];
+        tmp[p][q] = s;
+      }
+    for (int p = 0; p < 6; ++p)
+      for (int q = 0; q < 6; ++q) {
+        double s = 0.0;
+        for (int k = 0; k < 6; ++k) s += Rt[k][p] * tmp[k][q];
+        Hg[p][q] = s;
+      }
+  } else {
+    for (int p = 0; p < 6; ++p)
+      for (int q = 0; q < 6; ++q) Hg[p][q] = Hl[p][q];
+  }
+  // shift the hydrostatic eigenvalue 0 to -1 so that it is isolated: A = Hg - v0 v0^T
+  const double v0 = 0.57735026918962576451;
+  double A[6][6], V[6][6];
+  for (int p = 0; p < 6; ++p)
+    for (int q = 0; q < 6; ++q) {
+      A[p][q] = Hg[p][q] - ((p < 3 && q < 3) ? v0 * v0 : 0.0);
+      V[p][q] = (p == q) ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int p = 0; p < 6; ++p) {
+      dia += A[p][p] * A[p][p];
+      for (int q = p + 1; q < 6; ++q) off += A[p][q] * A[p][q];
+    }
+    if (off <= 1e-32 * dia) break;
+    for (int p = 0; p < 5; ++p)
+      for (int q = p + 1; q < 6; ++q) {
+        double apq = A[p][q];
+        if (apq == 0.0) continue;
+        double thv = (A[q][q] - A[p][p]) / (2.0 * apq);
+        double t = (fabs(thv) > 1e15) ? 0.5 / thv : (thv >= 0 ? 1.0 : -1.0) / (fabs(thv) + sqrt(thv * thv + 1.0));
+        double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+        A[p][p] -= t * apq;
+        A[q][q] += t * apq;
+        A[p][q] = A[q][p] = 0.0;
+        for (int k = 0; k < 6; ++k) {
+          if (k == p || k == q) continue;
+          double akp = A[k][p], akq = A[k][q];
+          A[k][p] = A[p][k] = cs * akp - sn * akq;
+          A[k][q] = A[q][k] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < 6; ++k) {
+          double vp = V[k][p], vq = V[k][q];
+          V[k][p] = cs * vp - sn * vq;
+          V[k][q] = sn * vp + cs * vq;
+        }
+      }
+  }
+  int i0 = 0;
+  for (int j = 1; j < 6; ++j)
+    if (fabs(A[j][j] + 1.0) < fabs(A[i0][i0] + 1.0)) i0 = j;
+  // order: hydrostatic first, then the others in their Jacobi order
+  int ord[6];
+  ord[0] = i0;
+  for (int j = 0, k = 1; j < 6; ++j)
+    if (j != i0) ord[k++] = j;
+  double hmin = 1e300;
+  for (int k = 0; k < 6; ++k) {
+    int j = ord[k];
+    double hv = (k == 0) ? 0.0 : A[j][j];
+    r.h[k] = hv;
+    if (k > 0 && hv < hmin) hmin = hv;
+    for (int i = 0; i < 6; ++i) r.QH[i * 6 + k] = V[i][j];
+  }
+  // exact hydrostatic vector, other columns re-orthogonalised against it
+  for (int i = 0; i < 6; ++i) r.QH[i * 6 + 0] = (i < 3) ? v0 : 0.0;
+  for (int k = 1; k < 6; ++k) {
+    double d = v0 * (r.QH[0 * 6 + k] + r.QH[1 * 6 + k] + r.QH[2 * 6 + k]);
+    double nn = 0.0;
+    for (int i = 0; i < 6; ++i) {
+      r.QH[i * 6 + k] -= d * ((i < 3) ? v0 : 0.0);
+      nn += r.QH[i * 6 + k] * r.QH[i * 6 + k];
+    }
+    double inv = 1.0 / sqrt(nn);
+    for (int i = 0; i < 6; ++i) r.QH[i * 6 + k] *= inv;
+  }
+  r.hmin = hmin;
+  if (!(hmin > 0.0) || !(r.mu > 0.0) || !(r.kap3 > 0.0) || !isfinite(hmin)) atomicAdd(bad, 1);
+  out[id] = r;
+  if (outf != nullptr) {
+    MatRecF f;
+    for (int k = 0; k < 6; ++k) f.h64[k] = r.h[k];
+    f.mu64 = r.mu;
+    for (int k = 0; k < 3; ++k) f.hard64[k] = r.hard[k];
+    f.lam = (float)r.lam; f.mu = (float)r.mu; f.kap3 = (float)r.kap3;
+    for (int k = 0; k < 6; ++k) f.h[k] = (float)r.h[k];
+    f.hmin = (float)r.hmin;
+    for (int k = 0; k < 36; ++k) f.QH[k] = (float)r.QH[k];
+    for (int k = 0; k < 3; ++k) f.hard[k] = (float)r.hard[k];
+    f.pad = 0.0f;
+    outf[id] = f;
+  }
+}
+
+// sigma_y(alpha) cache (history component 7) recomputed in FP64 from alpha (component 6).
+__global__ void sigma_cache_kernel(double* hist, const MatRec* mat, int per_element, int type, int64_t n_gp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_gp) return;
+  const MatRec& m = mat[per_element ? (i >> 3) : 0];
+  double sy, dsy;
+  sigy64(type, m.hard, hist[6 * n_gp + i], sy, dsy);
+  hist[7 * n_gp + i] = sy;
+}
+
+}  // namespace
+
+void launch_material_setup(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,
+                                MatRecF* outf, int* bad, cudaStream_t s) {
+  int threads = 64;
+  int blocks = (int)((n_mat + threads - 1) / threads);
+  material_setup_kernel<<<blocks, threads, 0, s>>>(theta, Theta, n_mat, out, outf, bad);
+}
+
+void launch_sigma_cache(double* hist, const void* mat, int mat_per_element, int hardening, int64_t n_gp,
+                        cudaStream_t s) {
+  int threads = 256;
+  int64_t blocks = (n_gp + threads - 1) / threads;
+  sigma_cache_kernel<<<(unsigned)blocks, threads, 0, s>>>(hist, reinterpret_cast<const MatRec*>(mat),
+                                                          mat_per_element, hardening, n_gp);
+}
+
+template <typename R, bool TANGENT>
+static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cudaStream_t s) {
+  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kThreads * kGpStride);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_done = true;
+  }
+  for (size_t c = 0; c + 1 < off.size(); ++c) {
+    int64_t cnt = off[c + 1] - off[c];
+    if (cnt <= 0) continue;
+    unsigned blocks = (unsigned)((cnt + kElemsPerCta - 1) / kElemsPerCta);
+    gp_sweep_kernel<R, TANGENT><<<blocks, kThreads, smem, s>>>(a, off[c], cnt);
+  }
+}
+
+void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
+                     cudaStream_t s) {
+  if (fp64) {
+    if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true>(a, color_off, s);
+    else launch_typed<double, false>(a, color_off, s);
+  } else {
+    if (mode == HFE_SWEEP_TANGENT) launch_typed<float, true>(a, color_off, s);
+    else launch_typed<float, false>(a, color_off, s);
+  }
+}
+
+}  // namespace hfe

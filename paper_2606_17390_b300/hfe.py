@@ -1,0 +1,276 @@
+"""Thin Python binding of the C ABI in include/hfe.h (argument marshalling only).
+
+Every computation runs in ``libhfe.so`` (hand-written CUDA for sm_103a).  There is no CPU
+fallback: if the library is missing or no CUDA device is present the calls raise.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they must be contiguous
+and of the documented dtype (float64 for reals, int32 for ``conn``, int64 for dofs).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["HfeError", "Solver", "lib", "LIB_PATH", "STATUS", "material_arrays"]
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhfe.so")
+
+STATUS = {0: "HFE_OK", -1: "HFE_EINVAL", -2: "HFE_ENOMEM", -3: "HFE_ECUDA", -4: "HFE_EDETJ",
+          1: "HFE_ENEWTON", 2: "HFE_ELOCAL", 3: "HFE_EPCG", 4: "HFE_ENONFINITE"}
+PRECISION = {"fp64": 0, "mixed": 1}
+HARDENING = {"swift": 0, "voce": 1}
+SWEEP_RESIDUAL, SWEEP_TANGENT = 0, 1
+
+
+class HfeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_el", C.c_int64), ("X", C.c_void_p), ("conn", C.c_void_p)]
+
+
+class _BC(C.Structure):
+    _fields_ = [("n_fixed", C.c_int64), ("dof", C.c_void_p), ("value", C.c_void_p), ("f_ext", C.c_void_p)]
+
+
+class _Material(C.Structure):
+    _fields_ = [("hardening", C.c_int), ("n_mat", C.c_int64), ("theta", C.c_void_p), ("Theta", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("newton_rtol", C.c_double), ("newton_atol", C.c_double),
+                ("newton_maxit", C.c_int), ("newton_stag_tol", C.c_double), ("pcg_rtol", C.c_double),
+                ("pcg_maxit", C.c_int), ("pcg_check_every", C.c_int), ("precond", C.c_int),
+                ("local_maxit", C.c_int), ("local_tol", C.c_double), ("ckpt_every", C.c_int),
+                ("predictor", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int64), ("pcg_iters", C.c_int64), ("sweeps", C.c_int64),
+                ("plastic_gps", C.c_int64), ("local_fail", C.c_int64), ("max_local_iters", C.c_int32),
+                ("steps_done", C.c_int32), ("last_residual", C.c_double), ("sweep_ms", C.c_double),
+                ("solve_ms", C.c_double), ("total_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_el", C.c_int64), ("n_dof", C.c_int64), ("n_gp", C.c_int64),
+                ("n_blocks", C.c_int64), ("n_fixed", C.c_int64), ("n_colors", C.c_int32),
+                ("precision", C.c_int32), ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def lib():
+    """Load libhfe.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2606_17390_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    L.hfe_default_options.argtypes = [C.POINTER(Options), i32]
+    L.hfe_default_options.restype = None
+    L.hfe_create.argtypes = [C.POINTER(_Mesh), C.POINTER(_BC), C.POINTER(_Material), C.POINTER(Options), vp,
+                             C.POINTER(vp)]
+    L.hfe_destroy.argtypes = [vp]
+    L.hfe_destroy.restype = None
+    L.hfe_last_error.argtypes = [vp]
+    L.hfe_last_error.restype = C.c_char_p
+    L.hfe_get_info.argtypes = [vp, C.POINTER(Info)]
+    L.hfe_set_material.argtypes = [vp, C.POINTER(_Material)]
+    L.hfe_set_state.argtypes = [vp, vp, vp]
+    L.hfe_get_state.argtypes = [vp, vp, vp]
+    L.hfe_gp_sweep.argtypes = [vp, vp, dbl, i32, vp, vp, C.POINTER(Stats)]
+    L.hfe_get_bsr.argtypes = [vp, vp, vp, vp]
+    L.hfe_spmv.argtypes = [vp, vp, vp]
+    L.hfe_solve.argtypes = [vp, vp, vp, C.POINTER(Stats)]
+    L.hfe_forward.argtypes = [vp, i32, vp, vp, vp, vp, C.POINTER(Stats)]
+    L.hfe_adjoint.argtypes = [vp, i32, vp, vp, dbl, vp, vp, C.POINTER(Stats)]
+    for name in ("hfe_create", "hfe_get_info", "hfe_set_material", "hfe_set_state", "hfe_get_state",
+                 "hfe_gp_sweep", "hfe_get_bsr", "hfe_spmv", "hfe_solve", "hfe_forward", "hfe_adjoint"):
+        getattr(L, name).restype = i32
+    _LIB = L
+    return L
+
+
+def _ptr(x, dtype=None):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {x.dtype}")
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def material_arrays(theta, Theta=None):
+    th = np.ascontiguousarray(np.atleast_2d(np.asarray(theta, dtype=np.float64)))
+    Th = None
+    if Theta is not None:
+        Th = np.asarray(Theta, dtype=np.float64)
+        if Th.ndim == 2:
+            Th = Th[None]
+        if Th.shape[0] == 1 and th.shape[0] > 1:
+            Th = np.repeat(Th, th.shape[0], axis=0)
+        Th = np.ascontiguousarray(Th.reshape(-1, 9))
+        if np.allclose(Th, np.eye(3).ravel()[None]):
+            Th = None
+    return th, Th
+
+
+class Solver:
+    """One handle of the library: mesh, Dirichlet data, material and workspaces on the GPU."""
+
+    def __init__(self, X, conn, fixed_dof, fixed_val, theta, hardening, Theta=None, precision="fp64",
+                 f_ext=None, stream=None, **options):
+        L = lib()
+        self._keep = []
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        dof = np.ascontiguousarray(fixed_dof, dtype=np.int64)
+        val = np.ascontiguousarray(fixed_val, dtype=np.float64)
+        th, Th = material_arrays(theta, Theta)
+        self.n_nodes, self.n_el = X.shape[0], conn.shape[0]
+        self.n_dof, self.n_gp = 3 * self.n_nodes, 8 * self.n_el
+        self.hardening = hardening
+        self.n_mat = th.shape[0]
+        mesh = _Mesh(self.n_nodes, self.n_el, _ptr(X), _ptr(conn))
+        fe = None if f_ext is None else np.ascontiguousarray(f_ext, dtype=np.float64)
+        bc = _BC(dof.size, _ptr(dof), _ptr(val), _ptr(fe))
+        mat = _Material(HARDENING[hardening], th.shape[0], _ptr(th), _ptr(Th))
+        opt = Options()
+        L.hfe_default_options(C.byref(opt), PRECISION[precision])
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise KeyError(k)
+            setattr(opt, k, v)
+        self.options = opt
+        self.precision = precision
+        h = C.c_void_p()
+        st = L.hfe_create(C.byref(mesh), C.byref(bc), C.byref(mat), C.byref(opt), stream, C.byref(h))
+        self._h = h
+        if st != 0:
+            msg = L.hfe_last_error(h).decode() if h.value else "hfe_create failed"
+            self.close()
+            raise HfeError(st, msg)
+
+    # -- helpers
+    def _check(self, st):
+        if st != 0:
+            raise HfeError(st, lib().hfe_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().hfe_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        inf = Info()
+        self._check(lib().hfe_get_info(self._h, C.byref(inf)))
+        return inf.as_dict()
+
+    # -- state and material
+    def set_material(self, theta, Theta=None):
+        th, Th = material_arrays(theta, Theta)
+        mat = _Material(HARDENING[self.hardening], th.shape[0], _ptr(th), _ptr(Th))
+        self._check(lib().hfe_set_material(self._h, C.byref(mat)))
+
+    def set_state(self, u=None, hist=None):
+        self._check(lib().hfe_set_state(self._h, _ptr(u), _ptr(hist)))
+
+    def get_state(self):
+        u = np.empty(self.n_dof)
+        hist = np.empty((7, self.n_gp))
+        self._check(lib().hfe_get_state(self._h, _ptr(u), _ptr(hist)))
+        return u, hist
+
+    # -- hot path
+    def sweep(self, u, load=1.0, tangent=True, R_out=None, hist_out=None, stats=True):
+        """One Gauss-point sweep; returns (R, hist_trial, stats) with host arrays unless the
+        caller passes its own (host or device) output buffers."""
+        R = np.empty(self.n_dof) if R_out is None else R_out
+        H = hist_out
+        s = Stats() if stats else None
+        st = lib().hfe_gp_sweep(self._h, _ptr(u), float(load), SWEEP_TANGENT if tangent else SWEEP_RESIDUAL,
+                                _ptr(R), _ptr(H), C.byref(s) if s is not None else None)
+        self._check(st)
+        return R, H, (s.as_dict() if s is not None else None)
+
+    def get_bsr(self, values=True):
+        inf = self.info()
+        rowptr = np.empty(self.n_nodes + 1, dtype=np.int64)
+        cols = np.empty(inf["n_blocks"], dtype=np.int32)
+        vals = np.empty(9 * inf["n_blocks"]) if values else None
+        self._check(lib().hfe_get_bsr(self._h, _ptr(rowptr), _ptr(cols), _ptr(vals)))
+        return rowptr, cols, (vals.reshape(-1, 3, 3) if values else None)
+
+    def spmv(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x
+        y = np.empty(self.n_dof) if isinstance(x, np.ndarray) else x.new_empty(self.n_dof)
+        self._check(lib().hfe_spmv(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def solve(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b
+        x = np.empty(self.n_dof) if isinstance(b, np.ndarray) else b.new_empty(self.n_dof)
+        s = Stats()
+        self._check(lib().hfe_solve(self._h, _ptr(b), _ptr(x), C.byref(s)))
+        return x, s.as_dict()
+
+    def forward(self, t, u_out=None, sigma_out=None, hist_out=None, want_u=True):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        if u_out is None and want_u:
+            u_out = np.empty((t.size, self.n_dof))
+        s = Stats()
+        self._check(lib().hfe_forward(self._h, int(t.size), _ptr(t), _ptr(u_out), _ptr(sigma_out),
+                                      _ptr(hist_out), C.byref(s)))
+        return u_out, s.as_dict()
+
+    def adjoint(self, t, u_target, w=1.0, grad_out=None):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        if grad_out is None:
+            grad_out = np.empty((self.n_mat, 11))
+        J = C.c_double()
+        s = Stats()
+        self._check(lib().hfe_adjoint(self._h, int(t.size), _ptr(t), _ptr(u_target), float(w), C.byref(J),
+                                      _ptr(grad_out), C.byref(s)))
+        return J.value, grad_out, s.as_dict()
+
+
+def from_inputs(mesh, bc, mat, precision="fp64", theta=None, **options):
+    """Solver for the dataclasses of paper_2606_17390_b300.inputs."""
+    th = mat.theta_vector() if theta is None else theta
+    return Solver(mesh.X, mesh.conn, bc.dof, bc.value, th, mat.hardening, mat.Theta, precision=precision,
+                  **options)

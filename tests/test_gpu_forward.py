@@ -1,0 +1,99 @@
+"""Full forward solves on the GPU (load steps, global Newton, block-CSR assembly, PCG) vs the
+FP64 oracle on the same seeded inputs.  Tolerances: FP64 path 1e-10 relative in displacement
+(max over dofs / max |u| per step); mixed path 1e-5 in displacement and 1e-4 in von Mises
+stress (max |dvm| / max vm)."""
+import numpy as np
+import pytest
+
+from oracle import material, solver
+from paper_2606_17390_b300 import hfe, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def config0_oracle():
+    mesh, bc, mat, ts = inputs.config0_problem()
+    prob = solver.from_inputs(mesh, bc, mat)
+    us, hs, infos = solver.forward(prob, ts, rtol=1e-12)
+    return mesh, bc, mat, ts, us, hs, infos
+
+
+@pytest.fixture(scope="module")
+def plate_oracle():
+    mesh, bc, mat, ts = inputs.config1_problem(nx=24, ny=12, nz=2, n_steps=6)
+    prob = solver.from_inputs(mesh, bc, mat)
+    us, hs, infos = solver.forward(prob, ts, rtol=1e-12)
+    return mesh, bc, mat, ts, us, hs, infos
+
+
+def _per_step_rel(u, uo):
+    return max(np.abs(u[n] - uo[n]).max() / np.abs(uo[n]).max() for n in range(len(uo)))
+
+
+def _vm_rel(sig, sig_o):
+    vm = material.von_mises(sig.reshape(-1, 3, 3) if sig.ndim == 3 else _sym(sig))
+    vmo = material.von_mises(sig_o.reshape(-1, 3, 3))
+    return np.abs(vm - vmo).max() / vmo.max()
+
+
+def _sym(s6):
+    return material.sym(s6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config0_forward(config0_oracle, precision):
+    mesh, bc, mat, ts, uo, ho, infos = config0_oracle
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, **opts) as s:
+        sig = np.empty((mesh.n_el * 8, 6))
+        hist = np.empty((7, mesh.n_el * 8))
+        u, st = s.forward(ts, sigma_out=sig, hist_out=hist)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    assert _per_step_rel(u, uo) < tol
+    assert _vm_rel(sig, infos[-1]["sigma"]) < (1e-10 if precision == "fp64" else 1e-4)
+    assert np.abs(hist[6] - ho[-1][..., 6].ravel()).max() < (1e-12 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plate_forward(plate_oracle, precision):
+    mesh, bc, mat, ts, uo, ho, infos = plate_oracle
+    assert 0 < infos[-1]["plastic"] < 8 * mesh.n_el      # heterogeneous elastic/plastic mix
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, **opts) as s:
+        sig = np.empty((mesh.n_el * 8, 6))
+        u, st = s.forward(ts, sigma_out=sig)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    assert _per_step_rel(u, uo) < tol, _per_step_rel(u, uo)
+    assert _vm_rel(sig, infos[-1]["sigma"]) < (1e-9 if precision == "fp64" else 1e-4)
+
+
+def test_spmv_and_solve_consistent():
+    """SpMV with symmetric Dirichlet elimination against scipy on the exported block-CSR
+    matrix (perforated plate), and PCG solves with the elastic tangent (u = 0, positive
+    definite) on a clamped cube; the mixed solve's true residual is bounded by the FP32
+    matrix (kappa * eps_32), so its bound is looser."""
+    from tests._helpers import bsr_to_csr
+    plate = inputs.config1_problem(nx=16, ny=8, nz=2, n_steps=4)
+    cube = inputs.config2_problem(n=6)
+    for (mesh, bc, mat, ts), check_solve in ((plate, False), (cube, True)):
+        for precision, tol_mv, tol_x in (("fp64", 1e-12, 1e-10), ("mixed", 1e-6, 1e-4)):
+            with hfe.from_inputs(mesh, bc, mat, precision=precision) as s:
+                s.sweep(np.zeros(mesh.n_dof), 0.0)
+                rowptr, cols, vals = s.get_bsr()
+                K = bsr_to_csr(rowptr, cols, vals, mesh.n_nodes)
+                free = np.ones(mesh.n_dof, bool)
+                free[bc.dof] = False
+                x = np.random.default_rng(0).standard_normal(mesh.n_dof)
+                y = s.spmv(x)
+                xm = np.where(free, x, 0.0)
+                y_ref = np.where(free, K @ xm, x)
+                assert np.abs(y - y_ref).max() < tol_mv * np.abs(y_ref).max()
+                if not check_solve:
+                    continue
+                b = np.where(free, np.random.default_rng(1).standard_normal(mesh.n_dof), 0.0)
+                dx, st = s.solve(b)
+                assert st["pcg_iters"] > 0
+                res = np.where(free, K @ np.where(free, dx, 0.0), 0.0) - b
+                assert np.linalg.norm(res) < tol_x * np.linalg.norm(b)
+                assert np.all(dx[~free] == 0.0)

@@ -38,7 +38,7 @@ def _uniaxial_closed_form(t, mesh):
 def test_homogeneous_uniaxial_closed_form():
     mesh, bc, mat, ts = inputs.config0_problem()
     prob = solver.from_inputs(mesh, bc, mat)
-    us, hs, infos = solver.forward(prob, ts, rtol=1e-12)
+    us, hs, infos = solver.forward(prob, ts, rtol=1e-13)
     for n, t in enumerate(ts):
         uex, a, T11, e11 = _uniaxial_closed_form(t, mesh)
         assert a > 0                                   # every step is plastic
