@@ -1,0 +1,314 @@
+"""Benchmark of the Gauss-point sweep on the 100^3 hex8 cube (3,090,903 dofs, 8,000,000 Gauss
+points; Hill-48 with Swift hardening, clamped-platen compression).
+
+One step = one pass of the per-Newton-iteration element sweep through the C ABI
+(hfe_gp_sweep, tangent mode): gather, kinematics, log strain, Hill-48 return mapping,
+consistent tangent, post-processing, element contraction, conflict-free scatter into the
+block-CSR matrix, and the FP64 residual norm over the free dofs.  The state is the
+deterministic mid-step compression state of paper_2606_17390_b300.inputs.compression_state
+(every Gauss point plastic).  Inputs (history 512 MB, K 982 MB) exceed the 126 MB L2, so no
+flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+# the CPU baseline runs the oracle single-threaded (set before numpy loads its BLAS)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+from paper_2606_17390_b300 import inputs  # noqa: E402
+
+METRIC = "Gauss-point updates/s (FP32-mixed vs FP64) at 3M DOF; adjoint/forward time ratio"
+UNIT = "GP/s"
+LOAD = 0.5
+# FP32 flops per Gauss point of the tangent sweep counted from the formulation (kinematics
+# 0.6k, eigen-decomposition 0.5k, return mapping and recovery 0.7k, post-processor and
+# rotated gradients 0.4k, algorithmic tangent in the eigenbasis of C 1.7k, dP/dF 1.0k,
+# element contraction with the symmetric K^e 3.4k); see the design doc.
+ALG_FLOPS_PER_GP = 8.3e3
+# algorithmic DRAM bytes per element of a mixed tangent sweep: conn 32, nodal X and u 48,
+# history in 448 and out 448, R 24, K 27 blocks x 36 B = 972
+ALG_BYTES_PER_EL = 32 + 48 + 448 + 448 + 24 + 972
+
+
+def _peaks():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def workload(n):
+    mesh, bc, mat, _ = inputs.config2_problem(n=n)
+    u, hist = inputs.compression_state(mesh, LOAD)
+    return mesh, bc, mat, u, hist
+
+
+def cpu_oracle_rate(mesh, mat, u, hist, target_s=12.0, seed=0):
+    """The FP64 oracle (as it stands) on a bounded sample of the same workload: the tangent
+    sweep of a seeded random sample of elements plus the assembly of their contributions,
+    single-threaded.  Returns (GP/s, description, cores, seconds)."""
+    from oracle import element, solver
+    hist_el = np.ascontiguousarray(hist.T.reshape(mesh.n_el, 8, 7))
+    rng = np.random.default_rng(seed)
+    prob = solver.Problem(X=mesh.X, conn=mesh.conn.astype(np.int64), fixed_dof=np.zeros(0, np.int64),
+                          fixed_val=np.zeros(0), theta=mat.theta_vector(), hardening=mat.hardening)
+
+    def run(k):
+        els = np.sort(rng.choice(mesh.n_el, size=k, replace=False))
+        sub = solver.Problem(X=mesh.X, conn=prob.conn[els], fixed_dof=prob.fixed_dof, fixed_val=prob.fixed_val,
+                             theta=prob.theta, hardening=prob.hardening)
+        t0 = time.perf_counter()
+        es = element.element_sweep(mesh.X, sub.conn, u, hist_el[els], sub.theta, sub.hardening)
+        solver.assemble_R(sub, es["Re"])
+        solver.assemble_K(sub, es["Ke"])
+        return time.perf_counter() - t0
+
+    t_probe = run(64)
+    k = int(min(mesh.n_el, max(64, 64 * target_s / max(t_probe, 1e-3))))
+    dt = run(k)
+    return 8 * k / dt, f"oracle tangent sweep + assembly of {k} random elements ({8 * k} Gauss points) of the same state", 1, dt
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    mesh, bc, mat, u, hist = workload(args.n)
+    rates, times = [], []
+    for i in range(args.warmup + args.steps):
+        r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist, target_s=args.ref_step_s, seed=i)
+        if i >= args.warmup:
+            rates.append(r)
+            times.append(dt)
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 8 * mesh.n_el / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"hex8 cube {args.n}^3, {mesh.n_dof} dofs, {8 * mesh.n_el} Gauss points, "
+                                   "Hill-48 + Swift, clamped compression, mid-step state; CPU oracle on a sample",
+                       "n_el": mesh.n_el, "n_dof": mesh.n_dof, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=100, help="cube edge in elements (100 = 3.09M dofs)")
+    ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64 comparison (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+    from paper_2606_17390_b300 import hfe
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    mesh, bc, mat, u, hist = workload(args.n)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(precision):
+        s = hfe.from_inputs(mesh, bc, mat, precision=precision, stream=stream.cuda_stream)
+        s.set_state(u, hist)
+        return s
+
+    solver = make(args.precision)
+    info = solver.info()
+    u_d = torch.from_numpy(u).to(dev)
+    R_d = torch.empty(mesh.n_dof, dtype=torch.float64, device=dev)
+    rn_d = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def step(s):
+        s.sweep(u_d, LOAD, tangent=True, R_out=R_d, rnorm_out=rn_d, stats=False)
+
+    # correctness / status of the workload before timing
+    _, _, st0 = solver.sweep(u_d, LOAD, tangent=True, R_out=R_d, rnorm_out=rn_d, stats=True)
+    for _ in range(args.warmup):
+        step(solver)
+    torch.cuda.synchronize()
+
+    def timed(s, k):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step(s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms
+
+    with ClockSampler(local) as clk:
+        ms_total = timed(solver, args.steps)
+    ms_step = ms_total / args.steps
+    value = world * 8 * mesh.n_el / (ms_step * 1e-3)
+
+    # per-launch device time of the dominant kernel (gp_sweep, one launch per colour),
+    # CUDA events on the library's launching stream (hfe_stats.sweep_ms)
+    sweep_ms = []
+    for _ in range(5):
+        _, _, st = solver.sweep(u_d, LOAD, tangent=True, R_out=R_d, rnorm_out=rn_d, stats=True)
+        sweep_ms.append(st["sweep_ms"])
+    sweep_ms_avg = float(np.mean(sweep_ms))
+    launch_ms = sweep_ms_avg / info["n_colors"]
+    el_per_launch = mesh.n_el / info["n_colors"]
+    flops_launch = ALG_FLOPS_PER_GP * 8 * el_per_launch
+    peak_fp32 = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
+    roofline = {"bound": "alu", "achieved": flops_launch / (launch_ms * 1e-3) / 1e12, "peak": peak_fp32,
+                "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": "gp_sweep_kernel<float,true>", "launch_ms": launch_ms,
+                "alg_flops_per_launch": flops_launch, "alg_bytes_per_launch": ALG_BYTES_PER_EL * el_per_launch,
+                "hbm_frac_of_measured": None, "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    roofline["frac"] = roofline["achieved"] / peak_fp32
+    peaks, src = _peaks()
+    roofline["hbm_frac_of_measured"] = ALG_BYTES_PER_EL * el_per_launch / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
+    traffic_file = os.path.join(HERE, "profiles", "gp_sweep_traffic.json")
+    if os.path.exists(traffic_file):
+        with open(traffic_file) as f:
+            tr = json.load(f)
+        if tr.get("precision") == args.precision and tr.get("n") == args.n:
+            roofline["traffic"] = tr.get("dram_bytes_per_launch")
+
+    # end to end through the C ABI with host buffers (pinned): u in, R and |R_free| out
+    u_h = torch.from_numpy(u).pin_memory()
+    R_h = torch.empty(mesh.n_dof, dtype=torch.float64).pin_memory()
+    rn_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    k_e2e = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        solver.sweep(u_h, LOAD, tangent=True, R_out=R_h, rnorm_out=rn_h, stats=False)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * 8 * mesh.n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * mesh.n_dof,
+           "d2h_bytes_per_step": 8 * mesh.n_dof + 8, "ms_per_step": 1e3 * e2e_s}
+
+    # FP64 form of the same sweep (the comparison the metric names)
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision == "mixed":
+        solver.close()
+        s64 = make("fp64")
+        step(s64)
+        ms64 = timed(s64, args.fp64_steps) / args.fp64_steps
+        fp64 = {"value": world * 8 * mesh.n_el / (ms64 * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps,
+                "mixed_speedup": ms64 / ms_step}
+        s64.close()
+    else:
+        solver.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": f"hex8 cube {args.n}^3 ({mesh.n_dof} dofs, {8 * mesh.n_el} Gauss points), "
+                                       "Hill-48 + Swift, clamped-platen compression, mid-step state, tangent sweep "
+                                       "+ assembly + residual norm",
+                           "n_el": mesh.n_el, "n_dof": mesh.n_dof, "n_blocks": info["n_blocks"],
+                           "precision": args.precision, "l2": "inputs larger than L2 (history 512 MB, K 982 MB)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
+                "gpu_launches": (info["n_colors"] + 1) * args.steps,
+                "clocks": clk.summary(), "peaks_source": src,
+                "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -168,12 +168,16 @@ hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist);
 #define HFE_SWEEP_TANGENT 1    /* R, trial history and K (into the internal BSR values) */
 
 /* One Gauss-point sweep at displacement u (host or device, [n_dof]) against the stored
- * history h_n: R_out[n_dof] (host or device, may be NULL) receives the internal force
- * minus t*f_ext with t = load (Dirichlet rows included, no elimination);
- * hist_trial_out [7][n_gp] (host or device, may be NULL) the updated history; in tangent
- * mode K is assembled into the handle (read it with hfe_get_bsr).  stats may be NULL. */
+ * history h_n (the per-Newton-iteration element pass, paper Sec. 2.2.5 "Parallel element-
+ * wise residual and stiffness calculation"): R_out[n_dof] (host or device, may be NULL)
+ * receives the internal force minus t*f_ext with t = load (Dirichlet rows included, no
+ * elimination); rnorm_out (host or device, may be NULL) the FP64 norm of R over the free
+ * dofs; hist_trial_out [7][n_gp] (host or device, may be NULL) the updated history; in
+ * tangent mode K is assembled into the handle (read it with hfe_get_bsr).  With stats ==
+ * NULL and device outputs the call does not synchronise (device status is checked by the
+ * next call that passes stats). */
 hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, double* R_out,
-                        double* hist_trial_out, hfe_stats* stats);
+                        double* rnorm_out, double* hist_trial_out, hfe_stats* stats);
 
 /* Export the block-CSR pattern (rowptr[n_nodes+1], cols[n_blocks]) and the values of the
  * last assembled K as float64 [n_blocks*9] (row-major 3x3 blocks); any pointer may be NULL;

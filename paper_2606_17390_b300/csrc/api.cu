@@ -435,8 +435,8 @@ hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist) {
   return cuda_check(h, cudaStreamSynchronize(h->s), "get state");
 }
 
-hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, double* R_out, double* hist_trial_out,
-                        hfe_stats* stats) {
+hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, double* R_out, double* rnorm_out,
+                        double* hist_trial_out, hfe_stats* stats) {
   if (h == nullptr || u == nullptr) return HFE_EINVAL;
   if (mode != HFE_SWEEP_RESIDUAL && mode != HFE_SWEEP_TANGENT) return fail(h, HFE_EINVAL, "sweep: unknown mode");
   auto w0 = std::chrono::steady_clock::now();
@@ -450,6 +450,11 @@ hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, d
   cudaEventRecord(h->t0, h->s);
   HFE_TRY(sweep(h, ud, load, mode, Rd, nullptr));
   cudaEventRecord(h->t1, h->s);
+  if (rnorm_out != nullptr) {
+    const bool dev = is_device_ptr(rnorm_out);
+    free_norm(Rd, h->freem, h->n_dof, h->sc, h->part, h->s, dev ? rnorm_out : h->b64);
+    if (!dev) HFE_TRY(copy_out(h, rnorm_out, h->b64, sizeof(double)));
+  }
   if (R_out != nullptr && Rd != R_out) HFE_TRY(copy_out(h, R_out, Rd, sizeof(double) * h->n_dof));
   if (hist_trial_out) HFE_TRY(copy_out(h, hist_trial_out, h->hist_trial, sizeof(double) * 7 * h->n_gp));
   if (stats != nullptr) {
@@ -557,7 +562,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         spmv_rows<float>(K, (const float*)h->K, h->freem, (const float*)h->vp, (float*)h->vq, h->s);
         predictor_rhs<float>(h->R, (const float*)h->vq, h->f_ext, t[n] - t_prev, h->freem, h->b64, h->n_dof, h->s);
       }
-      free_norm(h->b64, h->freem, h->n_dof, h->sc, h->part, h->s);
+      free_norm(h->b64, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
       HFE_TRY(read_status(h));
       ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
       set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
@@ -580,7 +585,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       cudaEventRecord(h->t0, h->s);
       HFE_TRY(sweep(h, h->u, t[n], HFE_SWEEP_TANGENT, h->R, nullptr));
       cudaEventRecord(h->t1, h->s);
-      free_norm(h->R, h->freem, h->n_dof, h->sc, h->part, h->s);
+      free_norm(h->R, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
       HFE_TRY(read_status(h));
       loc.sweeps++;
       loc.sweep_ms += elapsed(h->t0, h->t1);

@@ -288,7 +288,7 @@ __global__ void precond_kernel(const R* __restrict__ vals, const int64_t* __rest
 
 // ||R_free||^2 (FP64, deterministic) into sc->rr via the last-CTA reduction.
 __global__ void __launch_bounds__(kBlock) free_norm_kernel(const double* __restrict__ R_, const uint8_t* __restrict__ freem,
-                                                           int64_t n_dof, PcgScalars* sc, double* part) {
+                                                           int64_t n_dof, PcgScalars* sc, double* part, double* out) {
   const int64_t d0 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   double s = 0.0, nf = 0.0;
   for (int64_t d = d0; d < n_dof; d += (int64_t)gridDim.x * kBlock) {
@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(kBlock) free_norm_kernel(const double* __restr
   if (last_block_reduce(s, nf, part, &sc->ticket, ts, tn) && threadIdx.x == 0) {
     sc->norm2 = ts;
     sc->nonfinite = tn;
+    if (out != nullptr) *out = sqrt(ts);
   }
 }
 
@@ -386,8 +387,8 @@ void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const 
 }
 
 void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,
-               cudaStream_t s) {
-  free_norm_kernel<<<rblk(n_dof, kBlock), kBlock, 0, s>>>(R_, freem, n_dof, sc, part);
+               cudaStream_t s, double* out) {
+  free_norm_kernel<<<rblk(n_dof, kBlock), kBlock, 0, s>>>(R_, freem, n_dof, sc, part, out);
 }
 
 template <typename R>

@@ -49,8 +49,9 @@ void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>
 template <typename R>
 void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
                    int block3, int* bad, cudaStream_t s);
+// ||R_free||^2 into sc->norm2 and, if out != nullptr, ||R_free|| into *out (device)
 void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,
-               cudaStream_t s);
+               cudaStream_t s, double* out);
 template <typename R>
 void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s);
 void set_dirichlet(double* u, const int64_t* dof, const double* val, double t, int64_t n_fixed, cudaStream_t s);

@@ -93,7 +93,7 @@ def lib():
     L.hfe_set_material.argtypes = [vp, C.POINTER(_Material)]
     L.hfe_set_state.argtypes = [vp, vp, vp]
     L.hfe_get_state.argtypes = [vp, vp, vp]
-    L.hfe_gp_sweep.argtypes = [vp, vp, dbl, i32, vp, vp, C.POINTER(Stats)]
+    L.hfe_gp_sweep.argtypes = [vp, vp, dbl, i32, vp, vp, vp, C.POINTER(Stats)]
     L.hfe_get_bsr.argtypes = [vp, vp, vp, vp]
     L.hfe_spmv.argtypes = [vp, vp, vp]
     L.hfe_solve.argtypes = [vp, vp, vp, C.POINTER(Stats)]
@@ -217,14 +217,15 @@ class Solver:
         return u, hist
 
     # -- hot path
-    def sweep(self, u, load=1.0, tangent=True, R_out=None, hist_out=None, stats=True):
-        """One Gauss-point sweep; returns (R, hist_trial, stats) with host arrays unless the
-        caller passes its own (host or device) output buffers."""
+    def sweep(self, u, load=1.0, tangent=True, R_out=None, hist_out=None, stats=True, rnorm_out=None):
+        """One Gauss-point sweep; returns (R, hist_trial, stats).  Host arrays are allocated
+        unless the caller passes its own (host or device) output buffers; rnorm_out (a
+        1-element buffer) receives the FP64 norm of R over the free dofs."""
         R = np.empty(self.n_dof) if R_out is None else R_out
         H = hist_out
         s = Stats() if stats else None
         st = lib().hfe_gp_sweep(self._h, _ptr(u), float(load), SWEEP_TANGENT if tangent else SWEEP_RESIDUAL,
-                                _ptr(R), _ptr(H), C.byref(s) if s is not None else None)
+                                _ptr(R), _ptr(rnorm_out), _ptr(H), C.byref(s) if s is not None else None)
         self._check(st)
         return R, H, (s.as_dict() if s is not None else None)
 

@@ -22,7 +22,7 @@ __all__ = [
     "clamp_displace_bcs", "config0_problem", "config1_problem", "config2_problem",
     "config2h_problem", "config1_material", "config0_material", "load_factors",
     "random_deformation_gradients", "random_history", "distorted_box_mesh",
-    "hill_from_r_values",
+    "hill_from_r_values", "compression_state",
 ]
 
 
@@ -241,6 +241,31 @@ def config2h_problem(n: int = 100, n_steps: int = 10):
     """Homogeneous variant of config2_problem: roller symmetry BCs, u_x(x=1) = -0.1 t."""
     mesh = box_mesh(n, n, n)
     return mesh, roller_uniaxial_bcs(mesh, -0.1, axis=0), config0_material(), load_factors(n_steps)
+
+
+def compression_state(mesh: Mesh, t: float, strain: float = 0.1, bulge: float = 0.3,
+                      alpha_lag: float = 0.85, H: float = 0.70, G: float = 0.30):
+    """A seeded-free, deterministic mid-step state of the clamped-platen compression of the
+    unit cube (config 2) at load factor t: displacement u_x = -strain t X, lateral bulge
+    u_y = bulge strain t (Y - 1/2) 4X(1-X), u_z likewise (zero on both clamped faces, so the
+    Dirichlet data hold exactly), and a history that lags behind it: alpha = alpha_lag *
+    strain * t * (1 + 4X(1-X)) / 2 with eps_p = alpha * diag(-1, H, G) (the traceless
+    compression flow direction of a Hill material with G + H = 1).  Returns u [n_dof] and
+    the history [7][n_gp] at the Gauss points' elements' centres."""
+    X = mesh.X
+    s = 4.0 * X[:, 0] * (1.0 - X[:, 0])
+    u = np.stack([-strain * t * X[:, 0], bulge * strain * t * (X[:, 1] - 0.5) * s,
+                  bulge * strain * t * (X[:, 2] - 0.5) * s], axis=1).ravel()
+    xc = X[mesh.conn].mean(axis=1)
+    sc = 4.0 * xc[:, 0] * (1.0 - xc[:, 0])
+    alpha_el = alpha_lag * strain * t * 0.5 * (1.0 + sc)
+    alpha = np.repeat(alpha_el, 8)
+    hist = np.zeros((7, alpha.size))
+    hist[0] = -alpha
+    hist[1] = H * alpha
+    hist[2] = G * alpha
+    hist[6] = alpha
+    return u, hist
 
 
 def hill_from_r_values(r11, r22, r33, r12, r23, r13):
