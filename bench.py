@@ -229,6 +229,20 @@ def main():
     ms_step = ms_total / args.steps
     value = world * 8 * mesh.n_el / (ms_step * 1e-3)
 
+    # the same sweep without the tangent and assembly (residual and history only), for context
+    def step_res(s):
+        s.sweep(u_d, LOAD, tangent=False, R_out=R_d, rnorm_out=rn_d, stats=False)
+    step_res(solver)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_res = max(3, args.steps // 4)
+    e0.record(stream)
+    for _ in range(k_res):
+        step_res(solver)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_res = e0.elapsed_time(e1) / k_res
+
     # per-launch device time of the dominant kernel (gp_sweep, one launch per colour),
     # CUDA events on the library's launching stream (hfe_stats.sweep_ms)
     sweep_ms = []
@@ -302,6 +316,7 @@ def main():
                            "precision": args.precision, "l2": "inputs larger than L2 (history 512 MB, K 982 MB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
+                "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

@@ -95,6 +95,10 @@ hfe_status upload_material(hfe_handle* h, const hfe_material* m) {
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
   launch_material_setup(h->theta, h->Theta, h->n_mat, h->mat64, h->matf, h->bad, h->s);
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
+  if (h->n_mat == 1) {
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(&h->h_mat64, h->mat64, sizeof(MatRec), cudaMemcpyDeviceToHost, h->s), "copy"));
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(&h->h_matf, h->matf, sizeof(MatRecF), cudaMemcpyDeviceToHost, h->s), "copy"));
+  }
   HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "material set-up"));
   if (*h->h_bad != 0) return fail(h, HFE_EINVAL, "material: " + std::to_string(*h->h_bad) +
                                                      " record(s) with non-positive Hill eigenvalue or elastic modulus");
@@ -109,15 +113,45 @@ hfe_status read_status(hfe_handle* h) {
   return cuda_check(h, cudaGetLastError(), "kernel launch");
 }
 
+hfe_status ensure_hist_io(hfe_handle* h) {
+  if (h->hist_io == nullptr) HFE_TRY(dalloc(h, &h->hist_io, 7 * (size_t)h->n_gp));
+  return HFE_OK;
+}
+
+// user history (FP64 [7][n_gp], host or device) into an internal history buffer
+hfe_status import_history(hfe_handle* h, const double* user, void* dst) {
+  const double* src = user;
+  if (!is_device_ptr(user)) {
+    HFE_TRY(ensure_hist_io(h));
+    HFE_TRY(copy_in(h, h->hist_io, user, sizeof(double) * 7 * h->n_gp));
+    src = h->hist_io;
+  }
+  launch_hist_import(src, dst, h->fp64 != 0, h->n_gp, h->s);
+  return HFE_OK;
+}
+
+// internal history buffer out to FP64 [7][n_gp] (host or device)
+hfe_status export_history(hfe_handle* h, const void* src, double* user) {
+  if (is_device_ptr(user)) {
+    launch_hist_export(src, user, h->fp64 != 0, h->n_gp, h->s);
+    return HFE_OK;
+  }
+  HFE_TRY(ensure_hist_io(h));
+  launch_hist_export(src, h->hist_io, h->fp64 != 0, h->n_gp, h->s);
+  return copy_out(h, user, h->hist_io, sizeof(double) * 7 * h->n_gp);
+}
+
 // one sweep on the internal stream; u may be any device pointer; R into Rdst (device)
 hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev) {
   SweepArgs a;
   a.X = h->X;
+  a.dX32 = h->dX32;
   a.conn = h->conn;
   a.u = u_dev;
   a.hist = h->hist;
   a.hist_trial = h->hist_trial;
   a.mat = h->fp64 ? (const void*)h->mat64 : (const void*)h->matf;
+  a.mat_host = h->n_mat == 1 ? (h->fp64 ? (const void*)&h->h_mat64 : (const void*)&h->h_matf) : nullptr;
   a.mat_per_element = h->n_mat > 1 ? 1 : 0;
   a.hardening = h->hardening;
   a.elems = h->elems;
@@ -290,8 +324,27 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   HFE_TRY(dalloc(h, &h->X, h->n_dof));
   HFE_TRY(dalloc(h, &h->conn, h->n_el * 8));
   HFE_TRY(dalloc(h, &h->u, h->n_dof));
-  HFE_TRY(dalloc(h, &h->hist, 8 * h->n_gp));
-  HFE_TRY(dalloc(h, &h->hist_trial, 8 * h->n_gp));
+  {
+    unsigned char* b = nullptr;
+    HFE_TRY(dalloc(h, &b, hist_bytes(h->n_gp, f64))); h->hist = b;
+    HFE_TRY(dalloc(h, &b, hist_bytes(h->n_gp, f64))); h->hist_trial = b;
+  }
+  if (!f64) {   // coordinate differences X_a - X_0 (a = 1..7) per element, rounded once to FP32
+    std::vector<double> Xh(h->n_dof);
+    if (is_device_ptr(mesh->X)) cudaMemcpy(Xh.data(), mesh->X, 8 * h->n_dof, cudaMemcpyDeviceToHost);
+    else std::memcpy(Xh.data(), mesh->X, 8 * h->n_dof);
+    std::vector<float> dx(21 * (size_t)h->n_el);
+    for (int64_t e = 0; e < h->n_el; ++e) {
+      const int64_t n0 = conn_h[e * 8];
+      for (int a = 1; a < 8; ++a) {
+        const int64_t na = conn_h[e * 8 + a];
+        for (int c = 0; c < 3; ++c) dx[e * 21 + (a - 1) * 3 + c] = (float)(Xh[3 * na + c] - Xh[3 * n0 + c]);
+      }
+    }
+    HFE_TRY(dalloc(h, &h->dX32, dx.size()));
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->dX32, dx.data(), 4 * dx.size(), cudaMemcpyHostToDevice, h->s), "copy"));
+    HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));
+  }
   HFE_TRY(dalloc(h, &h->rowptr, h->n_nodes + 1));
   HFE_TRY(dalloc(h, &h->cols, h->P.n_blocks));
   HFE_TRY(dalloc(h, &h->diag_slot, h->n_nodes));
@@ -367,8 +420,8 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   }
   HFE_TRY(upload_material(h, mat));
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, sizeof(double) * h->n_dof, h->s), "memset"));
-  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->hist, 0, sizeof(double) * 8 * h->n_gp, h->s), "memset"));
-  launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->hist, 0, hist_bytes(h->n_gp, f64), h->s), "memset"));
+  launch_sigma_cache(h->hist, f64, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
   HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "create"));
   return cuda_check(h, cudaGetLastError(), "create kernels");
 }
@@ -411,7 +464,7 @@ hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat) {
   if (h == nullptr) return HFE_EINVAL;
   StreamScope scope(h);
   HFE_TRY(upload_material(h, mat));
-  launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+  launch_sigma_cache(h->hist, h->fp64 != 0, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
   return cuda_check(h, cudaStreamSynchronize(h->s), "set material");
 }
 
@@ -420,9 +473,9 @@ hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist) {
   StreamScope scope(h);
   if (u) HFE_TRY(copy_in(h, h->u, u, sizeof(double) * h->n_dof));
   else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, sizeof(double) * h->n_dof, h->s), "memset"));
-  if (hist) HFE_TRY(copy_in(h, h->hist, hist, sizeof(double) * 7 * h->n_gp));
-  else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->hist, 0, sizeof(double) * 7 * h->n_gp, h->s), "memset"));
-  launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+  if (hist) HFE_TRY(import_history(h, hist, h->hist));
+  else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->hist, 0, hist_bytes(h->n_gp, h->fp64 != 0), h->s), "memset"));
+  launch_sigma_cache(h->hist, h->fp64 != 0, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
   h->t_state = 0.0;
   return cuda_check(h, cudaStreamSynchronize(h->s), "set state");
 }
@@ -431,7 +484,7 @@ hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist) {
   if (h == nullptr) return HFE_EINVAL;
   StreamScope scope(h);
   HFE_TRY(copy_out(h, u, h->u, sizeof(double) * h->n_dof));
-  HFE_TRY(copy_out(h, hist, h->hist, sizeof(double) * 7 * h->n_gp));
+  if (hist) HFE_TRY(export_history(h, h->hist, hist));
   return cuda_check(h, cudaStreamSynchronize(h->s), "get state");
 }
 
@@ -456,7 +509,7 @@ hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, d
     if (!dev) HFE_TRY(copy_out(h, rnorm_out, h->b64, sizeof(double)));
   }
   if (R_out != nullptr && Rd != R_out) HFE_TRY(copy_out(h, R_out, Rd, sizeof(double) * h->n_dof));
-  if (hist_trial_out) HFE_TRY(copy_out(h, hist_trial_out, h->hist_trial, sizeof(double) * 7 * h->n_gp));
+  if (hist_trial_out) HFE_TRY(export_history(h, h->hist_trial, hist_trial_out));
   if (stats != nullptr) {
     HFE_TRY(read_status(h));
     std::memset(stats, 0, sizeof(*stats));
@@ -630,7 +683,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       HFE_TRY(copy_out(h, sigma_out, h->sigma, sizeof(double) * 6 * h->n_gp));
     }
     std::swap(h->hist, h->hist_trial);   // commit h_n = H(u_n, h_{n-1})
-    if (!h->fp64) launch_sigma_cache(h->hist, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+    if (!h->fp64) launch_sigma_cache(h->hist, false, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
     if (u_out_dev_or_host != nullptr) {
       double* dst = u_out_dev_or_host + (size_t)n * h->n_dof;
       if (u_out_dev) HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, h->u, 8 * h->n_dof, cudaMemcpyDeviceToDevice, h->s), "copy"));
@@ -640,7 +693,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
     if (hook) HFE_TRY(hook->after_commit(h, n));
     loc.steps_done = n + 1;
   }
-  if (hist_out) HFE_TRY(copy_out(h, hist_out, h->hist, sizeof(double) * 7 * h->n_gp));
+  if (hist_out) HFE_TRY(export_history(h, h->hist, hist_out));
   HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "forward"));
   loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
   if (st) *st = loc;

@@ -34,8 +34,10 @@ struct hfe_handle {
   double* X = nullptr;
   int32_t* conn = nullptr;
   double* u = nullptr;
-  double* hist = nullptr;
-  double* hist_trial = nullptr;
+  void* hist = nullptr;         // internal history layout (hist_bytes)
+  void* hist_trial = nullptr;
+  float* dX32 = nullptr;        // mixed path: per-element coordinate differences
+  double* hist_io = nullptr;    // FP64 [7][n_gp] staging for state transfer (lazy)
   int64_t* rowptr = nullptr;
   int32_t* cols = nullptr;
   int64_t* diag_slot = nullptr;
@@ -51,6 +53,8 @@ struct hfe_handle {
   double* Theta = nullptr;
   MatRec* mat64 = nullptr;
   MatRecF* matf = nullptr;
+  MatRec h_mat64;               // host copies of the record when n_mat == 1
+  MatRecF h_matf;
   DevStatus* status = nullptr;
   PcgScalars* sc = nullptr;
   double* part = nullptr;
@@ -111,6 +115,8 @@ bool is_device_ptr(const void* p);
 hfe_status copy_in(hfe_handle* h, void* dst, const void* src, size_t bytes);
 hfe_status copy_out(hfe_handle* h, void* dst, const void* src, size_t bytes);
 hfe_status read_status(hfe_handle* h);
+hfe_status import_history(hfe_handle* h, const double* user, void* dst);
+hfe_status export_history(hfe_handle* h, const void* src, double* user);
 hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev);
 hfe_status check_sweep_status(hfe_handle* h);
 hfe_status solve_any(hfe_handle* h, const double* b, double bscale, int64_t* iters);

@@ -50,13 +50,20 @@ struct DevStatus {
   int pad[2];
 };
 
+// History storage.  FP64 path: double [8][n_gp] = eps_p (6), alpha, sigma_y(alpha).
+// Mixed path: float [7][n_gp] = eps_p (6), alpha, followed by double [n_gp] sigma_y(alpha)
+// at byte offset 28 n_gp (the FP64 yield-stress cache of the FP64 return-mapping steps).
+inline size_t hist_bytes(int64_t n_gp, bool fp64) { return fp64 ? 64 * (size_t)n_gp : 36 * (size_t)n_gp; }
+
 struct SweepArgs {
   const double* X;         // [n_nodes*3]
+  const float* dX32;       // [n_el*21] X_a - X_0 of nodes 1..7 (mixed path)
   const int32_t* conn;     // [n_el*8]
   const double* u;         // [n_dof]
-  const double* hist;      // [8][n_gp]  eps_p(6), alpha, sigma_y(alpha) cache
-  double* hist_trial;      // [8][n_gp]
-  const void* mat;         // MatRec* or MatRecF*
+  const void* hist;        // layout above
+  void* hist_trial;
+  const void* mat;         // MatRec* or MatRecF* (device)
+  const void* mat_host;    // host copy of the record when one material serves every element, else nullptr
   int mat_per_element;
   int hardening;
   const int32_t* elems;    // colour-sorted element ids
@@ -77,7 +84,10 @@ void launch_material_setup(const double* theta, const double* Theta, int64_t n_m
 // mode: HFE_SWEEP_RESIDUAL / HFE_SWEEP_TANGENT; fp64 selects the plain FP64 kernel.
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
                      cudaStream_t s);
-void launch_sigma_cache(double* hist, const void* mat, int mat_per_element, int hardening,
+void launch_sigma_cache(void* hist, bool fp64, const MatRec* mat, int mat_per_element, int hardening,
                         int64_t n_gp, cudaStream_t s);
+// user layout double [7][n_gp] <-> internal layout (the cache is not touched)
+void launch_hist_import(const double* user, void* hist, bool fp64, int64_t n_gp, cudaStream_t s);
+void launch_hist_export(const void* hist, double* user, bool fp64, int64_t n_gp, cudaStream_t s);
 
 }  // namespace hfe

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "hfe_internal.h"
 
@@ -31,13 +32,24 @@ constexpr double kSq2 = 1.41421356237309504880;
 constexpr double kISq2 = 0.70710678118654752440;
 constexpr int kElemsPerCta = 16;
 constexpr int kThreads = 128;
-constexpr int kGpStride = 120;   // shared floats per Gauss point: A 84 (81 used), g 24, P 12 (9 used)
+constexpr int kGpStride = 81;    // shared words per Gauss point: A 45 (major-symmetric), P 9, g 24, pad 3
+constexpr int kOffP = 45;
+constexpr int kOffG = 54;
+// per element: 648 = 8 mod 32, so the 4 elements of a warp read from banks 0, 8, 16, 24 in
+// phase 2, and the 32 Gauss points of a warp (offsets 8 le + 17 g mod 32) write to 32
+// distinct banks in phase 1
+constexpr int kElStride = 8 * kGpStride;
 
 // Mandel pair index helpers: p -> (i, j) and (i, j) -> p for the order 11,22,33,12,23,13.
 __host__ __device__ constexpr int pI(int p) { return p < 3 ? p : (p == 4 ? 1 : 0); }
 __host__ __device__ constexpr int pJ(int p) { return p < 3 ? p : (p == 3 ? 1 : 2); }
 __host__ __device__ constexpr int pidx(int i, int j) {
   return i == j ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5));
+}
+
+// packed index of the major-symmetric A_PQ (P = 3i + J, Q = 3k + L), upper triangle P <= Q
+__host__ __device__ constexpr int asym(int P, int Q) {
+  return P <= Q ? P * 9 - (P * (P - 1)) / 2 + (Q - P) : Q * 9 - (Q * (Q - 1)) / 2 + (P - Q);
 }
 
 template <typename R> struct Num;
@@ -158,16 +170,22 @@ __device__ __forceinline__ R dd2(R ei, R ej, R ek, R f_kj, R f_ji) {
 }
 
 // ----------------------------------------------------------------------------------------
+// Small value types: the helpers below receive copies, never addresses, of material data
+// (a uniform material record is a kernel parameter, whose address must not be taken).
+struct Hard3 { double p0, p1, p2; };
+struct Vec6d { double v[6]; };
+struct Vec6f { float v[6]; };
+
 // Hardening.  Plain FP64 evaluation (library pow / exp).
-__device__ __forceinline__ void sigy64(int type, const double* hp, double a, double& sy, double& dsy) {
+__device__ __forceinline__ void sigy64(int type, Hard3 hp, double a, double& sy, double& dsy) {
   if (type == HFE_HARDENING_SWIFT) {
-    double z = hp[1] + a;
-    sy = hp[0] * pow(z, hp[2]);
-    dsy = hp[2] * sy / z;
+    double z = hp.p1 + a;
+    sy = hp.p0 * pow(z, hp.p2);
+    dsy = hp.p2 * sy / z;
   } else {
-    double e = exp(-hp[2] * a);
-    sy = hp[0] + hp[1] * (1.0 - e);
-    dsy = hp[1] * hp[2] * e;
+    double e = exp(-hp.p2 * a);
+    sy = hp.p0 + hp.p1 * (1.0 - e);
+    dsy = hp.p1 * hp.p2 * e;
   }
 }
 
@@ -215,8 +233,8 @@ struct RM {
 };
 
 // Plain FP64 form (every operation in FP64).
-__device__ RM return_map_fp64(const double t[6], const double h[6], double mu, double hmin,
-                              int type, const double* hp, double alpn, double ftr, int maxit,
+__device__ __forceinline__ RM return_map_fp64(const double t[6], const Vec6d hv, double mu, double hmin,
+                              int type, Hard3 hp, double alpn, double ftr, int maxit,
                               double tol) {
   RM out;
   double dg = 0.0, lo = 0.0, hi = ftr / (2.0 * mu * hmin);
@@ -231,9 +249,9 @@ __device__ RM return_map_fp64(const double t[6], const double h[6], double mu, d
     double phi2 = 0.0, acc = 0.0;
 #pragma unroll
     for (int i = 1; i < 6; ++i) {
-      double d = 1.0 + s * h[i];
+      double d = 1.0 + s * hv.v[i];
       double Ti = t[i] / d;
-      double hT = h[i] * Ti;
+      double hT = hv.v[i] * Ti;
       phi2 += hT * Ti;
       acc += hT * hT / d;
     }
@@ -258,7 +276,7 @@ __device__ RM return_map_fp64(const double t[6], const double h[6], double mu, d
 
 // Mixed form: the Newton iterations in FP32 to ~1e-6, then one FP64 Newton step on the yield
 // residual (written as phi^2 - phi_y^2 to avoid a square root) with FP64 reciprocals.
-__device__ RM return_map_mixed(const float t[6], const double* h, const float* hf, float mu,
+__device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv, const Vec6f hfv, float mu,
                                float hmin, const HardInc& inc, double syn64, float ftr, int maxit) {
   RM out;
   const float sq23 = (float)kSq23;
@@ -275,9 +293,9 @@ __device__ RM return_map_mixed(const float t[6], const double* h, const float* h
     float phi2 = 0.0f, acc = 0.0f;
 #pragma unroll
     for (int i = 1; i < 6; ++i) {
-      float d = 1.0f + s * hf[i];
+      float d = 1.0f + s * hfv.v[i];
       float Ti = t[i] / d;
-      float hT = hf[i] * Ti;
+      float hT = hfv.v[i] * Ti;
       phi2 += hT * Ti;
       acc += hT * hT / d;
     }
@@ -301,9 +319,9 @@ __device__ RM return_map_mixed(const float t[6], const double* h, const float* h
   double phi2 = 0.0;
 #pragma unroll
   for (int i = 1; i < 6; ++i) {
-    double c = rcp64(fma(s, h[i], 1.0));
+    double c = rcp64(fma(s, hv.v[i], 1.0));
     double Ti = (double)t[i] * c;
-    phi2 = fma(h[i] * Ti, Ti, phi2);
+    phi2 = fma(hv.v[i] * Ti, Ti, phi2);
   }
   double rt = phi2 - phy * phy;
   float corr = (float)rt / (2.0f * (float)phy * dr);
@@ -318,16 +336,28 @@ __device__ RM return_map_mixed(const float t[6], const double* h, const float* h
   return out;
 }
 
+template <typename R> struct Hist {
+  // component c of Gauss point i, and the FP64 sigma_y(alpha) cache
+  __device__ static R* comp(void* b, int c, int64_t ng) { return reinterpret_cast<R*>(b) + c * ng; }
+  __device__ static double* cache(void* b, int64_t ng) {
+    return sizeof(R) == 8 ? reinterpret_cast<double*>(b) + 7 * ng
+                          : reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(b) + 28 * ng);
+  }
+};
+
 template <typename R> struct MatOf;
 template <> struct MatOf<float> { using T = MatRecF; };
 template <> struct MatOf<double> { using T = MatRec; };
 
 // ----------------------------------------------------------------------------------------
-template <typename R, bool TANGENT>
-__global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t cbeg, int64_t ccount) {
+// UNIF: one material for all elements, passed by value so that its entries are kernel-
+// parameter (constant-bank) operands rather than loads.
+template <typename R, bool TANGENT, bool UNIF>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
+    gp_sweep_kernel(SweepArgs a, const typename MatOf<R>::T mrec, int64_t cbeg, int64_t ccount) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sNode = reinterpret_cast<R*>(smem_raw);                     // [16][8][6]: dX(3), du(3)
-  R* sGp = sNode + kElemsPerCta * 8 * 6;                           // [128][kGpStride]
+  R* sGp = sNode + kElemsPerCta * 8 * 6;                           // [16][kElStride]
 
   const int tid = threadIdx.x;
   const int le = tid >> 3;
@@ -339,26 +369,49 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
   const unsigned gmask = 0xffu << (lane & 24);
 
   using MR = typename MatOf<R>::T;
-  const MatRec* mat64 = reinterpret_cast<const MatRec*>(a.mat);   // FP64 records (FP64 path)
   const MR* matR = reinterpret_cast<const MR*>(a.mat);
   const int mi = a.mat_per_element ? e : 0;
 
+  // history of this Gauss point, loaded first so that it arrives during the kinematics
+  const int64_t ng = a.n_gp;
+  const int64_t gpi = (int64_t)e * 8 + g;   // global Gauss-point index
+  R epn[6];
+  R alpn_r = R(0);
+  double syn_cache = 0.0;
+  if (valid) {
+    void* hb = const_cast<void*>(a.hist);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) epn[c] = Hist<R>::comp(hb, c, ng)[gpi];
+    alpn_r = Hist<R>::comp(hb, 6, ng)[gpi];
+    if (sizeof(R) == 4) syn_cache = Hist<R>::cache(hb, ng)[gpi];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) epn[c] = R(0);
+  }
+
   // ---- S1 gather: node g of element e; coordinates and displacements relative to node 0
-  // (differences taken in FP64, then rounded to R)
+  // (displacement differences taken in FP64, then rounded to R; the mixed path reads the
+  // element's coordinate differences, rounded once at set-up)
   {
     int node = valid ? a.conn[(int64_t)e * 8 + g] : 0;
-    double x0 = a.X[3 * (int64_t)node], x1 = a.X[3 * (int64_t)node + 1], x2 = a.X[3 * (int64_t)node + 2];
     double u0 = a.u[3 * (int64_t)node], u1 = a.u[3 * (int64_t)node + 1], u2 = a.u[3 * (int64_t)node + 2];
     const int src = lane & 24;
-    double bx0 = __shfl_sync(gmask, x0, src), bx1 = __shfl_sync(gmask, x1, src), bx2 = __shfl_sync(gmask, x2, src);
     double bu0 = __shfl_sync(gmask, u0, src), bu1 = __shfl_sync(gmask, u1, src), bu2 = __shfl_sync(gmask, u2, src);
     R* dst = sNode + (le * 8 + g) * 6;
-    dst[0] = (R)(x0 - bx0); dst[1] = (R)(x1 - bx1); dst[2] = (R)(x2 - bx2);
+    if constexpr (sizeof(R) == 8) {
+      double x0 = a.X[3 * (int64_t)node], x1 = a.X[3 * (int64_t)node + 1], x2 = a.X[3 * (int64_t)node + 2];
+      double bx0 = __shfl_sync(gmask, x0, src), bx1 = __shfl_sync(gmask, x1, src), bx2 = __shfl_sync(gmask, x2, src);
+      dst[0] = (R)(x0 - bx0); dst[1] = (R)(x1 - bx1); dst[2] = (R)(x2 - bx2);
+    } else {
+      const float* dx = a.dX32 + (int64_t)e * 21 + (g - 1) * 3;
+      dst[0] = (g > 0 && valid) ? dx[0] : 0.0f;
+      dst[1] = (g > 0 && valid) ? dx[1] : 0.0f;
+      dst[2] = (g > 0 && valid) ? dx[2] : 0.0f;
+    }
     dst[3] = (R)(u0 - bu0); dst[4] = (R)(u1 - bu1); dst[5] = (R)(u2 - bu2);
   }
   __syncwarp(gmask);
 
-  const int64_t gpi = (int64_t)e * 8 + g;   // global Gauss-point index
   int flag_detj = 0, flag_local = 0, flag_plastic = 0, local_iters = 0;
 
   if (valid) {
@@ -457,17 +510,12 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
     }
 
     // ---- S4 elastic predictor (Eq. Tr_stress) and return mapping in the Hill eigenbasis
-    const double* hist = a.hist;
-    const int64_t ng = a.n_gp;
-    double epn[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) epn[c] = hist[c * ng + gpi];
-    const double alpn = hist[6 * ng + gpi];
-    const MR& m = matR[mi];
+    const double alpn = (double)alpn_r;
+    const MR& m = UNIF ? mrec : matR[mi];
     const R lam = m.lam, mu = m.mu;
     R ee[6];
 #pragma unroll
-    for (int p = 0; p < 6; ++p) ee[p] = epsM[p] - (R)(p < 3 ? epn[p] : kSq2 * epn[p]);
+    for (int p = 0; p < 6; ++p) ee[p] = epsM[p] - (p < 3 ? epn[p] : R(kSq2) * epn[p]);
     R tre = ee[0] + ee[1] + ee[2];
     R Ttr[6];
 #pragma unroll
@@ -485,9 +533,13 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
     rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0;
     double syn64;
     if constexpr (sizeof(R) == 8) {
-      const MatRec& m64 = mat64[mi];
+      const MR& m64 = m;
       double dsy0;
-      sigy64(a.hardening, m64.hard, alpn, syn64, dsy0);
+      const Hard3 hp3{m64.hard[0], m64.hard[1], m64.hard[2]};
+      Vec6d hv;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) hv.v[i] = m64.h[i];
+      sigy64(a.hardening, hp3, alpn, syn64, dsy0);
       double phi2 = 0.0;
 #pragma unroll
       for (int i = 1; i < 6; ++i) phi2 += m64.h[i] * (double)t[i] * (double)t[i];
@@ -497,15 +549,15 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
         double td[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) td[i] = (double)t[i];
-        rm = return_map_fp64(td, m64.h, m64.mu, m64.hmin, a.hardening, m64.hard, alpn, ftr, a.local_maxit,
+        rm = return_map_fp64(td, hv, m64.mu, m64.hmin, a.hardening, hp3, alpn, ftr, a.local_maxit,
                              a.local_tol);
       } else {
         rm.syn1 = syn64;
         rm.dsy = (float)dsy0;
       }
     } else {
-      syn64 = hist[7 * ng + gpi];
-      const MatRecF& mf = reinterpret_cast<const MatRecF*>(a.mat)[mi];
+      syn64 = syn_cache;
+      const MR& mf = m;
       float phi2 = 0.0f;
 #pragma unroll
       for (int i = 1; i < 6; ++i) phi2 += mf.h[i] * (float)t[i] * (float)t[i];
@@ -532,7 +584,11 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
         float tf[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) tf[i] = (float)t[i];
-        rm = return_map_mixed(tf, mf.h64, mf.h, mf.mu, mf.hmin, inc, syn64, ftr, a.local_maxit);
+        Vec6d hv;
+        Vec6f hfv;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { hv.v[i] = mf.h64[i]; hfv.v[i] = mf.h[i]; }
+        rm = return_map_mixed(tf, hv, hfv, mf.mu, mf.hmin, inc, syn64, ftr, a.local_maxit);
       } else {
         float incv, dsy;
         inc.eval(0.0f, incv, dsy);
@@ -563,7 +619,7 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
       TM[i] = s;
     }
     {
-      double* ht = a.hist_trial;
+      void* hb = a.hist_trial;
       if (plastic) {
         R neig[6];
         neig[0] = R(0);
@@ -575,16 +631,15 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
           R s = R(0);
 #pragma unroll
           for (int j = 1; j < 6; ++j) s += m.QH[p * 6 + j] * neig[j];
-          double inc_t = (double)(dgR * s) * (p < 3 ? 1.0 : kISq2);
-          ht[p * ng + gpi] = epn[p] + inc_t;
+          Hist<R>::comp(hb, p, ng)[gpi] = epn[p] + dgR * s * (p < 3 ? R(1) : R(kISq2));
         }
-        ht[6 * ng + gpi] = alpn + kSq23 * rm.dgamma;
+        Hist<R>::comp(hb, 6, ng)[gpi] = (R)(alpn + kSq23 * rm.dgamma);
       } else {
 #pragma unroll
-        for (int p = 0; p < 6; ++p) ht[p * ng + gpi] = epn[p];
-        ht[6 * ng + gpi] = alpn;
+        for (int p = 0; p < 6; ++p) Hist<R>::comp(hb, p, ng)[gpi] = epn[p];
+        Hist<R>::comp(hb, 6, ng)[gpi] = alpn_r;
       }
-      ht[7 * ng + gpi] = rm.syn1;
+      Hist<R>::cache(hb, ng)[gpi] = rm.syn1;
     }
 
     // ---- S6 post-processor in the eigenbasis of C: That = Q^T T Q, Shat_ab = 2 f1_ab That_ab
@@ -629,17 +684,17 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) Ft[i][j] = F[i][0] * Q[0][j] + F[i][1] * Q[1][j] + F[i][2] * Q[2][j];
-    R* gp = sGp + (size_t)tid * kGpStride;
+    R* gp = sGp + (size_t)le * kElStride + g * kGpStride;
     const R wd = det0;
 #pragma unroll
     for (int n = 0; n < 8; ++n)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) gp[84 + n * 3 + j] = gN[n][0] * Q[0][j] + gN[n][1] * Q[1][j] + gN[n][2] * Q[2][j];
+      for (int j = 0; j < 3; ++j) gp[kOffG + n * 3 + j] = gN[n][0] * Q[0][j] + gN[n][1] * Q[1][j] + gN[n][2] * Q[2][j];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        gp[108 + i * 3 + j] = wd * (Ft[i][0] * Sh[0][j] + Ft[i][1] * Sh[1][j] + Ft[i][2] * Sh[2][j]);
+        gp[kOffP + i * 3 + j] = wd * (Ft[i][0] * Sh[0][j] + Ft[i][1] * Sh[1][j] + Ft[i][2] * Sh[2][j]);
     if (a.sigma != nullptr) {   // Cauchy stress sigma = P F^T / J, P = Ftilde Shat Q^T
       R P[3][3];
 #pragma unroll
@@ -769,17 +824,14 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
           for (int q = 0; q < 6; ++q)
             Xt[i][J][q] = Ft[i][0] * Ct[pidx(0, J)][q] + Ft[i][1] * Ct[pidx(1, J)][q] + Ft[i][2] * Ct[pidx(2, J)][q];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+      for (int P = 0; P < 9; ++P)
 #pragma unroll
-        for (int J = 0; J < 3; ++J)
-#pragma unroll
-          for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int L = 0; L < 3; ++L) {
-              R s = Xt[i][J][pidx(0, L)] * Ft[k][0] + Xt[i][J][pidx(1, L)] * Ft[k][1] + Xt[i][J][pidx(2, L)] * Ft[k][2];
-              if (i == k) s += Sh[J][L];
-              gp[(i * 3 + J) * 9 + k * 3 + L] = wd * s;
-            }
+        for (int Qi = P; Qi < 9; ++Qi) {
+          const int i = P / 3, J = P % 3, k = Qi / 3, L = Qi % 3;
+          R s = Xt[i][J][pidx(0, L)] * Ft[k][0] + Xt[i][J][pidx(1, L)] * Ft[k][1] + Xt[i][J][pidx(2, L)] * Ft[k][2];
+          if (i == k) s += Sh[J][L];
+          gp[asym(P, Qi)] = wd * s;
+        }
     }
   }
 
@@ -802,19 +854,24 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
   if (!valid) return;
-  const R* G = sGp + (size_t)(le * 8) * kGpStride;
+  const R* G = sGp + (size_t)le * kElStride;
   R Ra[3] = {R(0), R(0), R(0)};
   const int arow = g;
   if constexpr (TANGENT) {
-    R Kr[8][9];
+    // K^e is symmetric (A is stored with its major symmetry), so row a computes the blocks
+    // (a, a + d mod 8) for d = 0..3 (d = 4 as well for a < 4): each unordered pair once, 4 or
+    // 5 blocks per thread, and writes every off-diagonal block together with its transpose.
+    constexpr int kNb = 5;
+    const int nb = (arow < 4) ? 5 : 4;
+    R Kr[kNb][9];
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
+    for (int d = 0; d < kNb; ++d)
 #pragma unroll
-      for (int c = 0; c < 9; ++c) Kr[b][c] = R(0);
+      for (int c = 0; c < 9; ++c) Kr[d][c] = R(0);
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
       const R* A = G + q * kGpStride;
-      const R* gt = A + 84;
+      const R* gt = A + kOffG;
       const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
       R U[3][3][3];
 #pragma unroll
@@ -823,42 +880,55 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
         for (int k = 0; k < 3; ++k)
 #pragma unroll
           for (int L = 0; L < 3; ++L)
-            U[i][k][L] = ga0 * A[(i * 3 + 0) * 9 + k * 3 + L] + ga1 * A[(i * 3 + 1) * 9 + k * 3 + L] +
-                         ga2 * A[(i * 3 + 2) * 9 + k * 3 + L];
+            U[i][k][L] = ga0 * A[asym(i * 3 + 0, k * 3 + L)] + ga1 * A[asym(i * 3 + 1, k * 3 + L)] +
+                         ga2 * A[asym(i * 3 + 2, k * 3 + L)];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        const R gb0 = gt[b * 3], gb1 = gt[b * 3 + 1], gb2 = gt[b * 3 + 2];
+      for (int d = 0; d < kNb; ++d) {
+        if (d < nb) {
+          const int b = (arow + d) & 7;
+          const R gb0 = gt[b * 3], gb1 = gt[b * 3 + 1], gb2 = gt[b * 3 + 2];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+          for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) Kr[b][i * 3 + k] += U[i][k][0] * gb0 + U[i][k][1] * gb1 + U[i][k][2] * gb2;
+            for (int k = 0; k < 3; ++k) Kr[d][i * 3 + k] += U[i][k][0] * gb0 + U[i][k][1] * gb1 + U[i][k][2] * gb2;
+        }
       }
-      const R* P = A + 108;
+      const R* P = A + kOffP;
 #pragma unroll
       for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
     }
     R* Kv = reinterpret_cast<R*>(a.K);
-    const int32_t* sl = a.slot + (int64_t)e * 64 + arow * 8;
+    const int32_t* sl = a.slot + (int64_t)e * 64;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int32_t sv = sl[b];
-      const bool store = sv < 0;
-      R* dst = Kv + (int64_t)(sv & 0x7fffffff) * 9;
-      if (store) {
+    for (int d = 0; d < kNb; ++d) {
+      if (d < nb) {
+        const int b = (arow + d) & 7;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) dst[c] = Kr[b][c];
-      } else {
+        for (int tr = 0; tr < 2; ++tr) {
+          if (tr == 1 && d == 0) continue;
+          const int32_t sv = tr == 0 ? sl[arow * 8 + b] : sl[b * 8 + arow];
+          R* dst = Kv + (int64_t)(sv & 0x7fffffff) * 9;
+          if (sv < 0) {
 #pragma unroll
-        for (int c = 0; c < 9; ++c) dst[c] += Kr[b][c];
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) dst[i * 3 + k] = tr == 0 ? Kr[d][i * 3 + k] : Kr[d][k * 3 + i];
+          } else {   // one writer per block per launch and launches in colour order: deterministic
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int k = 0; k < 3; ++k) atomicAdd(dst + i * 3 + k, tr == 0 ? Kr[d][i * 3 + k] : Kr[d][k * 3 + i]);
+          }
+        }
       }
     }
   } else {
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
       const R* A = G + q * kGpStride;
-      const R* gt = A + 84;
+      const R* gt = A + kOffG;
       const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
-      const R* P = A + 108;
+      const R* P = A + kOffP;
 #pragma unroll
       for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
     }
@@ -873,7 +943,7 @@ __global__ void __launch_bounds__(kThreads) gp_sweep_kernel(SweepArgs a, int64_t
     for (int i = 0; i < 3; ++i) {
       double v = (double)Ra[i];
       if (store) Rg[i] = v - (a.f_ext ? a.load * a.f_ext[3 * (int64_t)node + i] : 0.0);
-      else Rg[i] += v;
+      else atomicAdd(Rg + i, v);
     }
   }
 }
@@ -1014,14 +1084,29 @@ __global__ void material_setup_kernel(const double* theta, const double* Theta, 
   }
 }
 
-// sigma_y(alpha) cache (history component 7) recomputed in FP64 from alpha (component 6).
-__global__ void sigma_cache_kernel(double* hist, const MatRec* mat, int per_element, int type, int64_t n_gp) {
+// sigma_y(alpha) cache recomputed in FP64 from alpha (history component 6).
+template <typename R>
+__global__ void sigma_cache_kernel(void* hist, const MatRec* mat, int per_element, int type, int64_t n_gp) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_gp) return;
   const MatRec& m = mat[per_element ? (i >> 3) : 0];
   double sy, dsy;
-  sigy64(type, m.hard, hist[6 * n_gp + i], sy, dsy);
-  hist[7 * n_gp + i] = sy;
+  sigy64(type, Hard3{m.hard[0], m.hard[1], m.hard[2]}, (double)Hist<R>::comp(hist, 6, n_gp)[i], sy, dsy);
+  Hist<R>::cache(hist, n_gp)[i] = sy;
+}
+
+template <typename R>
+__global__ void hist_import_kernel(const double* user, void* hist, int64_t n_gp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 7 * n_gp) return;
+  Hist<R>::comp(hist, 0, n_gp)[i] = (R)user[i];
+}
+
+template <typename R>
+__global__ void hist_export_kernel(const void* hist, double* user, int64_t n_gp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 7 * n_gp) return;
+  user[i] = (double)Hist<R>::comp(const_cast<void*>(hist), 0, n_gp)[i];
 }
 
 }  // namespace
@@ -1033,38 +1118,57 @@ void launch_material_setup(const double* theta, const double* Theta, int64_t n_m
   material_setup_kernel<<<blocks, threads, 0, s>>>(theta, Theta, n_mat, out, outf, bad);
 }
 
-void launch_sigma_cache(double* hist, const void* mat, int mat_per_element, int hardening, int64_t n_gp,
+void launch_sigma_cache(void* hist, bool fp64, const MatRec* mat, int mat_per_element, int hardening, int64_t n_gp,
                         cudaStream_t s) {
-  int threads = 256;
-  int64_t blocks = (n_gp + threads - 1) / threads;
-  sigma_cache_kernel<<<(unsigned)blocks, threads, 0, s>>>(hist, reinterpret_cast<const MatRec*>(mat),
-                                                          mat_per_element, hardening, n_gp);
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n_gp + threads - 1) / threads);
+  if (fp64) sigma_cache_kernel<double><<<blocks, threads, 0, s>>>(hist, mat, mat_per_element, hardening, n_gp);
+  else sigma_cache_kernel<float><<<blocks, threads, 0, s>>>(hist, mat, mat_per_element, hardening, n_gp);
 }
 
-template <typename R, bool TANGENT>
+void launch_hist_import(const double* user, void* hist, bool fp64, int64_t n_gp, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((7 * n_gp + threads - 1) / threads);
+  if (fp64) hist_import_kernel<double><<<blocks, threads, 0, s>>>(user, hist, n_gp);
+  else hist_import_kernel<float><<<blocks, threads, 0, s>>>(user, hist, n_gp);
+}
+
+void launch_hist_export(const void* hist, double* user, bool fp64, int64_t n_gp, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((7 * n_gp + threads - 1) / threads);
+  if (fp64) hist_export_kernel<double><<<blocks, threads, 0, s>>>(hist, user, n_gp);
+  else hist_export_kernel<float><<<blocks, threads, 0, s>>>(hist, user, n_gp);
+}
+
+template <typename R, bool TANGENT, bool UNIF>
 static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cudaStream_t s) {
-  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kThreads * kGpStride);
+  using MR = typename MatOf<R>::T;
+  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * kElStride);
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_done = true;
   }
+  MR rec;
+  if (UNIF) memcpy(&rec, a.mat_host, sizeof(MR));   // host copy of the single record
+  else memset(&rec, 0, sizeof(MR));
   for (size_t c = 0; c + 1 < off.size(); ++c) {
     int64_t cnt = off[c + 1] - off[c];
     if (cnt <= 0) continue;
     unsigned blocks = (unsigned)((cnt + kElemsPerCta - 1) / kElemsPerCta);
-    gp_sweep_kernel<R, TANGENT><<<blocks, kThreads, smem, s>>>(a, off[c], cnt);
+    gp_sweep_kernel<R, TANGENT, UNIF><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
   }
 }
 
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
                      cudaStream_t s) {
+  const bool u = a.mat_host != nullptr;
   if (fp64) {
-    if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true>(a, color_off, s);
-    else launch_typed<double, false>(a, color_off, s);
+    if (mode == HFE_SWEEP_TANGENT) u ? launch_typed<double, true, true>(a, color_off, s) : launch_typed<double, true, false>(a, color_off, s);
+    else u ? launch_typed<double, false, true>(a, color_off, s) : launch_typed<double, false, false>(a, color_off, s);
   } else {
-    if (mode == HFE_SWEEP_TANGENT) launch_typed<float, true>(a, color_off, s);
-    else launch_typed<float, false>(a, color_off, s);
+    if (mode == HFE_SWEEP_TANGENT) u ? launch_typed<float, true, true>(a, color_off, s) : launch_typed<float, true, false>(a, color_off, s);
+    else u ? launch_typed<float, false, true>(a, color_off, s) : launch_typed<float, false, false>(a, color_off, s);
   }
 }
 

@@ -15,7 +15,9 @@ from tests._helpers import bsr_to_csr, hist_oracle_to_soa, mixed_state, rel_inf
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": dict(R=1e-11, K=1e-9, h=1e-12), "mixed": dict(R=2e-5, K=1e-4, h=2e-6)}
+# mixed: FP32 kinematics and FP32 history storage (eps_p, alpha); the history bound matches
+# the 1e-5 displacement tolerance of the mixed path
+TOL = {"fp64": dict(R=1e-11, K=1e-9, h=1e-12), "mixed": dict(R=2e-5, K=1e-4, h=1e-5)}
 
 
 def _oracle(mesh, u, hist, theta, hardening, Theta):
