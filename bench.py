@@ -164,6 +164,7 @@ def main():
     ap.add_argument("--n", type=int, default=100, help="cube edge in elements (100 = 3.09M dofs)")
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64 comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
     args = ap.parse_args()
 
@@ -287,6 +288,36 @@ def main():
     e2e = {"value": world * 8 * mesh.n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * mesh.n_dof,
            "d2h_bytes_per_step": 8 * mesh.n_dof + 8, "ms_per_step": 1e3 * e2e_s}
 
+    # the linear solve of the Newton step on the same mesh: block-Jacobi PCG with the BSR SpMV
+    # (elastic tangent at u = 0, fixed iteration count), for context
+    pcg = None
+    if args.pcg_iters > 0:
+        s_pcg = hfe.from_inputs(mesh, bc, mat, precision=args.precision, stream=stream.cuda_stream,
+                                pcg_maxit=args.pcg_iters, pcg_rtol=1e-30, pcg_check_every=args.pcg_iters)
+        s_pcg.sweep(np.zeros(mesh.n_dof), 0.0, tangent=True)
+        free = np.ones(mesh.n_dof)
+        free[bc.dof] = 0.0
+        b = torch.from_numpy(free).to(dev)
+        try:
+            s_pcg.solve(b)
+        except hfe.HfeError:
+            pass                       # the iteration cap is the point: time per iteration
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        try:
+            s_pcg.solve(b)
+        except hfe.HfeError:
+            pass
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n_blocks = info["n_blocks"]
+        bytes_spmv = n_blocks * (9 * (4 if args.precision == "mixed" else 8) + 4)
+        pcg = {"iters": args.pcg_iters, "ms_per_iter": ms / args.pcg_iters,
+               "spmv_alg_bytes": bytes_spmv}
+        s_pcg.close()
+
     # FP64 form of the same sweep (the comparison the metric names)
     fp64 = None
     if args.fp64_steps > 0 and args.precision == "mixed":
@@ -317,6 +348,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
+                "pcg": pcg,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

@@ -142,21 +142,22 @@ hfe_status export_history(hfe_handle* h, const void* src, double* user) {
 }
 
 // one sweep on the internal stream; u may be any device pointer; R into Rdst (device)
-hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev) {
+hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev,
+                    void* K, const void* hist, void* hist_trial, bool fp64) {
   SweepArgs a;
   a.X = h->X;
   a.dX32 = h->dX32;
   a.conn = h->conn;
   a.u = u_dev;
-  a.hist = h->hist;
-  a.hist_trial = h->hist_trial;
-  a.mat = h->fp64 ? (const void*)h->mat64 : (const void*)h->matf;
-  a.mat_host = h->n_mat == 1 ? (h->fp64 ? (const void*)&h->h_mat64 : (const void*)&h->h_matf) : nullptr;
+  a.hist = hist;
+  a.hist_trial = hist_trial;
+  a.mat = fp64 ? (const void*)h->mat64 : (const void*)h->matf;
+  a.mat_host = h->n_mat == 1 ? (fp64 ? (const void*)&h->h_mat64 : (const void*)&h->h_matf) : nullptr;
   a.mat_per_element = h->n_mat > 1 ? 1 : 0;
   a.hardening = h->hardening;
   a.elems = h->elems;
   a.slot = h->slot;
-  a.K = h->K;
+  a.K = K;
   a.R = Rdst;
   a.f_ext = h->f_ext;
   a.load = load;
@@ -166,8 +167,12 @@ hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, doub
   a.local_maxit = h->opt.local_maxit;
   a.local_tol = h->opt.local_tol;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->s), "memset"));
-  launch_gp_sweep(a, h->fp64 != 0, mode, h->P.color_off, h->s);
+  launch_gp_sweep(a, fp64, mode, h->P.color_off, h->s);
   return HFE_OK;
+}
+
+hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev) {
+  return sweep_ex(h, u_dev, load, mode, Rdst, sigma_dev, h->K, h->hist, h->hist_trial, h->fp64 != 0);
 }
 
 hfe_status check_sweep_status(hfe_handle* h) {
@@ -180,41 +185,41 @@ hfe_status check_sweep_status(hfe_handle* h) {
 }
 
 template <typename R>
-PcgVecs<R> vecs(hfe_handle* h) {
+PcgVecs<R> vecs(LinSys& ls) {
   PcgVecs<R> v;
-  v.x = (R*)h->vx; v.r = (R*)h->vr; v.z = (R*)h->vz; v.p = (R*)h->vp; v.q = (R*)h->vq; v.minv = (R*)h->vminv;
+  v.x = (R*)ls.vx; v.r = (R*)ls.vr; v.z = (R*)ls.vz; v.p = (R*)ls.vp; v.q = (R*)ls.vq; v.minv = (R*)ls.vminv;
   return v;
 }
 
 template <typename R>
-hfe_status build_pcg_graph(hfe_handle* h, int len) {
-  if (h->pcg_graph != nullptr && h->pcg_graph_len == len) return HFE_OK;
-  if (h->pcg_graph != nullptr) {
-    cudaGraphExecDestroy(h->pcg_graph);
-    h->pcg_graph = nullptr;
+hfe_status build_pcg_graph(hfe_handle* h, LinSys& ls, int len) {
+  if (ls.graph != nullptr && ls.graph_len == len) return HFE_OK;
+  if (ls.graph != nullptr) {
+    cudaGraphExecDestroy(ls.graph);
+    ls.graph = nullptr;
   }
   Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
-  PcgVecs<R> v = vecs<R>(h);
+  PcgVecs<R> v = vecs<R>(ls);
   const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
   cudaGraph_t g;
   HFE_TRY(cuda_check(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal), "capture"));
-  for (int i = 0; i < len; ++i) pcg_iteration<R>(K, (const R*)h->K, h->freem, v, block3, h->sc, h->part, h->s);
+  for (int i = 0; i < len; ++i) pcg_iteration<R>(K, (const R*)ls.K, h->freem, v, block3, h->sc, h->part, h->s);
   HFE_TRY(cuda_check(h, cudaStreamEndCapture(h->s, &g), "end capture"));
-  cudaError_t e = cudaGraphInstantiate(&h->pcg_graph, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&ls.graph, g, 0);
   cudaGraphDestroy(g);
   HFE_TRY(cuda_check(h, e, "graph instantiate"));
-  h->pcg_graph_len = len;
+  ls.graph_len = len;
   return HFE_OK;
 }
 
 // Solve Kt x = bscale * b with PCG (b device FP64 [n_dof]); x left in h->vx (precision R).
 template <typename R>
-hfe_status pcg_solve(hfe_handle* h, const double* b, double bscale, int64_t* iters_out) {
+hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters_out) {
   Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
-  PcgVecs<R> v = vecs<R>(h);
+  PcgVecs<R> v = vecs<R>(ls);
   const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
-  precond_setup<R>(K, (const R*)h->K, h->diag_slot, h->freem, v.minv, block3, h->bad, h->s);
+  precond_setup<R>(K, (const R*)ls.K, h->diag_slot, h->freem, v.minv, block3, h->bad, h->s);
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
   {
     const double rt2 = h->opt.pcg_rtol * h->opt.pcg_rtol;
@@ -232,10 +237,10 @@ hfe_status pcg_solve(hfe_handle* h, const double* b, double bscale, int64_t* ite
   if (rr0 > 0.0) {
     const double target = h->opt.pcg_rtol * h->opt.pcg_rtol * rr0;
     const int m = std::max(1, h->opt.pcg_check_every);
-    HFE_TRY(build_pcg_graph<R>(h, m));
+    HFE_TRY(build_pcg_graph<R>(h, ls, m));
     bool done = false;
     while (it < h->opt.pcg_maxit) {
-      HFE_TRY(cuda_check(h, cudaGraphLaunch(h->pcg_graph, h->s), "graph launch"));
+      HFE_TRY(cuda_check(h, cudaGraphLaunch(ls.graph, h->s), "graph launch"));
       it += m;
       HFE_TRY(read_status(h));
       if (h->h_sc->done || h->h_sc->rr <= target) { done = true; break; }
@@ -252,8 +257,12 @@ hfe_status pcg_solve(hfe_handle* h, const double* b, double bscale, int64_t* ite
   return HFE_OK;
 }
 
+hfe_status solve_sys(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters) {
+  return ls.fp64 ? pcg_solve<double>(h, ls, b, bscale, iters) : pcg_solve<float>(h, ls, b, bscale, iters);
+}
+
 hfe_status solve_any(hfe_handle* h, const double* b, double bscale, int64_t* iters) {
-  return h->fp64 ? pcg_solve<double>(h, b, bscale, iters) : pcg_solve<float>(h, b, bscale, iters);
+  return solve_sys(h, h->ls, b, bscale, iters);
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -372,6 +381,9 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vq = b;
     HFE_TRY(dalloc(h, &b, rsz * 9 * h->n_nodes)); h->vminv = b;
   }
+  h->ls.K = h->K;
+  h->ls.vx = h->vx; h->ls.vr = h->vr; h->ls.vz = h->vz; h->ls.vp = h->vp; h->ls.vq = h->vq; h->ls.vminv = h->vminv;
+  h->ls.fp64 = f64;
   if (cudaMallocHost(&h->h_sc, sizeof(PcgScalars)) != cudaSuccess ||
       cudaMallocHost(&h->h_status, sizeof(DevStatus)) != cudaSuccess || cudaMallocHost(&h->h_bad, sizeof(int)) != cudaSuccess)
     return fail(h, HFE_ENOMEM, "pinned host allocation failed");
@@ -430,7 +442,7 @@ void hfe_destroy(hfe_handle* h) {
   if (h == nullptr) return;
   if (h->s) cudaStreamSynchronize(h->s);
   adjoint_free(h->adj);
-  if (h->pcg_graph) cudaGraphExecDestroy(h->pcg_graph);
+  if (h->ls.graph) cudaGraphExecDestroy(h->ls.graph);
   for (void* p : h->allocs) cudaFree(p);
   if (h->sigma) cudaFree(h->sigma);
   if (h->h_sc) cudaFreeHost(h->h_sc);

@@ -21,6 +21,18 @@ using hfe::MatRecF;
 using hfe::Pattern;
 using hfe::PcgScalars;
 
+namespace hfe {
+// One linear system: block-CSR values in the pattern of the handle and the Krylov workspace
+// (precision R = double if fp64 else float), with its CUDA graph of CG iterations.
+struct LinSys {
+  void* K = nullptr;
+  void *vx = nullptr, *vr = nullptr, *vz = nullptr, *vp = nullptr, *vq = nullptr, *vminv = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  bool fp64 = true;
+};
+}  // namespace hfe
+
 struct hfe_handle {
   hfe_options opt;
   int fp64 = 1;
@@ -69,9 +81,7 @@ struct hfe_handle {
   PcgScalars* h_sc = nullptr;
   DevStatus* h_status = nullptr;
   int* h_bad = nullptr;
-  // CUDA graph of pcg_check_every CG iterations
-  cudaGraphExec_t pcg_graph = nullptr;
-  int pcg_graph_len = 0;
+  hfe::LinSys ls;              // the handle's own system (K and vectors above)
   size_t device_bytes = 0;
   std::string err;
   std::vector<void*> allocs;
@@ -118,6 +128,10 @@ hfe_status read_status(hfe_handle* h);
 hfe_status import_history(hfe_handle* h, const double* user, void* dst);
 hfe_status export_history(hfe_handle* h, const void* src, double* user);
 hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev);
+// sweep with explicit K values, history buffers and precision (FP64 systems of the adjoint)
+hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, double* Rdst, double* sigma_dev,
+                    void* K, const void* hist, void* hist_trial, bool fp64);
+hfe_status solve_sys(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters);
 hfe_status check_sweep_status(hfe_handle* h);
 hfe_status solve_any(hfe_handle* h, const double* b, double bscale, int64_t* iters);
 float elapsed(cudaEvent_t a, cudaEvent_t b);

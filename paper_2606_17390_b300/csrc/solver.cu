@@ -77,9 +77,12 @@ __device__ __forceinline__ bool last_block_reduce(double pa, double pb, double* 
 }
 
 // y = Kt x with Kt the matrix whose fixed rows/columns are dropped and whose fixed diagonal is 1.
-// One warp per block row; the lanes walk the row's values contiguously (coalesced), each
-// value v of the row belongs to block v/9, row (v%9)/3, column v%3.  Optionally
-// accumulates x.y (FP64) into a last-CTA reduction that sets alpha = rz / (p.Ap).
+// One warp per block row, one lane per 3x3 block (rows with more than 32 blocks loop): the
+// lane loads the block's column, the three x entries it multiplies and its 9 values (the
+// warp's value loads cover the row's contiguous 36-byte blocks), then the warp reduces the
+// three partial row sums.  COLMASK = false skips the column mask: inside CG the fixed
+// components of p are exactly zero (r, z and p start at zero there and stay zero).
+// Optionally accumulates x.y (FP64) into a last-CTA reduction that sets alpha = rz / (p.Ap).
 template <typename R, bool COLMASK>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(const int64_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ cols,
@@ -88,37 +91,53 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(const int64_t* __restrict_
                                                       const R* __restrict__ x, R* __restrict__ y,
                                                       int64_t n_nodes, PcgScalars* sc, double* part) {
   const int lane = threadIdx.x & 31;
-  const int64_t wstride = (int64_t)gridDim.x * (kBlock / 32);
+  const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
+  const int64_t w = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
   double dot = 0.0;
-  for (int64_t row = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); row < n_nodes; row += wstride) {
-    const int64_t b0 = rowptr[row];
-    const int nv = (int)(rowptr[row + 1] - b0) * 9;
-    const R* v = vals + b0 * 9;
-    R a0 = R(0), a1 = R(0), a2 = R(0);
-    for (int k = lane; k < nv; k += 32) {
-      const int blk = k / 9;
-      const int rr = k - blk * 9;
-      const int i = rr / 3;
-      const int c = rr - i * 3;
-      const int64_t col = cols[b0 + blk];
-      const int64_t d = 3 * col + c;
-      const R xv = (!COLMASK || freem[d]) ? x[d] : R(0);
-      const R p = v[k] * xv;
-      a0 += (i == 0) ? p : R(0);
-      a1 += (i == 1) ? p : R(0);
-      a2 += (i == 2) ? p : R(0);
-    }
-    a0 = warp_sum_r(a0);
-    a1 = warp_sum_r(a1);
-    a2 = warp_sum_r(a2);
-    if (lane == 0) {
-      const int64_t d = 3 * row;
-      R o[3] = {a0, a1, a2};
+  // each warp takes two rows per pass (rows w + 2k nwarps and w + (2k+1) nwarps): two
+  // independent load chains in flight per lane
+  for (int64_t r0 = w; r0 < n_nodes; r0 += 2 * nwarps) {
+    const int64_t r1 = r0 + nwarps;
+    const bool has1 = r1 < n_nodes;
+    const int64_t b0 = rowptr[r0], e0 = rowptr[r0 + 1];
+    const int64_t b1 = has1 ? rowptr[r1] : 0, e1 = has1 ? rowptr[r1 + 1] : 0;
+    const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
+    R a[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+    const int nmax = nb0 > nb1 ? nb0 : nb1;
+    for (int j = lane; j < nmax; j += 32) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        R out = freem[d + i] ? o[i] : (COLMASK ? x[d + i] : R(0));
-        y[d + i] = out;
-        dot += (double)x[d + i] * (double)out;
+      for (int t = 0; t < 2; ++t) {
+        const int nb = t == 0 ? nb0 : nb1;
+        if (j < nb) {
+          const int64_t blk = (t == 0 ? b0 : b1) + j;
+          const int64_t col = cols[blk];
+          const R* v = vals + blk * 9;
+          R x0 = x[3 * col], x1 = x[3 * col + 1], x2 = x[3 * col + 2];
+          if (COLMASK) {
+            x0 = freem[3 * col] ? x0 : R(0);
+            x1 = freem[3 * col + 1] ? x1 : R(0);
+            x2 = freem[3 * col + 2] ? x2 : R(0);
+          }
+          a[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
+          a[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
+          a[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) a[t][i] = warp_sum_r(a[t][i]);
+    if (lane < 6) {
+      const int t = lane / 3, i = lane % 3;
+      if (t == 0 || has1) {
+        const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
+        const R o = t == 0 ? (i == 0 ? a[0][0] : (i == 1 ? a[0][1] : a[0][2]))
+                           : (i == 0 ? a[1][0] : (i == 1 ? a[1][1] : a[1][2]));
+        const R xd = x[d];
+        const R out = freem[d] ? o : (COLMASK ? xd : R(0));
+        y[d] = out;
+        dot += (double)xd * (double)out;
       }
     }
   }
@@ -373,7 +392,7 @@ void pcg_init(const double* b, double bscale, const uint8_t* freem, PcgVecs<R>& 
 template <typename R>
 void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3, PcgScalars* sc,
                    double* part, cudaStream_t s) {
-  spmv_kernel<R, true><<<rblk(K.n_nodes, kBlock / 32), kBlock, 0, s>>>(K.rowptr, K.cols, vals, freem, v.p, v.q,
+  spmv_kernel<R, false><<<rblk(K.n_nodes, kBlock / 32), kBlock, 0, s>>>(K.rowptr, K.cols, vals, freem, v.p, v.q,
                                                                  K.n_nodes, sc, part);
   pcg_update_kernel<R><<<rblk(K.n_nodes, kBlock), kBlock, 0, s>>>(v.x, v.r, v.z, v.p, v.q, v.minv, block3,
                                                                   K.n_nodes, sc, part);

@@ -150,6 +150,7 @@ class Solver:
         dof = np.ascontiguousarray(fixed_dof, dtype=np.int64)
         val = np.ascontiguousarray(fixed_val, dtype=np.float64)
         th, Th = material_arrays(theta, Theta)
+        self.Theta_axes = Theta
         self.n_nodes, self.n_el = X.shape[0], conn.shape[0]
         self.n_dof, self.n_gp = 3 * self.n_nodes, 8 * self.n_el
         self.hardening = hardening
@@ -260,7 +261,11 @@ class Solver:
         return u_out, s.as_dict()
 
     def adjoint(self, t, u_target, w=1.0, grad_out=None):
+        """Misfit J = w sum_n ||u^n - u_target^n||^2 of a forward run from the zero state and its
+        gradient dJ/dtheta by the discrete adjoint; returns (J, grad [n_mat, 11], stats)."""
         t = np.ascontiguousarray(t, dtype=np.float64)
+        if isinstance(u_target, np.ndarray):
+            u_target = np.ascontiguousarray(u_target, dtype=np.float64)
         if grad_out is None:
             grad_out = np.empty((self.n_mat, 11))
         J = C.c_double()
