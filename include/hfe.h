@@ -115,6 +115,12 @@ typedef struct {
                              u = u_{n-1} + du_D + dK^-1 (-(R + K du_D)) built on the converged
                              start-of-step state, where K is positive definite; 0: from u_{n-1}
                              with the new Dirichlet values only */
+  int ew_forcing;         /* 1: inexact Newton, the CG tolerance of each Newton solve follows the
+                             Eisenstat-Walker forcing term (never below pcg_rtol) and a step is
+                             accepted only after a correction solved to pcg_rtol; about 2x fewer
+                             CG iterations on well-behaved runs, but loose solves can send the
+                             iterates of ill-conditioned meshes astray.  0 (default): every
+                             Newton solve to pcg_rtol */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */

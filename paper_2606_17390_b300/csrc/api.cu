@@ -222,7 +222,8 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   precond_setup<R>(K, (const R*)ls.K, h->diag_slot, h->freem, v.minv, block3, h->bad, h->s);
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
   {
-    const double rt2 = h->opt.pcg_rtol * h->opt.pcg_rtol;
+    const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
+    const double rt2 = rt * rt;
     HFE_TRY(cuda_check(h, cudaMemcpyAsync(&h->sc->target, &rt2, sizeof(double), cudaMemcpyHostToDevice, h->s),
                        "copy"));
     HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));   // rt2 lives on this stack frame
@@ -235,7 +236,8 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   if (!std::isfinite(rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
   int64_t it = 0;
   if (rr0 > 0.0) {
-    const double target = h->opt.pcg_rtol * h->opt.pcg_rtol * rr0;
+    const double rtc = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
+    const double target = rtc * rtc * rr0;
     const int m = std::max(1, h->opt.pcg_check_every);
     HFE_TRY(build_pcg_graph<R>(h, ls, m));
     bool done = false;
@@ -244,7 +246,16 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
       it += m;
       HFE_TRY(read_status(h));
       if (h->h_sc->done || h->h_sc->rr <= target) { done = true; break; }
-      if (h->h_sc->breakdown) return fail(h, HFE_EPCG, "CG breakdown (p.Ap <= 0 or non-finite)");
+      if (h->h_sc->breakdown) {
+        // negative curvature (p.Ap <= 0): the kernels froze x at the last iterate; truncated
+        // CG (Steihaug) returns it as an inexact Newton direction when allowed
+        if (h->allow_truncated && h->h_sc->iters > 0 && std::isfinite(h->h_sc->rr)) {
+          h->pcg_truncated = true;
+          done = true;
+          break;
+        }
+        return fail(h, HFE_EPCG, "CG breakdown (p.Ap <= 0 or non-finite)");
+      }
     }
     if (!done) {
       if (iters_out) *iters_out = it;
@@ -290,6 +301,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->local_tol = 1e-14;
   o->ckpt_every = 1;
   o->predictor = 1;
+  o->ew_forcing = 0;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
@@ -607,7 +619,11 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   std::memset(&loc, 0, sizeof(loc));
   const bool u_out_dev = is_device_ptr(u_out_dev_or_host);
   for (int n = 0; n < n_steps; ++n) {
-    double ref = -1.0, prev = 0.0;
+    double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
+    double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
+    bool last_tight = !h->opt.predictor || !h->opt.ew_forcing;   // the predictor solve is loose
+    bool force_tight = false;
+    int backtracks = 0;
     const double t_prev = h->t_state;
     if (h->opt.predictor) {
       // tangent predictor on the converged start-of-step state (u_{n-1}, h_{n-1}):
@@ -633,13 +649,19 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
       if (h->h_sc->norm2 > 0.0) {
         cudaEventRecord(h->t0, h->s);
-        HFE_TRY(solve_any(h, h->b64, 1.0, nullptr));
+        if (h->opt.ew_forcing) h->pcg_rtol_now = std::max(h->opt.pcg_rtol, 1e-3);   // predictor: rough solve
+        h->allow_truncated = true;
+        hfe_status pst = solve_any(h, h->b64, 1.0, nullptr);
+        h->allow_truncated = false;
+        h->pcg_rtol_now = 0.0;
+        HFE_TRY(pst);
         cudaEventRecord(h->t1, h->s);
         cudaEventSynchronize(h->t1);
         loc.solve_ms += elapsed(h->t0, h->t1);
         loc.pcg_iters += h->h_sc->iters;
         if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
         else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
+        step_scale = 1.0;
       }
     } else {
       set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
@@ -654,6 +676,17 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       HFE_TRY(read_status(h));
       loc.sweeps++;
       loc.sweep_ms += elapsed(h->t0, h->t1);
+      if ((h->h_status->detj > 0 || h->h_status->nonfinite > 0 || h->h_sc->nonfinite > 0) && step_scale > 0.0 &&
+          backtracks < 6) {
+        // the last correction inverted an element or produced non-finite values: halve it
+        const double c = -0.5 * step_scale;
+        if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s, c);
+        else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s, c);
+        step_scale *= 0.5;
+        ++backtracks;
+        --it;
+        continue;
+      }
       HFE_TRY(check_sweep_status(h));
       loc.plastic_gps = h->h_status->plastic;
       loc.max_local_iters = std::max<int32_t>(loc.max_local_iters, (int32_t)h->h_status->max_local_iters);
@@ -661,16 +694,47 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       const double nrm = std::sqrt(h->h_sc->norm2);
       loc.last_residual = nrm;
       if (ref < 0.0) ref = std::max(nrm, h->opt.newton_atol);
-      if (nrm <= h->opt.newton_rtol * ref) { conv = true; break; }
+      if (nrm <= h->opt.newton_rtol * ref) {
+        // accept only after a correction solved to pcg_rtol: with an ill-conditioned K a small
+        // residual after a loose solve can still hide a large error in the soft modes
+        if (last_tight || !h->opt.ew_forcing) { conv = true; break; }
+        force_tight = true;
+      }
+      const bool slow = it >= 1 && nrm > 0.5 * prev;
       if (!h->fp64 && it >= 2) {   // mixed: accept a stagnated residual below newton_stag_tol
-        stall = (nrm > 0.5 * prev) ? stall + 1 : 0;
+        // (only after solves at the tightest tolerance, so an inexact solve cannot stall it)
+        stall = (slow && last_tight) ? stall + 1 : 0;
         if (stall >= 2 && nrm <= h->opt.newton_stag_tol * ref) { conv = true; break; }
       }
       prev = nrm;
       if (it == h->opt.newton_maxit) break;
       int64_t pit = 0;
       cudaEventRecord(h->t0, h->s);
-      HFE_TRY(solve_any(h, h->R, -1.0, &pit));
+      // inexact Newton: Eisenstat-Walker forcing (choice 2, gamma = 0.9, alpha = 2) with their
+      // safeguard, bounded below by pcg_rtol; the converged solution does not depend on it
+      if (h->opt.ew_forcing) {
+        double eta = 1e-3;
+        if (prev_solve > 0.0) {
+          const double ratio = nrm / prev_solve;
+          eta = 0.9 * ratio * ratio;
+          const double safe = 0.9 * eta_prev * eta_prev;
+          if (safe > 0.1) eta = std::max(eta, safe);
+        }
+        eta = std::min(eta, 0.5);
+        if (slow || force_tight) eta = h->opt.pcg_rtol;   // slow progress or final correction: solve tightly
+        eta = std::max(eta, h->opt.pcg_rtol);
+        h->pcg_rtol_now = eta;
+        eta_prev = eta;
+      }
+      prev_solve = nrm;
+      last_tight = !h->opt.ew_forcing || h->pcg_rtol_now <= h->opt.pcg_rtol * 1.0000001;
+      h->allow_truncated = true;
+      h->pcg_truncated = false;
+      hfe_status sst = solve_any(h, h->R, -1.0, &pit);
+      h->allow_truncated = false;
+      h->pcg_rtol_now = 0.0;
+      HFE_TRY(sst);
+      if (h->pcg_truncated) last_tight = false;
       cudaEventRecord(h->t1, h->s);
       cudaEventSynchronize(h->t1);
       loc.solve_ms += elapsed(h->t0, h->t1);
@@ -678,6 +742,8 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       (void)pit;
       if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
       else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
+      step_scale = 1.0;
+      backtracks = 0;
       loc.newton_iters++;
     }
     if (!conv) {

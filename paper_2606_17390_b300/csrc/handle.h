@@ -76,6 +76,9 @@ struct hfe_handle {
   double* tmp64 = nullptr;     // n_dof doubles
   double* b64 = nullptr;       // n_dof doubles (predictor right-hand side)
   double t_state = 0.0;        // load factor of the stored state
+  double pcg_rtol_now = 0.0;   // CG tolerance of the current Newton solve (0: opt.pcg_rtol)
+  bool allow_truncated = false;  // Newton solves may stop at negative curvature
+  bool pcg_truncated = false;
   double* sigma = nullptr;     // n_gp * 6, allocated on demand
   // pinned host mirrors of the device scalars
   PcgScalars* h_sc = nullptr;

@@ -326,9 +326,9 @@ __global__ void __launch_bounds__(kBlock) free_norm_kernel(const double* __restr
 
 template <typename R>
 __global__ void add_update_kernel(double* __restrict__ u, const R* __restrict__ x, const uint8_t* __restrict__ freem,
-                                  int64_t n_dof) {
+                                  double c, int64_t n_dof) {
   const int64_t d = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (d < n_dof && freem[d]) u[d] += (double)x[d];
+  if (d < n_dof && freem[d]) u[d] += c * (double)x[d];
 }
 
 __global__ void set_dirichlet_kernel(double* __restrict__ u, const int64_t* __restrict__ dof,
@@ -411,8 +411,8 @@ void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars
 }
 
 template <typename R>
-void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s) {
-  add_update_kernel<R><<<nblk(n_dof, kBlock), kBlock, 0, s>>>(u, x, freem, n_dof);
+void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s, double c) {
+  add_update_kernel<R><<<nblk(n_dof, kBlock), kBlock, 0, s>>>(u, x, freem, c, n_dof);
 }
 
 void set_dirichlet(double* u, const int64_t* dof, const double* val, double t, int64_t n_fixed, cudaStream_t s) {
@@ -448,7 +448,7 @@ template void precond_setup<float>(const Csr&, const float*, const int64_t*, con
                                    cudaStream_t);
 template void precond_setup<double>(const Csr&, const double*, const int64_t*, const uint8_t*, double*, int, int*,
                                     cudaStream_t);
-template void add_update<float>(double*, const float*, const uint8_t*, int64_t, cudaStream_t);
-template void add_update<double>(double*, const double*, const uint8_t*, int64_t, cudaStream_t);
+template void add_update<float>(double*, const float*, const uint8_t*, int64_t, cudaStream_t, double);
+template void add_update<double>(double*, const double*, const uint8_t*, int64_t, cudaStream_t, double);
 
 }  // namespace hfe

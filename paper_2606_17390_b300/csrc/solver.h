@@ -52,8 +52,9 @@ void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const 
 // ||R_free||^2 into sc->norm2 and, if out != nullptr, ||R_free|| into *out (device)
 void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,
                cudaStream_t s, double* out);
+// u += c x on the free dofs
 template <typename R>
-void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s);
+void add_update(double* u, const R* x, const uint8_t* freem, int64_t n_dof, cudaStream_t s, double c = 1.0);
 void set_dirichlet(double* u, const int64_t* dof, const double* val, double t, int64_t n_fixed, cudaStream_t s);
 void to_double(const float* a, double* b, int64_t n, cudaStream_t s);
 void to_float(const double* a, float* b, int64_t n, cudaStream_t s);

@@ -22,7 +22,7 @@ __all__ = [
     "clamp_displace_bcs", "config0_problem", "config1_problem", "config2_problem",
     "config2h_problem", "config1_material", "config0_material", "load_factors",
     "random_deformation_gradients", "random_history", "distorted_box_mesh",
-    "hill_from_r_values", "compression_state",
+    "hill_from_r_values", "compression_state", "config3_problem", "perturbed_theta", "noise",
 ]
 
 
@@ -266,6 +266,28 @@ def compression_state(mesh: Mesh, t: float, strain: float = 0.1, bulge: float = 
     hist[2] = G * alpha
     hist[6] = alpha
     return u, hist
+
+
+def config3_problem(nx: int = 200, ny: int = 100, nz: int = 4, n_steps: int = 20):
+    """Config-1 mesh and loading with the nine uniform parameters of the gradient check
+    (F, G, H, L, M, N, K, eps0, n): Swift hardening with the config-0 values as the 'true'
+    set.  Returns (mesh, bc, material_true, t)."""
+    mesh, bc, _, ts = config1_problem(nx, ny, nz, n_steps)
+    return mesh, bc, config0_material(), ts
+
+
+def perturbed_theta(theta_true, seed: int = 4, rel: float = 0.2, indices=(2, 3, 4, 5, 6, 7, 8, 9, 10)):
+    """theta_true * (1 + rel * U(-1, 1)) on the given parameter indices (seeded)."""
+    rng = np.random.default_rng(seed)
+    th = np.array(theta_true, dtype=np.float64)
+    idx = np.asarray(indices)
+    th[..., idx] = th[..., idx] * (1.0 + rel * rng.uniform(-1.0, 1.0, size=th[..., idx].shape))
+    return th
+
+
+def noise(shape, scale: float, seed: int = 3) -> np.ndarray:
+    """Gaussian noise N(0, scale^2) of the given shape (seeded), added to target fields."""
+    return scale * np.random.default_rng(seed).standard_normal(shape)
 
 
 def hill_from_r_values(r11, r22, r33, r12, r23, r13):
