@@ -42,9 +42,11 @@ LOAD = 0.5
 # rotated gradients 0.4k, algorithmic tangent in the eigenbasis of C 1.7k, dP/dF 1.0k,
 # element contraction with the symmetric K^e 3.4k); see the design doc.
 ALG_FLOPS_PER_GP = 8.3e3
-# algorithmic DRAM bytes per element of a mixed tangent sweep: conn 32, nodal X and u 48,
-# history in 448 and out 448, R 24, K 27 blocks x 36 B = 972
-ALG_BYTES_PER_EL = 32 + 48 + 448 + 448 + 24 + 972
+# algorithmic DRAM bytes per element of a mixed tangent sweep (one node per element on a
+# large structured mesh): conn 32, nodal X (FP32) 12 and u (FP64) 24, history in and out
+# 8 Gauss points x (7 FP32 values + the FP64 sigma_y cache) = 288 each, R 24, K 27 blocks
+# x 36 B = 972
+ALG_BYTES_PER_EL = 32 + 12 + 24 + 288 + 288 + 24 + 972
 
 
 def _peaks():
@@ -165,6 +167,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64 comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
+    ap.add_argument("--adjoint-nx", type=int, default=200, help="plate resolution of the adjoint ratio run (0 = skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=20)
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
     args = ap.parse_args()
 
@@ -331,6 +335,32 @@ def main():
     else:
         solver.close()
 
+    # adjoint/forward time ratio (second part of the metric) on the config-3 problem: perforated
+    # plate, Swift parameters perturbed by +-20 %, noisy synthetic target; the gradient call runs
+    # its own forward pass (mixed, each step ending with an FP64 Newton iteration) and the FP64
+    # reverse sweep
+    adjoint = None
+    if args.adjoint_nx > 0:
+        m3, bc3, mat3, t3 = inputs.config3_problem(args.adjoint_nx, args.adjoint_nx // 2,
+                                                   4 if args.adjoint_nx >= 200 else 2, args.adjoint_steps)
+        with hfe.from_inputs(m3, bc3, mat3, precision="mixed", stream=stream.cuda_stream) as s3:
+            u_true, _ = s3.forward(t3)
+        u_gt = u_true + inputs.noise(u_true.shape, 1e-3 * np.abs(u_true).max())
+        th_eval = inputs.perturbed_theta(mat3.theta_vector())
+        with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th_eval, stream=stream.cuda_stream) as s3:
+            s3.set_state(None, None)
+            t0 = time.perf_counter()
+            _, fst = s3.forward(t3, want_u=False)
+            t_fwd = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            J3, g3, ast = s3.adjoint(t3, u_gt)
+            t_adj = time.perf_counter() - t0
+        adjoint = {"workload": f"perforated plate {args.adjoint_nx}x{args.adjoint_nx // 2} ({m3.n_el} elements, "
+                               f"{m3.n_dof} dofs), {args.adjoint_steps} steps, 9 Swift/Hill parameters",
+                   "forward_s": t_fwd, "gradient_call_s": t_adj, "reverse_s": ast["solve_ms"] * 1e-3,
+                   "gradient_over_forward": t_adj / t_fwd, "reverse_over_forward": ast["solve_ms"] * 1e-3 / t_fwd,
+                   "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist)
@@ -348,7 +378,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
-                "pcg": pcg,
+                "pcg": pcg, "adjoint": adjoint,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

@@ -56,7 +56,8 @@ typedef enum {
   HFE_EDETJ = -4,       /* an element has det(dX/dxi) <= 0 or det F <= 0 */
   HFE_ENEWTON = 1,      /* global Newton did not converge within newton_maxit */
   HFE_ELOCAL = 2,       /* a local return mapping did not converge (count in stats) */
-  HFE_EPCG = 3,         /* Krylov solve did not reach pcg_rtol within pcg_maxit */
+  HFE_EPCG = 3,         /* Krylov solve did not reach pcg_rtol within pcg_maxit, broke down, or (hfe_solve)
+                           the matrix has diagonal blocks that are not positive definite */
   HFE_ENONFINITE = 4    /* a non-finite value appeared in a residual, stress or solve */
 } hfe_status;
 

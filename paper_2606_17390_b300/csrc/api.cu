@@ -231,7 +231,11 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   pcg_init<R>(b, bscale, h->freem, v, block3, h->n_nodes, h->sc, h->part, h->s);
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
   HFE_TRY(read_status(h));
-  if (*h->h_bad != 0) return fail(h, HFE_EPCG, "preconditioner: non-positive diagonal (block)");
+  // a Newton correction may run on a tangent that is indefinite at some nodes (the surrogate
+  // blocks keep the preconditioner SPD and truncated CG stops at negative curvature); a plain
+  // solve of a matrix that is not SPD is refused
+  if (*h->h_bad != 0 && !h->allow_truncated)
+    return fail(h, HFE_EPCG, "preconditioner: " + std::to_string(*h->h_bad) + " diagonal blocks not positive definite");
   const double rr0 = h->h_sc->rr0;
   if (!std::isfinite(rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
   int64_t it = 0;

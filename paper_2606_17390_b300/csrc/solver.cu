@@ -260,6 +260,11 @@ __global__ void __launch_bounds__(kBlock) pcg_init_kernel(const double* __restri
 
 // Preconditioner from the diagonal blocks of Kt (fixed rows/columns dropped, unit diagonal):
 // Jacobi = 1 / diag, block3 = inverse of the 3x3 diagonal block (cofactors, FP64).
+__device__ __forceinline__ double surrogate_inv(double d) {
+  const double a = fabs(d);
+  return (a > 0.0 && isfinite(a)) ? 1.0 / a : 1.0;
+}
+
 template <typename R>
 __global__ void precond_kernel(const R* __restrict__ vals, const int64_t* __restrict__ diag_slot,
                                const uint8_t* __restrict__ freem, R* __restrict__ minv, int block3,
@@ -275,11 +280,14 @@ __global__ void precond_kernel(const R* __restrict__ vals, const int64_t* __rest
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) M[i][j] = (f[i] && f[j]) ? (double)B[3 * i + j] : (i == j ? 1.0 : 0.0);
+  // A block (or diagonal entry) that is not positive definite is counted in *bad and replaced by
+  // the positive surrogate diag(1/|M_ii|), so that the preconditioner stays SPD; the host either
+  // rejects the solve or, for a Newton correction that may stop at negative curvature, goes on.
   if (!block3) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       if (!(M[i][i] > 0.0)) atomicAdd(bad, 1);
-      minv[3 * n + i] = (R)(1.0 / M[i][i]);
+      minv[3 * n + i] = (R)surrogate_inv(M[i][i]);
     }
     return;
   }
@@ -287,7 +295,15 @@ __global__ void precond_kernel(const R* __restrict__ vals, const int64_t* __rest
   double c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
   double c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
   double det = M[0][0] * c00 + M[0][1] * c01 + M[0][2] * c02;
-  if (!(det > 0.0)) atomicAdd(bad, 1);
+  // Sylvester's criterion on the leading minors
+  if (!(M[0][0] > 0.0) || !(M[0][0] * M[1][1] - M[0][1] * M[1][0] > 0.0) || !(det > 0.0)) {
+    atomicAdd(bad, 1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) minv[9 * n + 3 * i + j] = (R)(i == j ? surrogate_inv(M[i][i]) : 0.0);
+    return;
+  }
   double id = 1.0 / det;
   double I[3][3];
   I[0][0] = c00 * id;
