@@ -280,3 +280,29 @@ def from_inputs(mesh, bc, mat, precision="fp64", theta=None, **options):
     th = mat.theta_vector() if theta is None else theta
     return Solver(mesh.X, mesh.conn, bc.dof, bc.value, th, mat.hardening, mat.Theta, precision=precision,
                   **options)
+
+
+FREE_NORM_STATIC_MAX_DOF = 4194304   # HFE_FREE_NORM_STATIC_MAX_DOF of include/hfe.h
+
+
+def free_norm_static(r, free_mask, norm_out, stream=None):
+    """||r_free||_2 into norm_out[0] through hfe_free_norm_static, which needs no handle and
+    allocates no device memory (its reduction scratch is a static device array of the library).
+    r: float64 CUDA tensor [n], free_mask: uint8 CUDA tensor [n] (0 = Dirichlet dof),
+    norm_out: float64 CUDA tensor [>= 1], all on the current device; stream: a cudaStream_t
+    handle (int) or None for the legacy default stream.  Asynchronous on that stream.  Calls
+    that overlap on one device race on the shared scratch."""
+    L = lib()
+    f = L.hfe_free_norm_static
+    f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    n = int(r.numel()) if hasattr(r, "numel") else int(np.asarray(r).size)
+    st = f(_ptr(r), _ptr(free_mask), n, _ptr(norm_out), stream)
+    if st != 0:
+        if n > FREE_NORM_STATIC_MAX_DOF:
+            msg = f"n = {n} exceeds the static scratch limit of {FREE_NORM_STATIC_MAX_DOF} dofs"
+        elif st == -1:
+            msg = "invalid argument (r, free_mask and norm_out must be device memory of the current device)"
+        else:
+            msg = "CUDA error in set-up or launch"
+        raise HfeError(st, "hfe_free_norm_static: " + msg)
