@@ -35,6 +35,10 @@ template <> struct Num<float> {
   __device__ static float log1p_(float x) { return log1pf(x); }
   __device__ static float sqrt_(float x) { return sqrtf(x); }
   __device__ static float rsqrt_(float x) { return rsqrtf(x); }
+  // FP32 quotients of the mixed path: the hardware reciprocal times a (within 2 ulp for the
+  // normal-range divisors met here), far inside the mixed tolerances, instead of the
+  // correctly rounded division with its slow-path branch
+  __device__ static float div(float a, float b) { return __fdividef(a, b); }
 };
 template <> struct Num<double> {
   static constexpr double jac_eps2 = 1e-30;
@@ -43,6 +47,7 @@ template <> struct Num<double> {
   __device__ static double log1p_(double x) { return log1p(x); }
   __device__ static double sqrt_(double x) { return sqrt(x); }
   __device__ static double rsqrt_(double x) { return rsqrt(x); }
+  __device__ static double div(double a, double b) { return a / b; }
 };
 
 // ----------------------------------------------------------------------------------------
@@ -66,10 +71,10 @@ __device__ __forceinline__ void jacobi3(R A[3][3], R w[3], R V[3][3]) {
       const int r = 3 - p - q;
       R apq = A[p][q];
       if (apq != R(0)) {
-        R theta = (A[q][q] - A[p][p]) / (R(2) * apq);
+        R theta = Num<R>::div(A[q][q] - A[p][p], R(2) * apq);
         R at = fabs(theta);
-        R t = (at > R(1e15)) ? R(0.5) / theta
-                             : (theta >= R(0) ? R(1) : R(-1)) / (at + Num<R>::sqrt_(theta * theta + R(1)));
+        R t = (at > R(1e15)) ? Num<R>::div(R(0.5), theta)
+                             : Num<R>::div(theta >= R(0) ? R(1) : R(-1), at + Num<R>::sqrt_(theta * theta + R(1)));
         R c = Num<R>::rsqrt_(t * t + R(1));
         R s = t * c;
         A[p][p] -= t * apq;
@@ -124,11 +129,11 @@ __device__ __forceinline__ void mandel_rotation(const R Q[3][3], R Rm[6][6]) {
 template <typename R>
 __device__ __forceinline__ R dd1(R ea, R eb) {
   R lb = R(1) + R(2) * eb;
-  R x = (R(2) * (ea - eb)) / lb;
+  R x = Num<R>::div(R(2) * (ea - eb), lb);
   R L;
   if (fabs(x) < Num<R>::dd1_series) L = R(1) + x * (R(-0.5) + x * (R(1) / R(3) + x * R(-0.25)));
-  else L = Num<R>::log1p_(x) / x;
-  return L / (R(2) * lb);
+  else L = Num<R>::div(Num<R>::log1p_(x), x);
+  return Num<R>::div(L, R(2) * lb);
 }
 
 // Second divided difference of f(l) = 1/2 ln l on the sorted multiset l_i <= l_j <= l_k:
@@ -138,10 +143,10 @@ template <typename R>
 __device__ __forceinline__ R dd2(R ei, R ej, R ek, R f_kj, R f_ji) {
   R li = R(1) + R(2) * ei, lj = R(1) + R(2) * ej;
   R den = R(2) * (ek - ei);
-  if (den > Num<R>::dd2_tau * lj) return (f_kj - f_ji) / den;
+  if (den > Num<R>::dd2_tau * lj) return Num<R>::div(f_kj - f_ji, den);
   R m = lj + (R(2) / R(3)) * (ei + ek - R(2) * ej);
   (void)li;
-  return R(-0.25) / (m * m);
+  return Num<R>::div(R(-0.25), m * m);
 }
 
 // ----------------------------------------------------------------------------------------

@@ -30,13 +30,46 @@ namespace {
 
 constexpr int kElemsPerCta = 16;
 constexpr int kThreads = 128;
-constexpr int kGpStride = 81;    // shared words per Gauss point: A 45 (major-symmetric), P 9, g 24, pad 3
-constexpr int kOffP = 45;
-constexpr int kOffG = 54;
-// per element: 648 = 8 mod 32, so the 4 elements of a warp read from banks 0, 8, 16, 24 in
-// phase 2, and the 32 Gauss points of a warp (offsets 8 le + 17 g mod 32) write to 32
-// distinct banks in phase 1
-constexpr int kElStride = 8 * kGpStride;
+// shared words per Gauss point: A 45 (major-symmetric) + pad 3, P 9 + pad 3, g 24; every
+// section starts on a 16-byte boundary, so phase 1 stores and phase 2 loads A and P as
+// 4-vectors
+constexpr int kGpStride = 84;
+constexpr int kOffP = 48;
+constexpr int kOffG = 60;
+// per element 680 = 8 mod 32 words: the 4 elements of a warp read g from banks offset by 0,
+// 8, 16, 24 in phase 2 (conflict-free scalar loads); the 8 Gauss points of one element (one
+// quarter-warp phase of a 16-byte store) start at 20 g mod 32 words: distinct bank quads
+constexpr int kElStride = 8 * kGpStride + 8;
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); completion
+// is awaited by cp_async_wait_all in the copying thread, then made visible by a barrier
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// 4-vector shared-memory stores and loads of R values (16-byte aligned addresses)
+template <typename R> struct V4;
+template <> struct V4<float> {
+  __device__ static void st(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  }
+  __device__ static void ld(const float* p, float* v) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+};
+template <> struct V4<double> {
+  __device__ static void st(double* p, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+  }
+  __device__ static void ld(const double* p, double* v) {
+    const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+};
 
 using namespace gpm;
 
@@ -49,9 +82,9 @@ struct HardInc {
   float p2, z_or_A, syn;   // Swift: n, eps0 + alpha_n, sy_n ; Voce: b, A, sy_n
   __device__ __forceinline__ void eval(float da, float& inc, float& dsy) const {
     if (type == HFE_HARDENING_SWIFT) {
-      float g = expm1f(p2 * log1pf(da / z_or_A));
+      float g = expm1f(p2 * log1pf(__fdividef(da, z_or_A)));
       inc = syn * g;
-      dsy = p2 * (syn + inc) / (z_or_A + da);
+      dsy = __fdividef(p2 * (syn + inc), z_or_A + da);
     } else {
       float em = expm1f(-p2 * da);
       inc = -z_or_A * em;
@@ -74,7 +107,7 @@ __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv,
                                float hmin, const HardInc& inc, double syn64, float ftr, int maxit) {
   RM out;
   const float sq23 = (float)kSq23;
-  float dg = 0.0f, lo = 0.0f, hi = ftr / (2.0f * mu * hmin);
+  float dg = 0.0f, lo = 0.0f, hi = __fdividef(ftr, 2.0f * mu * hmin);
   float dr = -1.0f;
   int k = 0;
   bool ok = false;
@@ -82,23 +115,24 @@ __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv,
     float incv, dsy;
     inc.eval(sq23 * dg, incv, dsy);
     float phy = sq23 * (inc.syn + incv), dphy = (2.0f / 3.0f) * dsy;
-    float s = 2.0f * mu * dg / phy;
-    float ds = 2.0f * mu * (phy - dg * dphy) / (phy * phy);
+    const float iphy = __fdividef(1.0f, phy);
+    float s = 2.0f * mu * dg * iphy;
+    float ds = 2.0f * mu * (phy - dg * dphy) * iphy * iphy;
     float phi2 = 0.0f, acc = 0.0f;
 #pragma unroll
     for (int i = 1; i < 6; ++i) {
-      float d = 1.0f + s * hfv.v[i];
-      float Ti = t[i] / d;
+      const float rd = __fdividef(1.0f, 1.0f + s * hfv.v[i]);
+      float Ti = t[i] * rd;
       float hT = hfv.v[i] * Ti;
       phi2 += hT * Ti;
-      acc += hT * hT / d;
+      acc += hT * hT * rd;
     }
     float phi = sqrtf(phi2);
     float r = phi - phy;
-    dr = -(acc / phi) * ds - dphy;
+    dr = -__fdividef(acc, phi) * ds - dphy;
     if (fabsf(r) <= 1e-6f * phy) { ok = true; break; }
     if (r > 0.0f) lo = dg; else hi = dg;
-    float dgn = dg - r / dr;
+    float dgn = dg - __fdividef(r, dr);
     if (!(dgn > lo && dgn < hi)) dgn = 0.5f * (lo + hi);
     if (fabsf(dgn - dg) <= 1e-7f * dg) { dg = dgn; ok = true; break; }
     dg = dgn;
@@ -118,7 +152,7 @@ __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv,
     phi2 = fma(hv.v[i] * Ti, Ti, phi2);
   }
   double rt = phi2 - phy * phy;
-  float corr = (float)rt / (2.0f * (float)phy * dr);
+  float corr = __fdividef((float)rt, 2.0f * (float)phy * dr);
   dg64 -= (double)corr;
   if (dg64 < 0.0) dg64 = 0.0;
   inc.eval(sq23 * (float)dg64, incv, dsy);
@@ -152,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sNode = reinterpret_cast<R*>(smem_raw);                     // [16][8][6]: dX(3), du(3)
   R* sGp = sNode + kElemsPerCta * 8 * 6;                           // [16][kElStride]
+  int32_t* sSlot = reinterpret_cast<int32_t*>(sGp + kElemsPerCta * kElStride);   // [16][64]
 
   const int tid = threadIdx.x;
   const int le = tid >> 3;
@@ -165,6 +200,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
   using MR = typename MatOf<R>::T;
   const MR* matR = reinterpret_cast<const MR*>(a.mat);
   const int mi = a.mat_per_element ? e : 0;
+
+  // the element's 64 slot-map entries (used by phase 2), copied to shared memory while
+  // phase 1 runs: 16 chunks of 16 bytes, two per thread of the element
+  if (valid) {
+    const int32_t* srow = a.slot + (int64_t)e * 64;
+    cp_async16(sSlot + le * 64 + 4 * g, srow + 4 * g);
+    cp_async16(sSlot + le * 64 + 4 * (g + 8), srow + 4 * (g + 8));
+  }
 
   // history of this Gauss point, loaded first so that it arrives during the kinematics
   const int64_t ng = a.n_gp;
@@ -183,11 +226,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     for (int c = 0; c < 6; ++c) epn[c] = R(0);
   }
 
+  int node;   // node g of element e (also row a = g of phase 2)
   // ---- S1 gather: node g of element e; coordinates and displacements relative to node 0
   // (displacement differences taken in FP64, then rounded to R; the mixed path reads the
   // element's coordinate differences, rounded once at set-up)
   {
-    int node = valid ? a.conn[(int64_t)e * 8 + g] : 0;
+    node = valid ? a.conn[(int64_t)e * 8 + g] : 0;
     double u0 = a.u[3 * (int64_t)node], u1 = a.u[3 * (int64_t)node + 1], u2 = a.u[3 * (int64_t)node + 2];
     const int src = lane & 24;
     double bu0 = __shfl_sync(gmask, u0, src), bu1 = __shfl_sync(gmask, u1, src), bu2 = __shfl_sync(gmask, u2, src);
@@ -239,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     R c02 = J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0];
     R det0 = J0[0][0] * c00 + J0[0][1] * c01 + J0[0][2] * c02;
     if (!(det0 > R(0))) flag_detj = 1;
-    R id = R(1) / det0;
+    R id = Num<R>::div(R(1), det0);
     R Ji[3][3];   // inverse of J0: Ji[j][k] = d xi_j / d X_k
     Ji[0][0] = c00 * id;
     Ji[1][0] = c01 * id;
@@ -399,11 +443,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     R s_pl = R(0), phy = R(1);
     if (plastic) {
       phy = (R)(kSq23 * rm.syn1);
-      s_pl = R(2) * mu * (R)rm.dgamma / phy;
+      s_pl = Num<R>::div(R(2) * mu * (R)rm.dgamma, phy);
     }
     Teig[0] = t[0];
 #pragma unroll
-    for (int i = 1; i < 6; ++i) Teig[i] = plastic ? t[i] / (R(1) + s_pl * (R)m.h[i]) : t[i];
+    for (int i = 1; i < 6; ++i) Teig[i] = plastic ? Num<R>::div(t[i], R(1) + s_pl * (R)m.h[i]) : t[i];
     R TM[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -418,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
         R neig[6];
         neig[0] = R(0);
 #pragma unroll
-        for (int i = 1; i < 6; ++i) neig[i] = (R)m.h[i] * Teig[i] / phy;
+        for (int i = 1; i < 6; ++i) neig[i] = Num<R>::div((R)m.h[i] * Teig[i], phy);
         const R dgR = (R)rm.dgamma;
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
@@ -464,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
       for (int bb = aa; bb < 3; ++bb) {
-        R v = (aa == bb) ? R(0.5) / (R(1) + R(2) * ev[aa]) : dd1<R>(ev[bb], ev[aa]);
+        R v = (aa == bb) ? Num<R>::div(R(0.5), R(1) + R(2) * ev[aa]) : dd1<R>(ev[bb], ev[aa]);
         f1[aa][bb] = f1[bb][aa] = v;
       }
     R Sh[3][3];
@@ -480,15 +524,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
       for (int j = 0; j < 3; ++j) Ft[i][j] = F[i][0] * Q[0][j] + F[i][1] * Q[1][j] + F[i][2] * Q[2][j];
     R* gp = sGp + (size_t)le * kElStride + g * kGpStride;
     const R wd = det0;
+    {
+      R gq[24];
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
+      for (int n = 0; n < 8; ++n)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) gp[kOffG + n * 3 + j] = gN[n][0] * Q[0][j] + gN[n][1] * Q[1][j] + gN[n][2] * Q[2][j];
+        for (int j = 0; j < 3; ++j) gq[n * 3 + j] = gN[n][0] * Q[0][j] + gN[n][1] * Q[1][j] + gN[n][2] * Q[2][j];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 6; ++k) V4<R>::st(gp + kOffG + 4 * k, gq[4 * k], gq[4 * k + 1], gq[4 * k + 2], gq[4 * k + 3]);
+      R pq[12];
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        gp[kOffP + i * 3 + j] = wd * (Ft[i][0] * Sh[0][j] + Ft[i][1] * Sh[1][j] + Ft[i][2] * Sh[2][j]);
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) pq[i * 3 + j] = wd * (Ft[i][0] * Sh[0][j] + Ft[i][1] * Sh[1][j] + Ft[i][2] * Sh[2][j]);
+      pq[9] = pq[10] = pq[11] = R(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) V4<R>::st(gp + kOffP + 4 * k, pq[4 * k], pq[4 * k + 1], pq[4 * k + 2], pq[4 * k + 3]);
+    }
     if (a.sigma != nullptr) {   // Cauchy stress sigma = P F^T / J, P = Ftilde Shat Q^T
       R P[3][3];
 #pragma unroll
@@ -504,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
       for (int p = 0; p < 6; ++p) {
         const int i = pI(p), j = pJ(p);
         R s = P[i][0] * F[j][0] + P[i][1] * F[j][1] + P[i][2] * F[j][2];
-        a.sigma[gpi * 6 + p] = (double)(s / detF);
+        a.sigma[gpi * 6 + p] = (double)Num<R>::div(s, detF);
       }
     }
 
@@ -522,19 +574,20 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
         // implicit function theorem on Eq. local_cpp (App. D) in the Hill eigenbasis:
         // Xi^-1 = E^-1 + dgamma (H - N (x) N) / phi, D = Xi - (Xi N)(Xi N)^T / (N Xi N + 2/3 H')
         const R dgR = (R)rm.dgamma;
-        const R cph = dgR / phy;
-        R nv[6], Dd[6], pv[6];
+        const R iphy = Num<R>::div(R(1), phy);
+        const R cph = dgR * iphy;
+        R nv[6], iDd[6], pv[6];
         R npn = R(0);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
           const R hi = (R)m.h[i];
-          nv[i] = (i == 0) ? R(0) : hi * Teig[i] / phy;
+          nv[i] = (i == 0) ? R(0) : hi * Teig[i] * iphy;
           const R ei = (i == 0) ? (R)m.kap3 : R(2) * mu;
-          Dd[i] = R(1) / ei + cph * hi;
-          pv[i] = nv[i] / Dd[i];
+          iDd[i] = Num<R>::div(R(1), Num<R>::div(R(1), ei) + cph * hi);
+          pv[i] = nv[i] * iDd[i];
           npn += nv[i] * pv[i];
         }
-        const R kap = cph / (R(1) - cph * npn);
+        const R kap = Num<R>::div(cph, R(1) - cph * npn);
         const R qf = R(1) + kap * npn;
         R qv[6];
         R nqn = R(0);
@@ -561,14 +614,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
           Wp[p] = s1;
           Wq[p] = s2;
         }
-        const R ib = R(1) / beta;
+        const R ib = Num<R>::div(R(1), beta);
 #pragma unroll
         for (int p = 0; p < 6; ++p)
 #pragma unroll
           for (int q = p; q < 6; ++q) {
             R s = R(0);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) s += W[p][j] * W[q][j] / Dd[j];
+            for (int j = 0; j < 6; ++j) s += W[p][j] * W[q][j] * iDd[j];
             s += kap * Wp[p] * Wp[q] - ib * Wq[p] * Wq[q];
             Dh[p][q] = Dh[q][p] = s;
           }
@@ -617,6 +670,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
 #pragma unroll
           for (int q = 0; q < 6; ++q)
             Xt[i][J][q] = Ft[i][0] * Ct[pidx(0, J)][q] + Ft[i][1] * Ct[pidx(1, J)][q] + Ft[i][2] * Ct[pidx(2, J)][q];
+      R av[48];
 #pragma unroll
       for (int P = 0; P < 9; ++P)
 #pragma unroll
@@ -624,8 +678,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
           const int i = P / 3, J = P % 3, k = Qi / 3, L = Qi % 3;
           R s = Xt[i][J][pidx(0, L)] * Ft[k][0] + Xt[i][J][pidx(1, L)] * Ft[k][1] + Xt[i][J][pidx(2, L)] * Ft[k][2];
           if (i == k) s += Sh[J][L];
-          gp[asym(P, Qi)] = wd * s;
+          av[asym(P, Qi)] = wd * s;
         }
+      av[45] = av[46] = av[47] = R(0);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) V4<R>::st(gp + 4 * k, av[4 * k], av[4 * k + 1], av[4 * k + 2], av[4 * k + 3]);
     }
   }
 
@@ -644,7 +701,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
       if (mx > 0) atomicMax(&a.status->max_local_iters, mx);
     }
   }
-  __syncthreads();
+  // an element's shared data (Gauss-point records, slot rows) is written and read by its own
+  // 8 threads, all in one warp: a warp barrier suffices, and warps move on independently
+  cp_async_wait_all();
+  __syncwarp();
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
   if (!valid) return;
@@ -664,9 +724,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
       for (int c = 0; c < 9; ++c) Kr[d][c] = R(0);
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
-      const R* A = G + q * kGpStride;
-      const R* gt = A + kOffG;
+      const R* Aq = G + q * kGpStride;
+      const R* gt = Aq + kOffG;
       const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
+      R A[48];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) V4<R>::ld(Aq + 4 * k, A + 4 * k);
       R U[3][3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
@@ -687,12 +750,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
             for (int k = 0; k < 3; ++k) Kr[d][i * 3 + k] += U[i][k][0] * gb0 + U[i][k][1] * gb1 + U[i][k][2] * gb2;
         }
       }
-      const R* P = A + kOffP;
+      R P[12];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffP + 4 * k, P + 4 * k);
 #pragma unroll
       for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
     }
     R* Kv = reinterpret_cast<R*>(a.K);
-    const int32_t* sl = a.slot + (int64_t)e * 64;
+    const int32_t* sl = sSlot + le * 64;
 #pragma unroll
     for (int d = 0; d < kNb; ++d) {
       if (d < nb) {
@@ -719,17 +784,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
   } else {
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
-      const R* A = G + q * kGpStride;
-      const R* gt = A + kOffG;
+      const R* Aq = G + q * kGpStride;
+      const R* gt = Aq + kOffG;
       const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
-      const R* P = A + kOffP;
+      R P[12];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffP + 4 * k, P + 4 * k);
 #pragma unroll
       for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
     }
   }
   {
-    const int node = a.conn[(int64_t)e * 8 + arow];
-    const bool store = a.slot[(int64_t)e * 64 + arow * 9] < 0;   // diagonal block (a, a)
+    // node of row a = g is the node this thread gathered in phase 1
+    const bool store = sSlot[le * 64 + arow * 9] < 0;   // diagonal block (a, a)
     double* Rg = a.R + 3 * (int64_t)node;
     if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
       atomicAdd(&a.status->nonfinite, 1);
@@ -937,7 +1004,8 @@ void launch_hist_export(const void* hist, double* user, bool fp64, int64_t n_gp,
 template <typename R, bool TANGENT, bool UNIF>
 static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cudaStream_t s) {
   using MR = typename MatOf<R>::T;
-  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * kElStride);
+  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * kElStride) +
+                     sizeof(int32_t) * kElemsPerCta * 64;
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
