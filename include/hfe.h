@@ -101,7 +101,8 @@ typedef struct {
 /* Options (hfe_default_options fills the defaults). */
 typedef struct {
   int precision;          /* HFE_PRECISION_FP64 or HFE_PRECISION_MIXED */
-  double newton_rtol;     /* ||R_free|| <= newton_rtol * max(||R_free^0||, newton_atol) */
+  double newton_rtol;     /* ||R_free|| <= newton_rtol * max(||R_free^0||, newton_atol);
+                             default 1e-10 (FP64), 1e-7 (mixed) */
   double newton_atol;
   int newton_maxit;
   double newton_stag_tol; /* mixed only: stagnation accepted below this relative norm */
@@ -122,6 +123,10 @@ typedef struct {
                              CG iterations on well-behaved runs, but loose solves can send the
                              iterates of ill-conditioned meshes astray.  0 (default): every
                              Newton solve to pcg_rtol */
+  int pcg_persistent;     /* 1 (default): each CG solve is one cooperative kernel launch that runs
+                             every iteration on the device (grid barriers, convergence tested each
+                             iteration); 0: chunks of pcg_check_every iterations as CUDA-graph
+                             launches with a host convergence check between chunks */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */

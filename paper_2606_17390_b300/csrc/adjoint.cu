@@ -745,6 +745,7 @@ hfe_status ensure_work(hfe_handle* h, int n_steps) {
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vp = b;
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vq = b;
     HFE_TRY(aalloc(h, w, &b, 9 * (size_t)h->n_nodes)); w->ls.vminv = b;
+    HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vp2 = b;
     w->ls.fp64 = true;
   }
   HFE_TRY(aalloc(h, w, &w->u_all, ndof * n_steps));

@@ -188,6 +188,7 @@ template <typename R>
 PcgVecs<R> vecs(LinSys& ls) {
   PcgVecs<R> v;
   v.x = (R*)ls.vx; v.r = (R*)ls.vr; v.z = (R*)ls.vz; v.p = (R*)ls.vp; v.q = (R*)ls.vq; v.minv = (R*)ls.vminv;
+  v.p2 = (R*)ls.vp2;
   return v;
 }
 
@@ -212,6 +213,39 @@ hfe_status build_pcg_graph(hfe_handle* h, LinSys& ls, int len) {
   return HFE_OK;
 }
 
+// The solve as one cooperative launch (preconditioner set up and scalars zeroed by the
+// caller); the same outcomes as the chunked form below.
+template <typename R>
+hfe_status pcg_solve_persistent(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs<R>& v, int block3, const double* b,
+                                double bscale, int64_t* iters_out) {
+  const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
+  HFE_TRY(cuda_check(h, pcg_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
+                                          h->opt.pcg_maxit, h->sc, h->part, partial_slots(), h->s),
+                     "persistent CG launch"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
+  HFE_TRY(read_status(h));
+  const PcgScalars& sc = *h->h_sc;
+  if (iters_out) *iters_out = sc.iters;
+  if (sc.gs.timeout) return fail(h, HFE_ECUDA, "persistent CG: a grid barrier wait ran out");
+  // a Newton correction may run on a tangent that is indefinite at some nodes (the surrogate
+  // blocks keep the preconditioner SPD and truncated CG stops at negative curvature); a plain
+  // solve of a matrix that is not SPD is refused
+  if (*h->h_bad != 0 && !h->allow_truncated)
+    return fail(h, HFE_EPCG, "preconditioner: " + std::to_string(*h->h_bad) + " diagonal blocks not positive definite");
+  if (!std::isfinite(sc.rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
+  if (sc.done) return HFE_OK;
+  if (sc.breakdown) {
+    // negative curvature (p.Ap <= 0): x holds the last iterate; truncated CG (Steihaug)
+    // returns it as an inexact Newton direction when allowed
+    if (h->allow_truncated && sc.iters > 0 && std::isfinite(sc.rr)) {
+      h->pcg_truncated = true;
+      return HFE_OK;
+    }
+    return fail(h, HFE_EPCG, "CG breakdown (p.Ap <= 0 or non-finite)");
+  }
+  return fail(h, HFE_EPCG, "CG did not converge: |r|/|b| = " + std::to_string(std::sqrt(sc.rr / sc.rr0)));
+}
+
 // Solve Kt x = bscale * b with PCG (b device FP64 [n_dof]); x left in h->vx (precision R).
 template <typename R>
 hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters_out) {
@@ -221,6 +255,7 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
   precond_setup<R>(K, (const R*)ls.K, h->diag_slot, h->freem, v.minv, block3, h->bad, h->s);
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
+  if (h->opt.pcg_persistent) return pcg_solve_persistent<R>(h, ls, K, v, block3, b, bscale, iters_out);
   {
     const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
     const double rt2 = rt * rt;
@@ -293,7 +328,9 @@ extern "C" {
 void hfe_default_options(hfe_options* o, int precision) {
   std::memset(o, 0, sizeof(*o));
   o->precision = precision;
-  o->newton_rtol = precision == HFE_PRECISION_FP64 ? 1e-10 : 1e-6;
+  // mixed: 1e-7 keeps the displacement within ~5e-7 of the exact solution on the 100^3 cube
+  // (1e-6 left 2e-5 - 6e-5 there, above the 1e-5 target)
+  o->newton_rtol = precision == HFE_PRECISION_FP64 ? 1e-10 : 1e-7;
   o->newton_atol = 1.0;
   o->newton_maxit = 25;
   o->newton_stag_tol = 1e-4;
@@ -306,6 +343,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->ckpt_every = 1;
   o->predictor = 1;
   o->ew_forcing = 0;
+  o->pcg_persistent = 1;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
@@ -396,6 +434,7 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vp = b;
     HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vq = b;
     HFE_TRY(dalloc(h, &b, rsz * 9 * h->n_nodes)); h->vminv = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->ls.vp2 = b;
   }
   h->ls.K = h->K;
   h->ls.vx = h->vx; h->ls.vr = h->vr; h->ls.vz = h->vz; h->ls.vp = h->vp; h->ls.vq = h->vq; h->ls.vminv = h->vminv;

@@ -27,6 +27,7 @@ namespace hfe {
 struct LinSys {
   void* K = nullptr;
   void *vx = nullptr, *vr = nullptr, *vz = nullptr, *vp = nullptr, *vq = nullptr, *vminv = nullptr;
+  void* vp2 = nullptr;   // second search direction (persistent CG)
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
   bool fp64 = true;

@@ -369,6 +369,249 @@ __global__ void predictor_rhs_kernel(const double* __restrict__ R_, const R* __r
   b[d] = freem[d] ? -v : 0.0;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Persistent PCG: the whole solve in one cooperative launch.  The rows (nodes) are split in
+// contiguous ranges over the CTAs; every global quantity (p.q, r.z, r.r) is a fixed-order
+// sum of per-CTA partials that every CTA recomputes after a grid barrier, so all CTAs take
+// the same decisions and the result is deterministic.  Two barriers per iteration: the
+// search direction p = z + beta p_prev is formed on the fly inside the SpMV (for the
+// gathered columns from z and the previous direction, for the own rows also stored), with
+// p_prev and p in two buffers that swap each iteration.
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 25;   // x >= 32 ns: about a second
+
+// Grid barrier fused with a reduction: every CTA publishes its partial pair in part, the
+// last CTA to arrive sums all pairs in CTA order (the same fixed order whichever CTA is
+// last) into gs.tot and releases the others, who read the totals.  Waits are bounded;
+// returns false once any wait has run out (sticky), after which every CTA leaves the solve.
+__device__ __forceinline__ bool grid_allreduce(GridSync* gs, const double* part, double& t0, double& t1) {
+  __shared__ int s_last, s_ok;
+  __shared__ double s_t0, s_t1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g0 = *(volatile unsigned*)&gs->gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gs->count, 1u);
+    s_last = arrived == gridDim.x - 1;
+    if (!s_last) {
+      unsigned long long spins = 0;
+      unsigned ns = 32;
+      while (*(volatile unsigned*)&gs->gen == g0) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicExch(&gs->timeout, 1);
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 256) ns *= 2;
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += kBlock) {
+      a += __ldcg(part + 2 * k);
+      b += __ldcg(part + 2 * k + 1);
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+      gs->tot[0] = a;
+      gs->tot[1] = b;
+      gs->count = 0u;
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    }
+  }
+  if (threadIdx.x == 0) {
+    s_t0 = __ldcg(&gs->tot[0]);
+    s_t1 = __ldcg(&gs->tot[1]);
+    s_ok = *(volatile int*)&gs->timeout == 0;
+  }
+  __syncthreads();
+  t0 = s_t0;
+  t1 = s_t1;
+  return s_ok != 0;
+}
+
+template <typename R>
+struct PersistArgs {
+  const int64_t* rowptr;
+  const int32_t* cols;
+  const R* vals;
+  const uint8_t* freem;
+  const R* minv;
+  const double* b;
+  double bscale, rtol2;
+  R *x, *r, *z, *pa, *pb, *q;
+  int64_t n_nodes, maxit;
+  int block3;
+  PcgScalars* sc;
+  double* part;   // 2 buffers x gridDim.x pairs
+};
+
+template <typename R>
+__device__ __forceinline__ void precond_apply(const R* minv, int block3, int64_t n, const R rv[3], R zv[3]) {
+  if (block3) {
+    const R* M = minv + 9 * n;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) zv[i] = M[3 * i] * rv[0] + M[3 * i + 1] * rv[1] + M[3 * i + 2] * rv[2];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) zv[i] = minv[3 * n + i] * rv[i];
+  }
+}
+
+// MINB = CTAs per SM the registers are budgeted for: 4 (64 registers) when the matrix stays
+// in L2 and the solve is latency-bound, 6 (40 registers, more warps in flight) when it
+// streams from HBM.
+template <typename R, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const PersistArgs<R> a) {
+  const int64_t n0 = (int64_t)blockIdx.x * a.n_nodes / gridDim.x;
+  const int64_t n1 = (int64_t)(blockIdx.x + 1) * a.n_nodes / gridDim.x;
+  PcgScalars* sc = a.sc;
+  // publish this CTA's partial pair, then the fused barrier + reduction; the partial
+  // buffers alternate, so a fast CTA never overwrites pairs a slow CTA may still be summing
+  int red = 0;
+  auto allreduce = [&](double v0, double v1, double& t0, double& t1) -> bool {
+    block_sum2(v0, v1);
+    double* pp = a.part + 2 * (size_t)gridDim.x * (red & 1);
+    if (threadIdx.x == 0) {
+      pp[2 * blockIdx.x] = v0;
+      pp[2 * blockIdx.x + 1] = v1;
+    }
+    ++red;
+    return grid_allreduce(&sc->gs, pp, t0, t1);
+  };
+  // r = b on the free dofs, x = 0, z = M^-1 r, p_prev = 0 (beta = 0 in the first iteration)
+  double rz = 0.0, rr = 0.0;
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
+    R rv[3], zv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t d = 3 * n + i;
+      rv[i] = a.freem[d] ? (R)(a.bscale * a.b[d]) : R(0);
+      a.r[d] = rv[i];
+      a.x[d] = R(0);
+      a.pa[d] = R(0);
+    }
+    precond_apply(a.minv, a.block3, n, rv, zv);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a.z[3 * n + i] = zv[i];
+      rz += (double)rv[i] * (double)zv[i];
+      rr += (double)rv[i] * (double)rv[i];
+    }
+  }
+  if (!allreduce(rz, rr, rz, rr)) return;
+  const double rr0 = rr;
+  const double target = a.rtol2 * rr0;
+  int breakdown = (isfinite(rz) && isfinite(rr)) ? 0 : 1;
+  int done = (!breakdown && rr <= target) ? 1 : 0;
+  double beta = 0.0, pq = 0.0;
+  int64_t it = 0;
+  R* pprev = a.pa;
+  R* pcur = a.pb;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int kWarps = kBlock / 32;
+  while (!done && !breakdown && it < a.maxit) {
+    // q = K p with p = z + beta p_prev (rows without the Dirichlet columns: p is zero there)
+    const R bt = (R)beta;
+    double dot = 0.0;
+    for (int64_t r0 = n0 + warp; r0 < n1; r0 += 2 * kWarps) {
+      const int64_t r1 = r0 + kWarps;
+      const bool has1 = r1 < n1;
+      const int64_t b0 = a.rowptr[r0], e0 = a.rowptr[r0 + 1];
+      const int64_t b1 = has1 ? a.rowptr[r1] : 0, e1 = has1 ? a.rowptr[r1 + 1] : 0;
+      const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
+      R acc[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+      const int nmax = nb0 > nb1 ? nb0 : nb1;
+      for (int j = lane; j < nmax; j += 32) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int nb = t == 0 ? nb0 : nb1;
+          if (j < nb) {
+            const int64_t blk = (t == 0 ? b0 : b1) + j;
+            const int64_t col = a.cols[blk];
+            const R* v = a.vals + blk * 9;
+            const R x0 = a.z[3 * col] + bt * pprev[3 * col];
+            const R x1 = a.z[3 * col + 1] + bt * pprev[3 * col + 1];
+            const R x2 = a.z[3 * col + 2] + bt * pprev[3 * col + 2];
+            acc[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
+            acc[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
+            acc[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[t][i] = warp_sum_r(acc[t][i]);
+      if (lane < 6) {
+        const int t = lane / 3, i = lane % 3;
+        if (t == 0 || has1) {
+          const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
+          const R o = t == 0 ? (i == 0 ? acc[0][0] : (i == 1 ? acc[0][1] : acc[0][2]))
+                             : (i == 0 ? acc[1][0] : (i == 1 ? acc[1][1] : acc[1][2]));
+          const R pd = a.z[d] + bt * pprev[d];
+          const R qd = a.freem[d] ? o : R(0);
+          pcur[d] = pd;
+          a.q[d] = qd;
+          dot += (double)pd * (double)qd;
+        }
+      }
+    }
+    double unused;
+    if (!allreduce(dot, 0.0, pq, unused)) return;
+    if (!(pq > 0.0) || !isfinite(pq)) {   // negative curvature or breakdown: x stays at the last iterate
+      breakdown = 1;
+      break;
+    }
+    const R al = (R)(rz / pq);
+    // x += alpha p, r -= alpha q, z = M^-1 r on the own rows
+    double rzn = 0.0, rrn = 0.0;
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
+      R rv[3], zv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t d = 3 * n + i;
+        a.x[d] += al * pcur[d];
+        rv[i] = a.r[d] - al * a.q[d];
+        a.r[d] = rv[i];
+      }
+      precond_apply(a.minv, a.block3, n, rv, zv);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        a.z[3 * n + i] = zv[i];
+        rzn += (double)rv[i] * (double)zv[i];
+        rrn += (double)rv[i] * (double)rv[i];
+      }
+    }
+    if (!allreduce(rzn, rrn, rzn, rrn)) return;
+    ++it;
+    if (!isfinite(rzn) || !isfinite(rrn)) { breakdown = 1; break; }
+    beta = rz > 0.0 ? rzn / rz : 0.0;
+    rz = rzn;
+    rr = rrn;
+    if (rr <= target) done = 1;
+    R* tmp = pprev;
+    pprev = pcur;
+    pcur = tmp;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->rr0 = rr0;
+    sc->pq = pq;
+    sc->target = target;
+    sc->iters = (int)it;
+    sc->breakdown = breakdown;
+    sc->done = done;
+  }
+}
+
 inline unsigned nblk(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 inline unsigned rblk(int64_t n, int per) {   // grid of a reducing (grid-stride) kernel
   int64_t b = (n + per - 1) / per;
@@ -413,6 +656,33 @@ void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>
   pcg_update_kernel<R><<<rblk(K.n_nodes, kBlock), kBlock, 0, s>>>(v.x, v.r, v.z, v.p, v.q, v.minv, block3,
                                                                   K.n_nodes, sc, part);
   pcg_p_kernel<R><<<nblk(3 * K.n_nodes, kBlock), kBlock, 0, s>>>(v.p, v.z, 3 * K.n_nodes, sc);
+}
+
+
+template <typename R>
+cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
+                           const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
+                           double* part, int64_t part_slots, cudaStream_t s) {
+  // matrix bytes (values + columns) against the 126 MB L2: resident -> latency-bound form
+  const bool streams = (double)K.n_blocks * (9.0 * sizeof(R) + 4.0) > 96e6;
+  const void* fn = streams ? (const void*)pcg_persistent_kernel<R, 6> : (const void*)pcg_persistent_kernel<R, 4>;
+  const int cap = streams ? 6 : 4;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  // every CTA must be resident (cooperative launch); at most cap per SM, and the partial
+  // buffers hold 2 x 2 doubles per CTA
+  int64_t grid = (int64_t)n_sm * (per_sm < cap ? per_sm : cap);
+  if (grid > part_slots / 4) grid = part_slots / 4;
+  const int64_t useful = (K.n_nodes + kBlock / 32 - 1) / (kBlock / 32);   // a warp per row at least
+  if (grid > useful) grid = useful;
+  if (grid < 1) grid = 1;
+  PersistArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.z, v.p, v.p2, v.q,
+                   K.n_nodes, maxit, block3, sc, part};
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
 }
 
 template <typename R>
@@ -460,6 +730,12 @@ template void pcg_iteration<float>(const Csr&, const float*, const uint8_t*, Pcg
                                    double*, cudaStream_t);
 template void pcg_iteration<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int, PcgScalars*,
                                     double*, cudaStream_t);
+template cudaError_t pcg_persistent<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int,
+                                            const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
+                                            cudaStream_t);
+template cudaError_t pcg_persistent<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int,
+                                             const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
+                                             cudaStream_t);
 template void precond_setup<float>(const Csr&, const float*, const int64_t*, const uint8_t*, float*, int, int*,
                                    cudaStream_t);
 template void precond_setup<double>(const Csr&, const double*, const int64_t*, const uint8_t*, double*, int, int*,

@@ -15,6 +15,19 @@ struct Csr {            // block-CSR pattern of K over node pairs (3x3 blocks)
   int64_t n_blocks;
 };
 
+// Grid-barrier words of the persistent solver, each in its own 128-byte line so that the
+// CTAs polling the generation do not contend with the arrivals.
+struct __align__(128) GridSync {
+  unsigned count;       // CTAs arrived at the current barrier
+  unsigned pad0[31];
+  unsigned gen;         // barrier generation, bumped by the last arrival
+  unsigned pad1[31];
+  int timeout;          // a barrier wait ran out (never expected; the solve stops)
+  int pad2[31];
+  double tot[2];        // the reduction the last arrival computed for everyone
+  double pad3[14];
+};
+
 struct PcgScalars {     // device-resident CG scalars
   double rz, rr, rr0, pq, alpha, beta, norm2, nonfinite;
   double target;        // rr at which the solve has converged (set by the host)
@@ -22,11 +35,13 @@ struct PcgScalars {     // device-resident CG scalars
   int breakdown;
   int iters;
   int done;             // set once rr <= target: later iterations leave x unchanged
+  GridSync gs;          // persistent solver only
 };
 
 template <typename R>
 struct PcgVecs {
   R *x, *r, *z, *p, *q, *minv;
+  R* p2;                // second search-direction buffer of the persistent solver
 };
 
 inline int64_t partial_slots() { return 2 * (int64_t)kMaxRedBlocks; }
@@ -46,6 +61,13 @@ void pcg_init(const double* b, double bscale, const uint8_t* freem, PcgVecs<R>& 
 template <typename R>
 void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3, PcgScalars* sc,
                    double* part, cudaStream_t s);
+// Whole PCG solve in one cooperative launch (grid barriers, no host round trips): x = K^-1 b
+// to |r| <= sqrt(rtol2) |r0| or maxit iterations; results in *sc (iters, rr, rr0, rz, pq,
+// breakdown, done, gs.timeout).  *sc must be zeroed before the launch.
+template <typename R>
+cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
+                           const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
+                           double* part, int64_t part_slots, cudaStream_t s);
 template <typename R>
 void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
                    int block3, int* bad, cudaStream_t s);

@@ -47,7 +47,7 @@ class Options(C.Structure):
                 ("newton_maxit", C.c_int), ("newton_stag_tol", C.c_double), ("pcg_rtol", C.c_double),
                 ("pcg_maxit", C.c_int), ("pcg_check_every", C.c_int), ("precond", C.c_int),
                 ("local_maxit", C.c_int), ("local_tol", C.c_double), ("ckpt_every", C.c_int),
-                ("predictor", C.c_int), ("ew_forcing", C.c_int)]
+                ("predictor", C.c_int), ("ew_forcing", C.c_int), ("pcg_persistent", C.c_int)]
 
 
 class Stats(C.Structure):

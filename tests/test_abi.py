@@ -38,7 +38,7 @@ def test_default_options(precision):
     o = hfe.Options()
     L.hfe_default_options(ctypes.byref(o), hfe.PRECISION[precision])
     assert o.precision == hfe.PRECISION[precision]
-    assert o.newton_rtol == (1e-10 if precision == "fp64" else 1e-6)
+    assert o.newton_rtol == (1e-10 if precision == "fp64" else 1e-7)
     assert o.local_maxit > 0 and o.pcg_maxit > 0 and o.pcg_check_every > 0
 
 

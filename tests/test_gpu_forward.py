@@ -97,3 +97,33 @@ def test_spmv_and_solve_consistent():
                 res = np.where(free, K @ np.where(free, dx, 0.0), 0.0) - b
                 assert np.linalg.norm(res) < tol_x * np.linalg.norm(b)
                 assert np.all(dx[~free] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_persistent_and_chunked_cg_agree(precision):
+    """The one-launch CG (grid barriers) and the chunked CG (CUDA-graph chunks, host checks)
+    run the same iteration: elastic solves on a clamped cube at 40^3 (the FP64 matrix, 141 MB,
+    takes the HBM-streaming register budget, the FP32 one the L2-resident one) and a
+    three-step forward on a reduced perforated plate."""
+    cube = inputs.config2_problem(n=40)
+    mesh, bc, mat, _ = cube
+    b = np.random.default_rng(1).standard_normal(mesh.n_dof)
+    b[bc.dof] = 0.0
+    xs, its = [], []
+    for pers in (1, 0):
+        with hfe.from_inputs(mesh, bc, mat, precision=precision, pcg_persistent=pers) as s:
+            s.sweep(np.zeros(mesh.n_dof), 0.0)
+            x, st = s.solve(b)
+        xs.append(x)
+        its.append(st["pcg_iters"])
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert np.abs(xs[0] - xs[1]).max() <= tol * np.abs(xs[1]).max()
+    assert abs(its[0] - its[1]) <= max(2, its[1] // 50), its
+    mesh, bc, mat, ts = inputs.config1_problem(nx=16, ny=8, nz=2, n_steps=20)
+    us = []
+    for pers in (1, 0):
+        with hfe.from_inputs(mesh, bc, mat, precision=precision, pcg_persistent=pers) as s:
+            u, _ = s.forward(ts[:3])
+        us.append(u)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    assert _per_step_rel(us[0], us[1]) < tol
