@@ -142,6 +142,8 @@ typedef struct {
   double sweep_ms;        /* device time in the sweep kernels */
   double solve_ms;        /* device time in the Krylov solves */
   double total_ms;        /* wall time of the call */
+  int64_t bicgstab_solves;/* Newton corrections whose CG met negative curvature and that were
+                             solved again by BiCGSTAB */
 } hfe_stats;
 
 /* Sizes of the internal data (for tests and benchmarks). */
@@ -172,9 +174,14 @@ hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info);
 hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat);
 
 /* State: displacement u[n_dof] and history [7][n_gp] at t_n (host or device).  hist may be
- * NULL in set_state to mean zero history. */
+ * NULL in set_state to mean zero history.  hfe_set_state resets the load factor of the
+ * stored state to 0; a state taken at t_n > 0 (hfe_get_state after a forward run) is
+ * continued correctly after hfe_set_load(h, t_n), since the next step's tangent predictor
+ * linearises the Dirichlet increment from t_n.  hfe_get_load returns it. */
 hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist);
 hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist);
+hfe_status hfe_set_load(hfe_handle* h, double t);
+hfe_status hfe_get_load(const hfe_handle* h, double* t);
 
 #define HFE_SWEEP_RESIDUAL 0   /* R and trial history only */
 #define HFE_SWEEP_TANGENT 1    /* R, trial history and K (into the internal BSR values) */

@@ -94,19 +94,25 @@ def residual(prob, u, hist, t=1.0, jacobians="tangent"):
     return R, K, es
 
 
-def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0, t_prev=None):
+def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0, t_prev=None, prev=None):
     """Equilibrium at load factor t from the converged start-of-step state u0 (at t_prev).
 
     Predictor (reading R14): the Dirichlet increment du_D is linearised at the start-of-step
-    state, u = u0 + du_D + K_ff^{-1} (-(R(u0) + K du_D - dt f_ext))_f, with K the tangent at
-    (u0, h_{n-1}).  The Newton iterations that follow are Eq. Stiffness_mat; the predictor
-    changes the iteration count only.  Without t_prev: u = u0 with the new Dirichlet values.
+    state, u = u0 + du_D + K_ff^{-1} (-(R(u0) + K du_D - dt f_ext))_f.  K and R are those of
+    the previous step's last Newton iteration (`prev`, its consistent algorithmic tangent at
+    u0), or, without `prev` (first step), the sweep at (u0, h_{n-1}).  The Newton iterations
+    that follow are Eq. Stiffness_mat; the predictor changes the iteration count only.
+    Without t_prev: u = u0 with the new Dirichlet values.  info["last"] = (R, K) of the last
+    iteration, the `prev` of the next step.
     """
     free = free_mask(prob)
     u = u0.copy()
     ref = None
     if t_prev is not None:
-        R0, K0, _ = residual(prob, u, hist, t_prev)
+        if prev is not None:
+            R0, K0 = prev
+        else:
+            R0, K0, _ = residual(prob, u, hist, t_prev)
         duD = np.zeros(prob.n_dof)
         duD[prob.fixed_dof] = (t - t_prev) * prob.fixed_val
         b = -(R0 + K0 @ duD)
@@ -125,7 +131,7 @@ def newton_step(prob, u0, hist, t, rtol=1e-10, maxit=30, atol_floor=1.0, t_prev=
         if ref is None:
             ref = max(rn, atol_floor)
         if rn <= rtol * ref:
-            return u, es, dict(iters=it, res=history, converged=True)
+            return u, es, dict(iters=it, res=history, converged=True, last=(R, K))
         if it == maxit:
             break
         Kff = K[free][:, free]
@@ -145,11 +151,13 @@ def forward(prob, t_steps, rtol=1e-10, maxit=30, hist0=None, predictor=True):
     u = np.zeros(prob.n_dof)
     us, hs, infos = [], [hist.copy()], []
     t_prev = 0.0
+    prev = None
     for t in t_steps:
         u, es, info = newton_step(prob, u, hist, t, rtol=rtol, maxit=maxit,
-                                  t_prev=t_prev if predictor else None)
+                                  t_prev=t_prev if predictor else None, prev=prev)
         if not info["converged"]:
             raise NewtonDivergence(f"step t={t}: residual history {info['res'][-3:]}")
+        prev = info.pop("last")
         t_prev = t
         hist = es["h_new"].copy()                  # commit h_n = H(u_n, h_{n-1}, theta)
         us.append(u.copy())

@@ -746,6 +746,10 @@ hfe_status ensure_work(hfe_handle* h, int n_steps) {
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vq = b;
     HFE_TRY(aalloc(h, w, &b, 9 * (size_t)h->n_nodes)); w->ls.vminv = b;
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vp2 = b;
+    HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vrh = b;
+    HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vy = b;
+    HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vt = b;
+    HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vxt = b;
     w->ls.fp64 = true;
   }
   HFE_TRY(aalloc(h, w, &w->u_all, ndof * n_steps));
@@ -796,7 +800,10 @@ struct AdjHook : StepHook {
     HFE_TRY(read_status(h));
     HFE_TRY(check_sweep_status(h));
     int64_t it = 0;
-    HFE_TRY(solve_sys(h, w->ls, w->R64, -1.0, &it));
+    h->allow_indefinite = true;   // an indefinite tangent is solved by BiCGSTAB
+    const hfe_status pst = solve_sys(h, w->ls, w->R64, -1.0, &it);
+    h->allow_indefinite = false;
+    HFE_TRY(pst);
     pcg_iters += h->h_sc->iters;
     add_update<double>(h->u, (const double*)w->ls.vx, h->freem, h->n_dof, h->s);
     HFE_TRY(sweep_ex(h, h->u, t[n], HFE_SWEEP_RESIDUAL, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
@@ -870,6 +877,7 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->ckpt, w->h_prev, 8 * ngp * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
                      "copy"));
   h->t_state = 0.0;
+  h->pred_valid = false;
   HFE_TRY(copy_in(h, w->ugt, u_target, ndof * n_steps * sizeof(double)));
   AdjHook hook;
   hook.w = w;
@@ -904,13 +912,17 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
     }
     HFE_TRY(read_status(h));
     HFE_TRY(check_sweep_status(h));
-    HFE_TRY(solve_sys(h, w->ls, w->rhs, 1.0, nullptr));          // K^T lambda = rhs (K symmetric)
+    h->allow_indefinite = true;   // K^T lambda = rhs (K symmetric; BiCGSTAB if indefinite)
+    const hfe_status ast = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
+    h->allow_indefinite = false;
+    HFE_TRY(ast);
     adj_pcg += h->h_sc->iters;
     launch_vjp(h, w, false, un, w->h_prev, reinterpret_cast<const double*>(w->ls.vx));   // pass B
     HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->mu, w->hbar, 7 * ngp * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
                        "copy"));
   }
   cudaEventRecord(tc, h->s);
+  h->pred_valid = false;   // the reverse pass reassembled K (FP64 handles share it)
   HFE_TRY(read_status(h));
   if (h->h_status->local_fail > 0) return fail(h, HFE_ELOCAL, "adjoint: local system failures");
   // J and gradient

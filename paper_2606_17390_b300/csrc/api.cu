@@ -189,6 +189,7 @@ PcgVecs<R> vecs(LinSys& ls) {
   PcgVecs<R> v;
   v.x = (R*)ls.vx; v.r = (R*)ls.vr; v.z = (R*)ls.vz; v.p = (R*)ls.vp; v.q = (R*)ls.vq; v.minv = (R*)ls.vminv;
   v.p2 = (R*)ls.vp2;
+  v.rh = (R*)ls.vrh; v.y = (R*)ls.vy; v.t = (R*)ls.vt;
   return v;
 }
 
@@ -213,6 +214,35 @@ hfe_status build_pcg_graph(hfe_handle* h, LinSys& ls, int len) {
   return HFE_OK;
 }
 
+// A Newton correction whose CG met negative curvature (p.Kp <= 0: the tangent is
+// indefinite at this iterate): solve the same system with preconditioned BiCGSTAB, which
+// needs no definiteness, as a direct solver would; if that fails too, the truncated CG
+// direction (Steihaug) is kept when there is one.  x in v.x either way.
+template <typename R>
+hfe_status indefinite_fallback(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs<R>& v, int block3, const double* b,
+                               double bscale) {
+  const int cg_iters = h->h_sc->iters;
+  const bool have_truncated = h->allow_truncated && cg_iters > 0 && std::isfinite(h->h_sc->rr);
+  const size_t bytes = (ls.fp64 ? sizeof(double) : sizeof(float)) * h->n_dof;
+  if (have_truncated) HFE_TRY(cuda_check(h, cudaMemcpyAsync(ls.vxt, v.x, bytes, cudaMemcpyDeviceToDevice, h->s), "copy"));
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
+  const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
+  HFE_TRY(cuda_check(h, bicgstab_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
+                                               h->opt.pcg_maxit, h->sc, h->part, partial_slots(), h->s),
+                     "BiCGSTAB launch"));
+  HFE_TRY(read_status(h));
+  h->n_bicgstab++;
+  h->h_sc->iters += cg_iters;
+  if (h->h_sc->gs.timeout) return fail(h, HFE_ECUDA, "BiCGSTAB: a grid barrier wait ran out");
+  if (h->h_sc->done) return HFE_OK;
+  if (have_truncated && h->allow_truncated) {
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(v.x, ls.vxt, bytes, cudaMemcpyDeviceToDevice, h->s), "copy"));
+    h->pcg_truncated = true;
+    return HFE_OK;
+  }
+  return fail(h, HFE_EPCG, "indefinite matrix: CG broke down and BiCGSTAB did not converge");
+}
+
 // The solve as one cooperative launch (preconditioner set up and scalars zeroed by the
 // caller); the same outcomes as the chunked form below.
 template <typename R>
@@ -230,17 +260,14 @@ hfe_status pcg_solve_persistent(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs
   // a Newton correction may run on a tangent that is indefinite at some nodes (the surrogate
   // blocks keep the preconditioner SPD and truncated CG stops at negative curvature); a plain
   // solve of a matrix that is not SPD is refused
-  if (*h->h_bad != 0 && !h->allow_truncated)
+  if (*h->h_bad != 0 && !h->allow_indefinite)
     return fail(h, HFE_EPCG, "preconditioner: " + std::to_string(*h->h_bad) + " diagonal blocks not positive definite");
   if (!std::isfinite(sc.rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
   if (sc.done) return HFE_OK;
   if (sc.breakdown) {
-    // negative curvature (p.Ap <= 0): x holds the last iterate; truncated CG (Steihaug)
-    // returns it as an inexact Newton direction when allowed
-    if (h->allow_truncated && sc.iters > 0 && std::isfinite(sc.rr)) {
-      h->pcg_truncated = true;
-      return HFE_OK;
-    }
+    // negative curvature (p.Ap <= 0) in a Newton correction: BiCGSTAB, else the truncated
+    // CG direction
+    if (h->allow_indefinite) return indefinite_fallback<R>(h, ls, K, v, block3, b, bscale);
     return fail(h, HFE_EPCG, "CG breakdown (p.Ap <= 0 or non-finite)");
   }
   return fail(h, HFE_EPCG, "CG did not converge: |r|/|b| = " + std::to_string(std::sqrt(sc.rr / sc.rr0)));
@@ -269,7 +296,7 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   // a Newton correction may run on a tangent that is indefinite at some nodes (the surrogate
   // blocks keep the preconditioner SPD and truncated CG stops at negative curvature); a plain
   // solve of a matrix that is not SPD is refused
-  if (*h->h_bad != 0 && !h->allow_truncated)
+  if (*h->h_bad != 0 && !h->allow_indefinite)
     return fail(h, HFE_EPCG, "preconditioner: " + std::to_string(*h->h_bad) + " diagonal blocks not positive definite");
   const double rr0 = h->h_sc->rr0;
   if (!std::isfinite(rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
@@ -286,12 +313,12 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
       HFE_TRY(read_status(h));
       if (h->h_sc->done || h->h_sc->rr <= target) { done = true; break; }
       if (h->h_sc->breakdown) {
-        // negative curvature (p.Ap <= 0): the kernels froze x at the last iterate; truncated
-        // CG (Steihaug) returns it as an inexact Newton direction when allowed
-        if (h->allow_truncated && h->h_sc->iters > 0 && std::isfinite(h->h_sc->rr)) {
-          h->pcg_truncated = true;
-          done = true;
-          break;
+        // negative curvature (p.Ap <= 0): the kernels froze x at the last iterate; in a
+        // Newton correction BiCGSTAB takes over, else the truncated CG direction is kept
+        if (h->allow_indefinite) {
+          HFE_TRY((indefinite_fallback<R>(h, ls, K, v, block3, b, bscale)));
+          if (iters_out) *iters_out = h->h_sc->iters;
+          return HFE_OK;
         }
         return fail(h, HFE_EPCG, "CG breakdown (p.Ap <= 0 or non-finite)");
       }
@@ -426,6 +453,7 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   HFE_TRY(dalloc(h, &h->bad, 1));
   HFE_TRY(dalloc(h, &h->tmp64, h->n_dof));
   HFE_TRY(dalloc(h, &h->b64, h->n_dof));
+  HFE_TRY(dalloc(h, &h->u_start, h->n_dof));
   {
     unsigned char* b = nullptr;
     HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vx = b;
@@ -435,6 +463,10 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->vq = b;
     HFE_TRY(dalloc(h, &b, rsz * 9 * h->n_nodes)); h->vminv = b;
     HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->ls.vp2 = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->ls.vrh = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->ls.vy = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->ls.vt = b;
+    HFE_TRY(dalloc(h, &b, rsz * h->n_dof)); h->ls.vxt = b;
   }
   h->ls.K = h->K;
   h->ls.vx = h->vx; h->ls.vr = h->vr; h->ls.vz = h->vz; h->ls.vp = h->vp; h->ls.vq = h->vq; h->ls.vminv = h->vminv;
@@ -528,6 +560,7 @@ hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info) {
 }
 
 hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat) {
+  if (h) h->pred_valid = false;
   if (h == nullptr) return HFE_EINVAL;
   StreamScope scope(h);
   HFE_TRY(upload_material(h, mat));
@@ -537,6 +570,7 @@ hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat) {
 
 hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist) {
   if (h == nullptr) return HFE_EINVAL;
+  if (h) h->pred_valid = false;
   StreamScope scope(h);
   if (u) HFE_TRY(copy_in(h, h->u, u, sizeof(double) * h->n_dof));
   else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, sizeof(double) * h->n_dof, h->s), "memset"));
@@ -545,6 +579,19 @@ hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist) {
   launch_sigma_cache(h->hist, h->fp64 != 0, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
   h->t_state = 0.0;
   return cuda_check(h, cudaStreamSynchronize(h->s), "set state");
+}
+
+hfe_status hfe_set_load(hfe_handle* h, double t) {
+  if (h == nullptr || !std::isfinite(t)) return HFE_EINVAL;
+  if (h) h->pred_valid = false;
+  h->t_state = t;
+  return HFE_OK;
+}
+
+hfe_status hfe_get_load(const hfe_handle* h, double* t) {
+  if (h == nullptr || t == nullptr) return HFE_EINVAL;
+  *t = h->t_state;
+  return HFE_OK;
 }
 
 hfe_status hfe_get_state(hfe_handle* h, double* u, double* hist) {
@@ -559,6 +606,7 @@ hfe_status hfe_gp_sweep(hfe_handle* h, const double* u, double load, int mode, d
                         double* hist_trial_out, hfe_stats* stats) {
   if (h == nullptr || u == nullptr) return HFE_EINVAL;
   if (mode != HFE_SWEEP_RESIDUAL && mode != HFE_SWEEP_TANGENT) return fail(h, HFE_EINVAL, "sweep: unknown mode");
+  h->pred_valid = false;   // R (and K) no longer those of the last converged Newton iteration
   auto w0 = std::chrono::steady_clock::now();
   StreamScope scope(h);
   const double* ud = u;
@@ -661,6 +709,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   hfe_stats loc;
   std::memset(&loc, 0, sizeof(loc));
   const bool u_out_dev = is_device_ptr(u_out_dev_or_host);
+  const int64_t bicg0 = h->n_bicgstab;
   for (int n = 0; n < n_steps; ++n) {
     double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
     double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
@@ -668,13 +717,21 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
     bool force_tight = false;
     int backtracks = 0;
     const double t_prev = h->t_state;
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u_start, h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
+                       "copy"));
     if (h->opt.predictor) {
-      // tangent predictor on the converged start-of-step state (u_{n-1}, h_{n-1}):
-      // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment
-      HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
-      HFE_TRY(read_status(h));
-      loc.sweeps++;
-      HFE_TRY(check_sweep_status(h));
+      // tangent predictor on the converged start-of-step state u_{n-1}:
+      // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment,
+      // with K and R of the previous step's last Newton iteration (its consistent tangent at
+      // u_{n-1}); without them (first step, or after the state was set) the sweep at
+      // (u_{n-1}, h_{n-1})
+      if (!h->pred_valid) {
+        HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
+        HFE_TRY(read_status(h));
+        loc.sweeps++;
+        HFE_TRY(check_sweep_status(h));
+      }
+      h->pred_valid = false;
       HFE_TRY(cuda_check(h, cudaMemsetAsync(h->tmp64, 0, sizeof(double) * h->n_dof, h->s), "memset"));
       set_dirichlet(h->tmp64, h->fixed_dof, h->fixed_val, t[n] - t_prev, h->n_fixed, h->s);
       Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
@@ -694,8 +751,10 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         cudaEventRecord(h->t0, h->s);
         if (h->opt.ew_forcing) h->pcg_rtol_now = std::max(h->opt.pcg_rtol, 1e-3);   // predictor: rough solve
         h->allow_truncated = true;
+        h->allow_indefinite = true;
         hfe_status pst = solve_any(h, h->b64, 1.0, nullptr);
         h->allow_truncated = false;
+        h->allow_indefinite = false;
         h->pcg_rtol_now = 0.0;
         HFE_TRY(pst);
         cudaEventRecord(h->t1, h->s);
@@ -772,9 +831,11 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       prev_solve = nrm;
       last_tight = !h->opt.ew_forcing || h->pcg_rtol_now <= h->opt.pcg_rtol * 1.0000001;
       h->allow_truncated = true;
+      h->allow_indefinite = true;
       h->pcg_truncated = false;
       hfe_status sst = solve_any(h, h->R, -1.0, &pit);
       h->allow_truncated = false;
+      h->allow_indefinite = false;
       h->pcg_rtol_now = 0.0;
       HFE_TRY(sst);
       if (h->pcg_truncated) last_tight = false;
@@ -790,7 +851,12 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       loc.newton_iters++;
     }
     if (!conv) {
+      loc.bicgstab_solves = h->n_bicgstab - bicg0;
       if (st) *st = loc;
+      // leave the stored state at the last converged step
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u, h->u_start, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice,
+                                            h->s), "copy"));
+      HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "restore"));
       return fail(h, HFE_ENEWTON, "Newton did not converge at step " + std::to_string(n) + ", |R| = " +
                                       std::to_string(loc.last_residual));
     }
@@ -811,12 +877,14 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       else HFE_TRY(copy_out(h, dst, h->u, sizeof(double) * h->n_dof));
     }
     h->t_state = t[n];
+    h->pred_valid = true;
     if (hook) HFE_TRY(hook->after_commit(h, n));
     loc.steps_done = n + 1;
   }
   if (hist_out) HFE_TRY(export_history(h, h->hist, hist_out));
   HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "forward"));
   loc.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+  loc.bicgstab_solves = h->n_bicgstab - bicg0;
   if (st) *st = loc;
   return HFE_OK;
 }

@@ -28,6 +28,8 @@ struct LinSys {
   void* K = nullptr;
   void *vx = nullptr, *vr = nullptr, *vz = nullptr, *vp = nullptr, *vq = nullptr, *vminv = nullptr;
   void* vp2 = nullptr;   // second search direction (persistent CG)
+  void *vrh = nullptr, *vy = nullptr, *vt = nullptr;   // BiCGSTAB work vectors
+  void* vxt = nullptr;   // truncated-CG direction kept while BiCGSTAB runs
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
   bool fp64 = true;
@@ -79,7 +81,14 @@ struct hfe_handle {
   double t_state = 0.0;        // load factor of the stored state
   double pcg_rtol_now = 0.0;   // CG tolerance of the current Newton solve (0: opt.pcg_rtol)
   bool allow_truncated = false;  // Newton solves may stop at negative curvature
+  bool allow_indefinite = false; // Newton and adjoint solves: indefinite K -> BiCGSTAB
   bool pcg_truncated = false;
+  int64_t n_bicgstab = 0;        // Newton corrections solved by the BiCGSTAB fallback
+  // K and R in the handle are those of the last Newton iteration of the step that produced
+  // the stored state (the next step's predictor reuses them); cleared by anything that
+  // changes the state, the material or K
+  bool pred_valid = false;
+  double* u_start = nullptr;     // start-of-step displacement, restored when a step fails
   double* sigma = nullptr;     // n_gp * 6, allocated on demand
   // pinned host mirrors of the device scalars
   PcgScalars* h_sc = nullptr;

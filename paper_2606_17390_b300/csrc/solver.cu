@@ -612,6 +612,191 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Persistent BiCGSTAB (van der Vorst 1992) with the same block-Jacobi preconditioner applied
+// on the right, for Newton corrections whose tangent turned out indefinite (CG met p.Kp <= 0).
+// Same row split, fixed-order reductions and fused barriers as the CG kernel: one plain
+// barrier and four barrier-reductions per iteration.
+template <typename R>
+struct BicgArgs {
+  const int64_t* rowptr;
+  const int32_t* cols;
+  const R* vals;
+  const uint8_t* freem;
+  const R* minv;
+  const double* b;
+  double bscale, rtol2;
+  R *x, *r, *rh, *p, *v, *y, *s, *z, *t;
+  int64_t n_nodes, maxit;
+  int block3;
+  PcgScalars* sc;
+  double* part;
+};
+
+// out = K in on the rows [n0, n1) (fixed rows 0; in is zero on fixed dofs), returning this
+// thread's share of out . w over those rows
+template <typename R>
+__device__ __forceinline__ double spmv_range(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
+                                             const R* __restrict__ vals, const uint8_t* __restrict__ freem,
+                                             const R* in, R* out, const R* w, int64_t n0, int64_t n1) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int kWarps = kBlock / 32;
+  double dot = 0.0;
+  for (int64_t r0 = n0 + warp; r0 < n1; r0 += 2 * kWarps) {
+    const int64_t r1 = r0 + kWarps;
+    const bool has1 = r1 < n1;
+    const int64_t b0 = rowptr[r0], e0 = rowptr[r0 + 1];
+    const int64_t b1 = has1 ? rowptr[r1] : 0, e1 = has1 ? rowptr[r1 + 1] : 0;
+    const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
+    R acc[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+    const int nmax = nb0 > nb1 ? nb0 : nb1;
+    for (int j = lane; j < nmax; j += 32) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int nb = t == 0 ? nb0 : nb1;
+        if (j < nb) {
+          const int64_t blk = (t == 0 ? b0 : b1) + j;
+          const int64_t col = cols[blk];
+          const R* v = vals + blk * 9;
+          const R x0 = in[3 * col], x1 = in[3 * col + 1], x2 = in[3 * col + 2];
+          acc[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
+          acc[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
+          acc[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc[t][i] = warp_sum_r(acc[t][i]);
+    if (lane < 6) {
+      const int t = lane / 3, i = lane % 3;
+      if (t == 0 || has1) {
+        const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
+        const R o = t == 0 ? (i == 0 ? acc[0][0] : (i == 1 ? acc[0][1] : acc[0][2]))
+                           : (i == 0 ? acc[1][0] : (i == 1 ? acc[1][1] : acc[1][2]));
+        const R od = freem[d] ? o : R(0);
+        out[d] = od;
+        dot += (double)od * (double)w[d];
+      }
+    }
+  }
+  return dot;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const BicgArgs<R> a) {
+  const int64_t n0 = (int64_t)blockIdx.x * a.n_nodes / gridDim.x;
+  const int64_t n1 = (int64_t)(blockIdx.x + 1) * a.n_nodes / gridDim.x;
+  PcgScalars* sc = a.sc;
+  int red = 0;
+  auto allreduce = [&](double v0, double v1, double& t0, double& t1) -> bool {
+    block_sum2(v0, v1);
+    double* pp = a.part + 2 * (size_t)gridDim.x * (red & 1);
+    if (threadIdx.x == 0) {
+      pp[2 * blockIdx.x] = v0;
+      pp[2 * blockIdx.x + 1] = v1;
+    }
+    ++red;
+    return grid_allreduce(&sc->gs, pp, t0, t1);
+  };
+  // x = 0, r = rh = b on the free dofs, p = v = 0
+  double rr = 0.0, dummy = 0.0;
+  for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) {
+    const R rv = a.freem[d] ? (R)(a.bscale * a.b[d]) : R(0);
+    a.r[d] = rv;
+    a.rh[d] = rv;
+    a.x[d] = R(0);
+    a.p[d] = R(0);
+    a.v[d] = R(0);
+    rr += (double)rv * (double)rv;
+  }
+  if (!allreduce(rr, 0.0, rr, dummy)) return;
+  const double rr0 = rr, target = a.rtol2 * rr0;
+  double rho = rr, rho_old = 1.0, alpha = 1.0, omega = 1.0, rv_ = 0.0;
+  int breakdown = (isfinite(rr)) ? 0 : 1;
+  int done = (!breakdown && rr <= target) ? 1 : 0;
+  int64_t it = 0;
+  while (!done && !breakdown && it < a.maxit) {
+    const double beta = (rho / rho_old) * (alpha / omega);
+    // p = r + beta (p - omega v), y = M^-1 p on the own nodes
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
+      R pv[3], yv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t d = 3 * n + i;
+        pv[i] = a.r[d] + (R)beta * (a.p[d] - (R)omega * a.v[d]);
+        a.p[d] = pv[i];
+      }
+      precond_apply(a.minv, a.block3, n, pv, yv);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) a.y[3 * n + i] = yv[i];
+    }
+    if (!allreduce(0.0, 0.0, dummy, dummy)) return;   // y complete
+    double d1 = spmv_range(a.rowptr, a.cols, a.vals, a.freem, a.y, a.v, a.rh, n0, n1);
+    if (!allreduce(d1, 0.0, rv_, dummy)) return;
+    if (rv_ == 0.0 || !isfinite(rv_)) { breakdown = 1; break; }
+    alpha = rho / rv_;
+    // x += alpha y, s = r - alpha v, z = M^-1 s
+    double ss = 0.0;
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
+      R sv[3], zv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t d = 3 * n + i;
+        a.x[d] += (R)alpha * a.y[d];
+        sv[i] = a.r[d] - (R)alpha * a.v[d];
+        a.s[d] = sv[i];
+        ss += (double)sv[i] * (double)sv[i];
+      }
+      precond_apply(a.minv, a.block3, n, sv, zv);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) a.z[3 * n + i] = zv[i];
+    }
+    if (!allreduce(ss, 0.0, ss, dummy)) return;
+    ++it;
+    if (!isfinite(ss)) { breakdown = 1; break; }
+    if (ss <= target) { rr = ss; done = 1; break; }
+    // t = K z; omega = (t.s) / (t.t)
+    double ts = 0.0, tt = 0.0;
+    {
+      // t.s from the SpMV's dot, t.t in a second pass over the own rows
+      ts = spmv_range(a.rowptr, a.cols, a.vals, a.freem, a.z, a.t, a.s, n0, n1);
+      __syncthreads();
+      for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) tt += (double)a.t[d] * (double)a.t[d];
+    }
+    if (!allreduce(ts, tt, ts, tt)) return;
+    if (!(tt > 0.0) || !isfinite(ts)) { breakdown = 1; break; }
+    omega = ts / tt;
+    // x += omega z, r = s - omega t; rho = rh.r, rr = r.r
+    double rhr = 0.0;
+    rr = 0.0;
+    for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) {
+      a.x[d] += (R)omega * a.z[d];
+      const R rv = a.s[d] - (R)omega * a.t[d];
+      a.r[d] = rv;
+      rhr += (double)a.rh[d] * (double)rv;
+      rr += (double)rv * (double)rv;
+    }
+    if (!allreduce(rhr, rr, rhr, rr)) return;
+    if (!isfinite(rr)) { breakdown = 1; break; }
+    if (rr <= target) { done = 1; break; }
+    if (omega == 0.0 || rhr == 0.0) { breakdown = 1; break; }
+    rho_old = rho;
+    rho = rhr;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rr = rr;
+    sc->rr0 = rr0;
+    sc->target = target;
+    sc->iters = (int)it;
+    sc->breakdown = breakdown;
+    sc->done = done;
+  }
+}
+
 inline unsigned nblk(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 inline unsigned rblk(int64_t n, int per) {   // grid of a reducing (grid-stride) kernel
   int64_t b = (n + per - 1) / per;
@@ -685,6 +870,28 @@ cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, Pc
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
 }
 
+
+template <typename R>
+cudaError_t bicgstab_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
+                                const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
+                                double* part, int64_t part_slots, cudaStream_t s) {
+  const void* fn = (const void*)bicgstab_persistent_kernel<R>;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)n_sm * (per_sm < 4 ? per_sm : 4);
+  if (grid > part_slots / 4) grid = part_slots / 4;
+  const int64_t useful = (K.n_nodes + kBlock / 32 - 1) / (kBlock / 32);
+  if (grid > useful) grid = useful;
+  if (grid < 1) grid = 1;
+  BicgArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.rh, v.p, v.q, v.y, v.p2, v.z,
+                v.t, K.n_nodes, maxit, block3, sc, part};
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
+}
+
 template <typename R>
 void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
                    int block3, int* bad, cudaStream_t s) {
@@ -736,6 +943,12 @@ template cudaError_t pcg_persistent<float>(const Csr&, const float*, const uint8
 template cudaError_t pcg_persistent<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int,
                                              const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
                                              cudaStream_t);
+template cudaError_t bicgstab_persistent<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int,
+                                                 const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
+                                                 cudaStream_t);
+template cudaError_t bicgstab_persistent<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int,
+                                                  const double*, double, double, int64_t, PcgScalars*, double*,
+                                                  int64_t, cudaStream_t);
 template void precond_setup<float>(const Csr&, const float*, const int64_t*, const uint8_t*, float*, int, int*,
                                    cudaStream_t);
 template void precond_setup<double>(const Csr&, const double*, const int64_t*, const uint8_t*, double*, int, int*,

@@ -42,6 +42,7 @@ template <typename R>
 struct PcgVecs {
   R *x, *r, *z, *p, *q, *minv;
   R* p2;                // second search-direction buffer of the persistent solver
+  R *rh, *y, *t;        // BiCGSTAB: shadow residual, preconditioned direction, K z
 };
 
 inline int64_t partial_slots() { return 2 * (int64_t)kMaxRedBlocks; }
@@ -68,6 +69,13 @@ template <typename R>
 cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
                            double* part, int64_t part_slots, cudaStream_t s);
+// Preconditioned BiCGSTAB in one cooperative launch for a symmetric indefinite (or
+// nonsymmetric) K with the same SPD block-Jacobi preconditioner: x (v.x) = K^-1 b; uses v.r,
+// v.rh, v.p, v.q (as v), v.y, v.p2 (as s), v.z, v.t.  Results in *sc as for pcg_persistent.
+template <typename R>
+cudaError_t bicgstab_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
+                                const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
+                                double* part, int64_t part_slots, cudaStream_t s);
 template <typename R>
 void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
                    int block3, int* bad, cudaStream_t s);

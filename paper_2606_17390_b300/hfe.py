@@ -54,7 +54,7 @@ class Stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int64), ("pcg_iters", C.c_int64), ("sweeps", C.c_int64),
                 ("plastic_gps", C.c_int64), ("local_fail", C.c_int64), ("max_local_iters", C.c_int32),
                 ("steps_done", C.c_int32), ("last_residual", C.c_double), ("sweep_ms", C.c_double),
-                ("solve_ms", C.c_double), ("total_ms", C.c_double)]
+                ("solve_ms", C.c_double), ("total_ms", C.c_double), ("bicgstab_solves", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +92,8 @@ def lib():
     L.hfe_get_info.argtypes = [vp, C.POINTER(Info)]
     L.hfe_set_material.argtypes = [vp, C.POINTER(_Material)]
     L.hfe_set_state.argtypes = [vp, vp, vp]
+    L.hfe_set_load.argtypes = [vp, dbl]
+    L.hfe_get_load.argtypes = [vp, C.POINTER(dbl)]
     L.hfe_get_state.argtypes = [vp, vp, vp]
     L.hfe_gp_sweep.argtypes = [vp, vp, dbl, i32, vp, vp, vp, C.POINTER(Stats)]
     L.hfe_get_bsr.argtypes = [vp, vp, vp, vp]
@@ -100,6 +102,7 @@ def lib():
     L.hfe_forward.argtypes = [vp, i32, vp, vp, vp, vp, C.POINTER(Stats)]
     L.hfe_adjoint.argtypes = [vp, i32, vp, vp, dbl, vp, vp, C.POINTER(Stats)]
     for name in ("hfe_create", "hfe_get_info", "hfe_set_material", "hfe_set_state", "hfe_get_state",
+                 "hfe_set_load", "hfe_get_load",
                  "hfe_gp_sweep", "hfe_get_bsr", "hfe_spmv", "hfe_solve", "hfe_forward", "hfe_adjoint"):
         getattr(L, name).restype = i32
     _LIB = L
@@ -210,6 +213,15 @@ class Solver:
 
     def set_state(self, u=None, hist=None):
         self._check(lib().hfe_set_state(self._h, _ptr(u), _ptr(hist)))
+
+    def set_load(self, t):
+        """Load factor of the stored state (hfe_set_state resets it to 0)."""
+        self._check(lib().hfe_set_load(self._h, float(t)))
+
+    def get_load(self):
+        t = C.c_double()
+        self._check(lib().hfe_get_load(self._h, C.byref(t)))
+        return t.value
 
     def get_state(self):
         u = np.empty(self.n_dof)

@@ -124,6 +124,45 @@ def _gaussian_smooth_2d(w: np.ndarray, sigma: float) -> np.ndarray:
     return gaussian_filter(w, sigma=sigma, mode="reflect")
 
 
+def _smooth_grf(nx: int, ny: int, seed: int, corr: float, upsample: int) -> np.ndarray:
+    """(ny, nx) Gaussian random field: white noise (seed) on the (nx/upsample)*(ny/upsample)
+    base grid, repeated `upsample` times per axis, Gaussian filter of std
+    corr*upsample/sqrt(2) elements (covariance exp(-r^2/(2 corr^2)) on the base grid)."""
+    rng = np.random.default_rng(seed)
+    bx, by = nx // upsample, ny // upsample
+    w = rng.standard_normal((by, bx))
+    if upsample > 1:
+        w = np.repeat(np.repeat(w, upsample, axis=0), upsample, axis=1)
+    return _gaussian_smooth_2d(w, corr * upsample / math.sqrt(2.0))
+
+
+def _largest_component(keep2d: np.ndarray) -> np.ndarray:
+    """Largest 4-connected component of the kept columns (face connectivity in 3-D since
+    every column spans the full thickness)."""
+    from scipy.ndimage import label
+    lab, nlab = label(keep2d)
+    if nlab > 1:
+        sizes = np.bincount(lab.ravel())
+        sizes[0] = 0
+        keep2d = lab == int(np.argmax(sizes))
+    return keep2d
+
+
+def _column_mesh(keep2d: np.ndarray, nz: int, Lx: float, Ly: float, Lz: float):
+    """Hex mesh of the kept through-thickness columns of an (ny, nx) grid; returns the mesh
+    and the column index j*nx + i of every element."""
+    ny, nx = keep2d.shape
+    full = box_mesh(nx, ny, nz, Lx, Ly, Lz)
+    col_keep = keep2d.ravel()                      # index j*nx + i
+    el_col = np.arange(full.n_el) % (nx * ny)
+    sel = col_keep[el_col]
+    conn = full.conn[sel]
+    used = np.unique(conn)
+    remap = -np.ones(full.n_nodes, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    return Mesh(X=full.X[used].copy(), conn=remap[conn].astype(np.int32)), el_col[sel]
+
+
 def grf_plate_mesh(nx: int = 200, ny: int = 100, nz: int = 4, Lx: float = 100.0,
                    Ly: float = 50.0, Lz: float = 2.0, seed: int = 1, corr: float = 8.0,
                    percentile: float = 70.0, grip_cols: int = 4, upsample: int = 1) -> Mesh:
@@ -133,32 +172,11 @@ def grf_plate_mesh(nx: int = 200, ny: int = 100, nz: int = 4, Lx: float = 100.0,
     i.e. covariance exp(-r^2/(2 corr^2)) on the base grid) removes every through-thickness
     column whose value exceeds its `percentile`; `grip_cols` columns at each x end stay
     solid; the largest face-connected component is kept and orphan nodes are dropped."""
-    rng = np.random.default_rng(seed)
-    bx, by = nx // upsample, ny // upsample
-    w = rng.standard_normal((by, bx))
-    if upsample > 1:
-        w = np.repeat(np.repeat(w, upsample, axis=0), upsample, axis=1)
-    g = _gaussian_smooth_2d(w, corr * upsample / math.sqrt(2.0))
-    thr = np.percentile(g, percentile)
-    keep2d = g <= thr
+    g = _smooth_grf(nx, ny, seed, corr, upsample)
+    keep2d = g <= np.percentile(g, percentile)
     keep2d[:, :grip_cols * upsample] = True
     keep2d[:, nx - grip_cols * upsample:] = True
-    # largest 4-connected component of the kept columns (face connectivity in 3-D since
-    # every column spans the full thickness)
-    from scipy.ndimage import label
-    lab, nlab = label(keep2d)
-    if nlab > 1:
-        sizes = np.bincount(lab.ravel())
-        sizes[0] = 0
-        keep2d = lab == int(np.argmax(sizes))
-    full = box_mesh(nx, ny, nz, Lx, Ly, Lz)
-    col_keep = keep2d.ravel()                      # index j*nx + i
-    el_col = np.arange(full.n_el) % (nx * ny)
-    conn = full.conn[col_keep[el_col]]
-    used = np.unique(conn)
-    remap = -np.ones(full.n_nodes, dtype=np.int64)
-    remap[used] = np.arange(used.size)
-    return Mesh(X=full.X[used].copy(), conn=remap[conn].astype(np.int32))
+    return _column_mesh(_largest_component(keep2d), nz, Lx, Ly, Lz)[0]
 
 
 def _face_nodes(mesh: Mesh, axis: int, where: str) -> np.ndarray:
@@ -228,6 +246,33 @@ def config1_problem(nx: int = 200, ny: int = 100, nz: int = 4, n_steps: int = 20
     mesh = grf_plate_mesh(nx, ny, nz, 100.0, 50.0, 2.0, seed=seed, corr=corr,
                           grip_cols=max(1, (4 * nx) // 200))
     return mesh, clamp_displace_bcs(mesh, (2.0, 0.0, 0.0)), config1_material(), load_factors(n_steps)
+
+
+def config4_problem(nx: int = 400, ny: int = 200, nz: int = 4, n_steps: int = 20):
+    """Config 1's 100 x 50 x 2 mm domain at 0.25 mm (400 x 200 x 4): the holes of the same
+    random field at twice the resolution (seed 1 white noise on the 200 x 100 base grid,
+    upsampled 2x, Gaussian filter of std 16/sqrt(2) fine columns, 70th percentile, 2 mm grips
+    at both ends), config-1 loading and Voce material, and per-element Hill F, G, H and
+    sigma0 = mean * (1 + 0.15 g_k / max|g_k|) with g_k smooth random fields of the same
+    construction (seeds 5, 6, 7, 8).  Other (nx, ny), e.g. a 40 x 20 x 2 re-mesh, sample the
+    400 x 200 hole mask and fields at their element-column centres.  Returns (mesh, bc,
+    material with the mean values, theta [n_el, 11], t)."""
+    NX, NY, up = 400, 200, 2
+    keep_f = (lambda g: g <= np.percentile(g, 70.0))(_smooth_grf(NX, NY, 1, 8.0, up))
+    keep_f[:, :4 * up] = True
+    keep_f[:, NX - 4 * up:] = True
+    fields = [_smooth_grf(NX, NY, sd, 8.0, up) for sd in (5, 6, 7, 8)]
+    fields = [1.0 + 0.15 * g / np.abs(g).max() for g in fields]
+    fi = np.minimum(((np.arange(nx) + 0.5) * NX / nx).astype(np.int64), NX - 1)
+    fj = np.minimum(((np.arange(ny) + 0.5) * NY / ny).astype(np.int64), NY - 1)
+    keep = keep_f[np.ix_(fj, fi)]
+    mesh, col = _column_mesh(_largest_component(keep), nz, 100.0, 50.0, 2.0)
+    mat = config1_material()
+    theta = np.tile(mat.theta_vector(), (mesh.n_el, 1))
+    cj, ci = fj[col // nx], fi[col % nx]
+    for k, idx in enumerate((2, 3, 4, 8)):      # F, G, H, sigma0
+        theta[:, idx] *= fields[k][cj, ci]
+    return mesh, clamp_displace_bcs(mesh, (2.0, 0.0, 0.0)), mat, theta, load_factors(n_steps)
 
 
 def config2_problem(n: int = 100, n_steps: int = 10):

@@ -87,3 +87,65 @@ def test_autograd_function(oracle_uniform):
         (2.0 * J).backward()
     assert abs(J.item() - Jo) < 1e-8 * Jo
     _check(theta.grad.numpy() / 2.0, go)
+
+
+def _config4_target(mesh, ts):
+    """A seeded synthetic target field (no arithmetic of the method): a uniform stretch along
+    x growing with the load factor plus noise."""
+    rng = np.random.default_rng(3)
+    u = np.stack([0.02 * mesh.X[:, 0], -0.003 * (mesh.X[:, 1] - 25.0), np.zeros(mesh.n_nodes)], 1).ravel()
+    return np.stack([t * u + 1e-4 * rng.standard_normal(u.size) for t in ts])
+
+
+def test_config4_remesh_per_element_vs_oracle():
+    """Config 4's per-element F, G, H, sigma0 fields on the 40 x 20 x 2 re-mesh of the plate,
+    evaluated at the spatially uniform mean parameters, three load steps of five: the GPU
+    adjoint (FP64 and mixed forward) against the oracle's per-element adjoint."""
+    mesh, bc, mat, th_true, ts = inputs.config4_problem(40, 20, 2, n_steps=5)
+    ts = ts[:3]
+    th = np.tile(mat.theta_vector(), (mesh.n_el, 1))
+    u_gt = _config4_target(mesh, ts)
+    prob = solver.from_inputs(mesh, bc, mat, th)
+    us, hs, infos = solver.forward(prob, ts, rtol=1e-13)
+    assert sum(i["plastic"] for i in infos) > 0
+    go = solver.adjoint(prob, ts, us, hs, u_gt, per_element=True)
+    for precision in ("fp64", "mixed"):
+        opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+        with hfe.from_inputs(mesh, bc, mat, precision=precision, theta=th, **opts) as s:
+            J, g, st = s.adjoint(ts, u_gt)
+        assert abs(J - solver.objective(us, u_gt)) < 1e-8 * J
+        assert g.shape == go.shape
+        assert np.linalg.norm(g - go) < 1e-6 * np.linalg.norm(go), (precision, np.linalg.norm(g - go) / np.linalg.norm(go))
+
+
+def test_config4_reduced_directional_fd_and_checkpoints():
+    """Config 4 on an 80 x 40 x 2 mesh of the plate (the true per-element fields perturbed
+    by a seeded +-5 %): the adjoint gradient along a seeded random direction against central
+    differences of J with the FP64 forward (relative step 1e-6), and checkpointing every 4
+    steps equal bit for bit to storing every step (8 load steps)."""
+    mesh, bc, mat, th_true, ts = inputs.config4_problem(80, 40, 2, n_steps=20)
+    rng = np.random.default_rng(11)
+    th = th_true * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, th_true.shape))
+    u_gt = _config4_target(mesh, ts[:8])
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13)
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", theta=th, **opts) as s:
+        J, g, _ = s.adjoint(ts[:4], u_gt[:4])
+    v = np.zeros_like(th)
+    v[:, [2, 3, 4, 8]] = rng.standard_normal((mesh.n_el, 4))
+    d = v * th
+    h = 1e-6
+    Jpm = []
+    for sgn in (1.0, -1.0):
+        with hfe.from_inputs(mesh, bc, mat, precision="fp64", theta=th + sgn * h * d, **opts) as s:
+            u, _ = s.forward(ts[:4])
+        Jpm.append(float(np.sum((u - u_gt[:4]) ** 2)))
+    fd = (Jpm[0] - Jpm[1]) / (2.0 * h)
+    ad = float(np.sum(g * d))
+    assert abs(fd - ad) < 1e-4 * abs(ad), (fd, ad)
+    for precision in ("fp64", "mixed"):
+        out = []
+        for k in (1, 4):
+            o = dict(opts) if precision == "fp64" else {}
+            with hfe.from_inputs(mesh, bc, mat, precision=precision, theta=th, ckpt_every=k, **o) as s:
+                out.append(s.adjoint(ts[:8], u_gt)[1])
+        assert np.array_equal(out[0], out[1]), precision
