@@ -127,6 +127,14 @@ typedef struct {
                              every iteration on the device (grid barriers, convergence tested each
                              iteration); 0: chunks of pcg_check_every iterations as CUDA-graph
                              launches with a host convergence check between chunks */
+  int adaptive;           /* 1 (default): adaptive load stepping - a load step whose Newton
+                             fails is rejected, the state restored, and retried with the
+                             increment times cutback (substeps between the requested load
+                             factors, which are hit exactly); 0: a failed step is an error */
+  double cutback;         /* increment factor after a rejected step (default 0.5); the increment
+                             grows by 1/cutback after two accepted substeps in a row */
+  int max_cutbacks;       /* the increment is never cut below (requested interval) x
+                             cutback^max_cutbacks (default 8: 1/256 of the interval) */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */
@@ -144,6 +152,8 @@ typedef struct {
   double total_ms;        /* wall time of the call */
   int64_t bicgstab_solves;/* Newton corrections whose CG met negative curvature and that were
                              solved again by BiCGSTAB */
+  int64_t substeps;       /* accepted load (sub)steps */
+  int64_t cutbacks;       /* rejected attempts (adaptive stepping) */
 } hfe_stats;
 
 /* Sizes of the internal data (for tests and benchmarks). */

@@ -692,6 +692,11 @@ __global__ void hist64_to_mixed_kernel(const double* h64, void* hm, int64_t n_gp
 
 struct AdjointWork {
   int n_steps = 0, n_ckpt = 0, k = 1;
+  // the forward pass's accepted (sub)steps: load factors, the requested step each one reaches
+  // (-1 for an intermediate substep of adaptive stepping), and the capacity of u_all / ckpt
+  std::vector<double> t_sub;
+  std::vector<int> mark;
+  int cap_sub = 0;
   LinSys ls;                 // FP64 system (K, CG vectors)
   std::vector<void*> mem;
   double *u_all = nullptr, *ckpt = nullptr, *h_prev = nullptr, *h_trial = nullptr, *h_tmp = nullptr;
@@ -722,7 +727,7 @@ hfe_status aalloc(hfe_handle* h, AdjointWork* w, T** p, size_t n) {
 
 hfe_status ensure_work(hfe_handle* h, int n_steps) {
   const int k = std::max(1, h->opt.ckpt_every);
-  const int n_ckpt = (n_steps + k - 1) / k;    // h^j for j = 0, k, 2k, ... < n_steps
+  const int n_ckpt = (n_steps + k - 1) / k;    // h^j for j = 0, k, 2k, ... (grows with substeps)
   AdjointWork* w = h->adj;
   if (w != nullptr && w->n_steps == n_steps && w->k == k) return HFE_OK;
   delete w;
@@ -753,7 +758,8 @@ hfe_status ensure_work(hfe_handle* h, int n_steps) {
     w->ls.fp64 = true;
   }
   HFE_TRY(aalloc(h, w, &w->u_all, ndof * n_steps));
-  HFE_TRY(aalloc(h, w, &w->ckpt, 8 * ngp * n_ckpt));
+  HFE_TRY(aalloc(h, w, &w->ckpt, 8 * ngp * (n_ckpt + 1)));
+  w->cap_sub = n_steps;
   HFE_TRY(aalloc(h, w, &w->h_prev, 8 * ngp));
   HFE_TRY(aalloc(h, w, &w->h_trial, 8 * ngp));
   HFE_TRY(aalloc(h, w, &w->h_tmp, 8 * ngp));
@@ -771,9 +777,41 @@ hfe_status ensure_work(hfe_handle* h, int n_steps) {
   return HFE_OK;
 }
 
+// Room for m substeps in u_all and their checkpoints (adaptive stepping adds substeps):
+// the buffers double, the stored part is copied over.
+template <typename T>
+hfe_status regrow(hfe_handle* h, AdjointWork* w, T** p, size_t keep, size_t n_new) {
+  T* q = nullptr;
+  HFE_TRY(aalloc(h, w, &q, n_new));
+  if (keep) HFE_TRY(cuda_check(h, cudaMemcpyAsync(q, *p, sizeof(T) * keep, cudaMemcpyDeviceToDevice, h->s), "copy"));
+  HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "copy"));
+  for (auto& x : w->mem)
+    if (x == *p) {
+      cudaFree(x);
+      x = w->mem.back();
+      w->mem.pop_back();
+      break;
+    }
+  *p = q;
+  return HFE_OK;
+}
+
+hfe_status ensure_substeps(hfe_handle* h, AdjointWork* w, int m) {
+  if (m <= w->cap_sub) return HFE_OK;
+  const int cap = std::max(m, 2 * w->cap_sub);
+  const size_t ndof = h->n_dof, ngp = h->n_gp;
+  HFE_TRY(regrow(h, w, &w->u_all, ndof * (size_t)w->t_sub.size(), ndof * (size_t)cap));
+  const int nck = cap / w->k + 1;
+  HFE_TRY(regrow(h, w, &w->ckpt, 8 * ngp * (size_t)(w->n_ckpt + 1), 8 * ngp * (size_t)(nck + 1)));
+  w->n_ckpt = nck;
+  w->cap_sub = cap;
+  return HFE_OK;
+}
+
 // FP64 history h^j: copy of the checkpoint at or below j, then one FP64 residual sweep per
 // step (h^{i+1} = H(u^{i+1}, h^i)); dst must differ from the scratch buffers used here.
-hfe_status history_at(hfe_handle* h, AdjointWork* w, const double* t, int j, double* dst) {
+hfe_status history_at(hfe_handle* h, AdjointWork* w, int j, double* dst) {
+  const double* t = w->t_sub.data();
   const size_t ngp = h->n_gp;
   const int j0 = (j / w->k) * w->k;
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, w->ckpt + 8 * ngp * (j0 / w->k), 8 * ngp * sizeof(double),
@@ -791,12 +829,11 @@ hfe_status history_at(hfe_handle* h, AdjointWork* w, const double* t, int j, dou
 // takes one FP64 Newton iteration at the converged mixed state and installs the FP64 history.
 struct AdjHook : StepHook {
   AdjointWork* w;
-  const double* t;
   int64_t pcg_iters = 0;
-  hfe_status before_commit(hfe_handle* h, int n) override {
+  hfe_status before_commit(hfe_handle* h, double t_new) override {
     if (h->fp64) return HFE_OK;
     const size_t ngp = h->n_gp;
-    HFE_TRY(sweep_ex(h, h->u, t[n], HFE_SWEEP_TANGENT, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
+    HFE_TRY(sweep_ex(h, h->u, t_new, HFE_SWEEP_TANGENT, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
     HFE_TRY(read_status(h));
     HFE_TRY(check_sweep_status(h));
     int64_t it = 0;
@@ -806,21 +843,25 @@ struct AdjHook : StepHook {
     HFE_TRY(pst);
     pcg_iters += h->h_sc->iters;
     add_update<double>(h->u, (const double*)w->ls.vx, h->freem, h->n_dof, h->s);
-    HFE_TRY(sweep_ex(h, h->u, t[n], HFE_SWEEP_RESIDUAL, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
+    HFE_TRY(sweep_ex(h, h->u, t_new, HFE_SWEEP_RESIDUAL, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
     HFE_TRY(read_status(h));
     HFE_TRY(check_sweep_status(h));
     const unsigned blocks = (unsigned)((8 * ngp + 255) / 256);
     hist64_to_mixed_kernel<<<blocks, 256, 0, h->s>>>(w->h_trial, h->hist_trial, (int64_t)ngp);
     return HFE_OK;
   }
-  hfe_status after_commit(hfe_handle* h, int n) override {
+  hfe_status after_commit(hfe_handle* h, double t_new, int marker) override {
     const size_t ngp = h->n_gp;
-    HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->u_all + (size_t)n * h->n_dof, h->u, h->n_dof * sizeof(double),
+    const int m = (int)w->t_sub.size();   // index of this substep
+    HFE_TRY(ensure_substeps(h, w, m + 1));
+    HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->u_all + (size_t)m * h->n_dof, h->u, h->n_dof * sizeof(double),
                                           cudaMemcpyDeviceToDevice, h->s), "copy"));
-    const double* hn = h->fp64 ? reinterpret_cast<const double*>(h->hist) : w->h_trial;   // h^{n+1}
+    w->t_sub.push_back(t_new);
+    w->mark.push_back(marker);
+    const double* hn = h->fp64 ? reinterpret_cast<const double*>(h->hist) : w->h_trial;   // h^{m+1}
     if (!h->fp64) std::swap(w->h_prev, w->h_trial);
-    const int j = n + 1;   // history index after this step
-    if (j < w->n_steps && j % w->k == 0)
+    const int j = m + 1;   // history index after this substep
+    if (j % w->k == 0)
       HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->ckpt + 8 * ngp * (j / w->k), h->fp64 ? hn : w->h_prev,
                                             8 * ngp * sizeof(double), cudaMemcpyDeviceToDevice, h->s), "copy"));
     return HFE_OK;
@@ -878,10 +919,11 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
                      "copy"));
   h->t_state = 0.0;
   h->pred_valid = false;
+  w->t_sub.clear();
+  w->mark.clear();
   HFE_TRY(copy_in(h, w->ugt, u_target, ndof * n_steps * sizeof(double)));
   AdjHook hook;
   hook.w = w;
-  hook.t = t.data();
   hfe_stats fst;
   std::memset(&fst, 0, sizeof(fst));
   cudaEvent_t ta, tb, tc;
@@ -891,22 +933,27 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
   cudaEventRecord(ta, h->s);
   HFE_TRY(newton_steps(h, n_steps, t.data(), nullptr, nullptr, nullptr, &fst, &hook));
   cudaEventRecord(tb, h->s);
-  // misfit
-  for (int n = 0; n < n_steps; ++n)
-    misfit_kernel<<<256, 256, 0, h->s>>>(w->u_all + (size_t)n * ndof, w->ugt + (size_t)n * ndof, h->freem, wgt,
-                                         w->rhs, (int64_t)ndof, w->part, w->ticket, w->Jn + n);
-  // reverse pass
+  // misfit at the requested load factors (substeps in between do not enter J)
+  const int M = (int)w->t_sub.size();
+  for (int m = 0; m < M; ++m)
+    if (w->mark[m] >= 0)
+      misfit_kernel<<<256, 256, 0, h->s>>>(w->u_all + (size_t)m * ndof, w->ugt + (size_t)w->mark[m] * ndof, h->freem,
+                                           wgt, w->rhs, (int64_t)ndof, w->part, w->ticket, w->Jn + w->mark[m]);
+  // reverse pass over the accepted (sub)steps
   HFE_TRY(cuda_check(h, cudaMemsetAsync(w->mu, 0, 7 * ngp * sizeof(double), h->s), "memset"));
   HFE_TRY(cuda_check(h, cudaMemsetAsync(w->thbar, 0, 11 * (size_t)h->n_el * sizeof(double), h->s), "memset"));
   int64_t adj_pcg = 0;
-  for (int n = n_steps - 1; n >= 0; --n) {
+  for (int n = M - 1; n >= 0; --n) {
     const double* un = w->u_all + (size_t)n * ndof;
-    HFE_TRY(history_at(h, w, t.data(), n, w->h_prev));           // h^n: history before step n
-    HFE_TRY(sweep_ex(h, un, t[n], HFE_SWEEP_TANGENT, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
-    misfit_kernel<<<256, 256, 0, h->s>>>(un, w->ugt + (size_t)n * ndof, h->freem, wgt, w->rhs, (int64_t)ndof, w->part,
-                                         w->ticket, w->R64);    // rhs = -dJ^n/du^n (R64 as scratch)
+    HFE_TRY(history_at(h, w, n, w->h_prev));           // h^n: history before substep n
+    HFE_TRY(sweep_ex(h, un, w->t_sub[n], HFE_SWEEP_TANGENT, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
+    if (w->mark[n] >= 0)                                // rhs = -dJ^n/du^n (R64 as scratch)
+      misfit_kernel<<<256, 256, 0, h->s>>>(un, w->ugt + (size_t)w->mark[n] * ndof, h->freem, wgt, w->rhs,
+                                           (int64_t)ndof, w->part, w->ticket, w->R64);
+    else
+      HFE_TRY(cuda_check(h, cudaMemsetAsync(w->rhs, 0, ndof * sizeof(double), h->s), "memset"));
     HFE_TRY(cuda_check(h, cudaMemsetAsync(w->hbar, 0, 7 * ngp * sizeof(double), h->s), "memset"));
-    if (n < n_steps - 1) {   // pass A: history cotangent mu^{n+1} of h^{n+1} = H(u^n, h^n)
+    if (n < M - 1) {   // pass A: history cotangent mu^{n+1} of h^{n+1} = H(u^n, h^n)
       launch_vjp(h, w, true, un, w->h_prev, nullptr);
       sub_free_kernel<<<(unsigned)((ndof + 255) / 256), 256, 0, h->s>>>(w->rhs, w->ubar, h->freem, (int64_t)ndof);
     }

@@ -371,6 +371,9 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->predictor = 1;
   o->ew_forcing = 0;
   o->pcg_persistent = 1;
+  o->adaptive = 1;
+  o->cutback = 0.5;
+  o->max_cutbacks = 8;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
@@ -386,6 +389,9 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   else hfe_default_options(&h->opt, HFE_PRECISION_FP64);
   if (h->opt.precision != HFE_PRECISION_FP64 && h->opt.precision != HFE_PRECISION_MIXED)
     return fail(h, HFE_EINVAL, "options: unknown precision");
+  if (h->opt.adaptive && !(h->opt.cutback > 0.0 && h->opt.cutback < 1.0))
+    return fail(h, HFE_EINVAL, "options: cutback must lie in (0, 1)");
+  if (h->opt.max_cutbacks < 0) return fail(h, HFE_EINVAL, "options: max_cutbacks must be >= 0");
   h->fp64 = h->opt.precision == HFE_PRECISION_FP64;
   h->user = reinterpret_cast<cudaStream_t>(stream);
   HFE_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"));
@@ -710,175 +716,227 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   std::memset(&loc, 0, sizeof(loc));
   const bool u_out_dev = is_device_ptr(u_out_dev_or_host);
   const int64_t bicg0 = h->n_bicgstab;
-  for (int n = 0; n < n_steps; ++n) {
-    double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
-    double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
-    bool last_tight = !h->opt.predictor || !h->opt.ew_forcing;   // the predictor solve is loose
-    bool force_tight = false;
-    int backtracks = 0;
-    const double t_prev = h->t_state;
-    HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u_start, h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
-                       "copy"));
-    if (h->opt.predictor) {
-      // tangent predictor on the converged start-of-step state u_{n-1}:
-      // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment,
-      // with K and R of the previous step's last Newton iteration (its consistent tangent at
-      // u_{n-1}); without them (first step, or after the state was set) the sweep at
-      // (u_{n-1}, h_{n-1})
-      if (!h->pred_valid) {
-        HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
+  // one load (sub)step from the stored state to t_new: predictor, Newton, commit; marker =
+  // index of the requested load factor it reaches, or -1 for an intermediate substep
+  auto one_step = [&](const double t_new, const int marker) -> hfe_status {
+      double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
+      double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
+      bool last_tight = !h->opt.predictor || !h->opt.ew_forcing;   // the predictor solve is loose
+      bool force_tight = false;
+      int backtracks = 0;
+      const double t_prev = h->t_state;
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u_start, h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
+                         "copy"));
+      if (h->opt.predictor) {
+        // tangent predictor on the converged start-of-step state u_{n-1}:
+        // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment,
+        // with K and R of the previous step's last Newton iteration (its consistent tangent at
+        // u_{n-1}); without them (first step, or after the state was set) the sweep at
+        // (u_{n-1}, h_{n-1})
+        if (!h->pred_valid) {
+          HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
+          HFE_TRY(read_status(h));
+          loc.sweeps++;
+          HFE_TRY(check_sweep_status(h));
+        }
+        h->pred_valid = false;
+        HFE_TRY(cuda_check(h, cudaMemsetAsync(h->tmp64, 0, sizeof(double) * h->n_dof, h->s), "memset"));
+        set_dirichlet(h->tmp64, h->fixed_dof, h->fixed_val, t_new - t_prev, h->n_fixed, h->s);
+        Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+        if (h->fp64) {
+          spmv_rows<double>(K, (const double*)h->K, h->freem, h->tmp64, (double*)h->vq, h->s);
+          predictor_rhs<double>(h->R, (const double*)h->vq, h->f_ext, t_new - t_prev, h->freem, h->b64, h->n_dof, h->s);
+        } else {
+          to_float(h->tmp64, (float*)h->vp, h->n_dof, h->s);
+          spmv_rows<float>(K, (const float*)h->K, h->freem, (const float*)h->vp, (float*)h->vq, h->s);
+          predictor_rhs<float>(h->R, (const float*)h->vq, h->f_ext, t_new - t_prev, h->freem, h->b64, h->n_dof, h->s);
+        }
+        free_norm(h->b64, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
+        HFE_TRY(read_status(h));
+        ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
+        set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
+        if (h->h_sc->norm2 > 0.0) {
+          cudaEventRecord(h->t0, h->s);
+          if (h->opt.ew_forcing) h->pcg_rtol_now = std::max(h->opt.pcg_rtol, 1e-3);   // predictor: rough solve
+          h->allow_truncated = true;
+          h->allow_indefinite = true;
+          hfe_status pst = solve_any(h, h->b64, 1.0, nullptr);
+          h->allow_truncated = false;
+          h->allow_indefinite = false;
+          h->pcg_rtol_now = 0.0;
+          HFE_TRY(pst);
+          cudaEventRecord(h->t1, h->s);
+          cudaEventSynchronize(h->t1);
+          loc.solve_ms += elapsed(h->t0, h->t1);
+          loc.pcg_iters += h->h_sc->iters;
+          if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
+          else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
+          step_scale = 1.0;
+        }
+      } else {
+        set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
+      }
+      int stall = 0;
+      bool conv = false;
+      for (int it = 0; it <= h->opt.newton_maxit; ++it) {
+        cudaEventRecord(h->t0, h->s);
+        HFE_TRY(sweep(h, h->u, t_new, HFE_SWEEP_TANGENT, h->R, nullptr));
+        cudaEventRecord(h->t1, h->s);
+        free_norm(h->R, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
         HFE_TRY(read_status(h));
         loc.sweeps++;
+        loc.sweep_ms += elapsed(h->t0, h->t1);
+        if ((h->h_status->detj > 0 || h->h_status->nonfinite > 0 || h->h_sc->nonfinite > 0) && step_scale > 0.0 &&
+            backtracks < 6) {
+          // the last correction inverted an element or produced non-finite values: halve it
+          const double c = -0.5 * step_scale;
+          if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s, c);
+          else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s, c);
+          step_scale *= 0.5;
+          ++backtracks;
+          --it;
+          continue;
+        }
         HFE_TRY(check_sweep_status(h));
-      }
-      h->pred_valid = false;
-      HFE_TRY(cuda_check(h, cudaMemsetAsync(h->tmp64, 0, sizeof(double) * h->n_dof, h->s), "memset"));
-      set_dirichlet(h->tmp64, h->fixed_dof, h->fixed_val, t[n] - t_prev, h->n_fixed, h->s);
-      Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
-      if (h->fp64) {
-        spmv_rows<double>(K, (const double*)h->K, h->freem, h->tmp64, (double*)h->vq, h->s);
-        predictor_rhs<double>(h->R, (const double*)h->vq, h->f_ext, t[n] - t_prev, h->freem, h->b64, h->n_dof, h->s);
-      } else {
-        to_float(h->tmp64, (float*)h->vp, h->n_dof, h->s);
-        spmv_rows<float>(K, (const float*)h->K, h->freem, (const float*)h->vp, (float*)h->vq, h->s);
-        predictor_rhs<float>(h->R, (const float*)h->vq, h->f_ext, t[n] - t_prev, h->freem, h->b64, h->n_dof, h->s);
-      }
-      free_norm(h->b64, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
-      HFE_TRY(read_status(h));
-      ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
-      set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
-      if (h->h_sc->norm2 > 0.0) {
+        loc.plastic_gps = h->h_status->plastic;
+        loc.max_local_iters = std::max<int32_t>(loc.max_local_iters, (int32_t)h->h_status->max_local_iters);
+        if (h->h_sc->nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite residual");
+        const double nrm = std::sqrt(h->h_sc->norm2);
+        loc.last_residual = nrm;
+        if (ref < 0.0) ref = std::max(nrm, h->opt.newton_atol);
+        if (nrm <= h->opt.newton_rtol * ref) {
+          // accept only after a correction solved to pcg_rtol: with an ill-conditioned K a small
+          // residual after a loose solve can still hide a large error in the soft modes
+          if (last_tight || !h->opt.ew_forcing) { conv = true; break; }
+          force_tight = true;
+        }
+        const bool slow = it >= 1 && nrm > 0.5 * prev;
+        if (!h->fp64 && it >= 2) {   // mixed: accept a stagnated residual below newton_stag_tol
+          // (only after solves at the tightest tolerance, so an inexact solve cannot stall it)
+          stall = (slow && last_tight) ? stall + 1 : 0;
+          if (stall >= 2 && nrm <= h->opt.newton_stag_tol * ref) { conv = true; break; }
+        }
+        prev = nrm;
+        if (it == h->opt.newton_maxit) break;
+        int64_t pit = 0;
         cudaEventRecord(h->t0, h->s);
-        if (h->opt.ew_forcing) h->pcg_rtol_now = std::max(h->opt.pcg_rtol, 1e-3);   // predictor: rough solve
+        // inexact Newton: Eisenstat-Walker forcing (choice 2, gamma = 0.9, alpha = 2) with their
+        // safeguard, bounded below by pcg_rtol; the converged solution does not depend on it
+        if (h->opt.ew_forcing) {
+          double eta = 1e-3;
+          if (prev_solve > 0.0) {
+            const double ratio = nrm / prev_solve;
+            eta = 0.9 * ratio * ratio;
+            const double safe = 0.9 * eta_prev * eta_prev;
+            if (safe > 0.1) eta = std::max(eta, safe);
+          }
+          eta = std::min(eta, 0.5);
+          if (slow || force_tight) eta = h->opt.pcg_rtol;   // slow progress or final correction: solve tightly
+          eta = std::max(eta, h->opt.pcg_rtol);
+          h->pcg_rtol_now = eta;
+          eta_prev = eta;
+        }
+        prev_solve = nrm;
+        last_tight = !h->opt.ew_forcing || h->pcg_rtol_now <= h->opt.pcg_rtol * 1.0000001;
         h->allow_truncated = true;
         h->allow_indefinite = true;
-        hfe_status pst = solve_any(h, h->b64, 1.0, nullptr);
+        h->pcg_truncated = false;
+        hfe_status sst = solve_any(h, h->R, -1.0, &pit);
         h->allow_truncated = false;
         h->allow_indefinite = false;
         h->pcg_rtol_now = 0.0;
-        HFE_TRY(pst);
+        HFE_TRY(sst);
+        if (h->pcg_truncated) last_tight = false;
         cudaEventRecord(h->t1, h->s);
         cudaEventSynchronize(h->t1);
         loc.solve_ms += elapsed(h->t0, h->t1);
         loc.pcg_iters += h->h_sc->iters;
+        (void)pit;
         if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
         else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
         step_scale = 1.0;
+        backtracks = 0;
+        loc.newton_iters++;
       }
-    } else {
-      set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t[n], h->n_fixed, h->s);
+      if (!conv)
+        return fail(h, HFE_ENEWTON, "Newton did not converge at t = " + std::to_string(t_new) + ", |R| = " +
+                                        std::to_string(loc.last_residual));
+      if (hook) HFE_TRY(hook->before_commit(h, t_new));
+      if (sigma_out != nullptr && marker == n_steps - 1) {
+        if (h->sigma == nullptr) {
+          if (cudaMalloc(&h->sigma, sizeof(double) * 6 * h->n_gp) != cudaSuccess) return fail(h, HFE_ENOMEM, "sigma");
+        }
+        HFE_TRY(sweep(h, h->u, t_new, HFE_SWEEP_RESIDUAL, h->R, h->sigma));
+        HFE_TRY(read_status(h));
+        HFE_TRY(copy_out(h, sigma_out, h->sigma, sizeof(double) * 6 * h->n_gp));
+      }
+      std::swap(h->hist, h->hist_trial);   // commit h_n = H(u_n, h_{n-1})
+      if (!h->fp64) launch_sigma_cache(h->hist, false, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+      if (u_out_dev_or_host != nullptr && marker >= 0) {
+        double* dst = u_out_dev_or_host + (size_t)marker * h->n_dof;
+        if (u_out_dev) HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, h->u, 8 * h->n_dof, cudaMemcpyDeviceToDevice, h->s), "copy"));
+        else HFE_TRY(copy_out(h, dst, h->u, sizeof(double) * h->n_dof));
+      }
+      h->t_state = t_new;
+      h->pred_valid = true;
+      if (hook) HFE_TRY(hook->after_commit(h, t_new, marker));
+      return HFE_OK;
+  };
+  // a failed attempt leaves the stored state at the last converged step
+  auto attempt = [&](const double t_new, const int marker) -> hfe_status {
+    const hfe_status s = one_step(t_new, marker);
+    if (s != HFE_OK) {
+      h->pred_valid = false;
+      h->allow_truncated = h->allow_indefinite = false;
+      h->pcg_rtol_now = 0.0;
+      cudaMemcpyAsync(h->u, h->u_start, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s);
+      cudaStreamSynchronize(h->s);
     }
-    int stall = 0;
-    bool conv = false;
-    for (int it = 0; it <= h->opt.newton_maxit; ++it) {
-      cudaEventRecord(h->t0, h->s);
-      HFE_TRY(sweep(h, h->u, t[n], HFE_SWEEP_TANGENT, h->R, nullptr));
-      cudaEventRecord(h->t1, h->s);
-      free_norm(h->R, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
-      HFE_TRY(read_status(h));
-      loc.sweeps++;
-      loc.sweep_ms += elapsed(h->t0, h->t1);
-      if ((h->h_status->detj > 0 || h->h_status->nonfinite > 0 || h->h_sc->nonfinite > 0) && step_scale > 0.0 &&
-          backtracks < 6) {
-        // the last correction inverted an element or produced non-finite values: halve it
-        const double c = -0.5 * step_scale;
-        if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s, c);
-        else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s, c);
-        step_scale *= 0.5;
-        ++backtracks;
-        --it;
+    return s;
+  };
+  // Adaptive load stepping (Sec. 2.2 Implementation Aspects): each requested load factor is
+  // first reached in one step; a step whose Newton fails (no convergence, an inverted
+  // element, non-finite values, a failed solve or local return mapping) is rejected and
+  // retried with the increment times `cutback`, down to the interval times
+  // cutback^max_cutbacks; after two accepted substeps in a row the increment grows back by
+  // 1/cutback, clipped so that the requested load factors are hit exactly.  A reduced
+  // increment carries over to the next interval.
+  double dt_carry = 0.0;
+  for (int n = 0; n < n_steps; ++n) {
+    int cuts = 0, ok_run = 0;
+    double dt_try = t[n] - h->t_state;
+    const double dt_min = dt_try * std::pow(h->opt.cutback, (double)h->opt.max_cutbacks);
+    if (dt_carry > 0.0 && dt_carry < dt_try) dt_try = dt_carry;
+    for (;;) {
+      const double remaining = t[n] - h->t_state;
+      const double dt = std::min(dt_try, remaining);
+      const bool hits = dt >= remaining * (1.0 - 1e-12);
+      const double t_new = hits ? t[n] : h->t_state + dt;
+      const hfe_status s = attempt(t_new, hits ? n : -1);
+      if (s == HFE_OK) {
+        loc.substeps++;
+        if (hits) break;
+        if (++ok_run >= 2) {
+          dt_try = dt / h->opt.cutback;
+          ok_run = 0;
+        } else {
+          dt_try = dt;
+        }
         continue;
       }
-      HFE_TRY(check_sweep_status(h));
-      loc.plastic_gps = h->h_status->plastic;
-      loc.max_local_iters = std::max<int32_t>(loc.max_local_iters, (int32_t)h->h_status->max_local_iters);
-      if (h->h_sc->nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite residual");
-      const double nrm = std::sqrt(h->h_sc->norm2);
-      loc.last_residual = nrm;
-      if (ref < 0.0) ref = std::max(nrm, h->opt.newton_atol);
-      if (nrm <= h->opt.newton_rtol * ref) {
-        // accept only after a correction solved to pcg_rtol: with an ill-conditioned K a small
-        // residual after a loose solve can still hide a large error in the soft modes
-        if (last_tight || !h->opt.ew_forcing) { conv = true; break; }
-        force_tight = true;
+      const bool recoverable = s == HFE_ENEWTON || s == HFE_EDETJ || s == HFE_ENONFINITE || s == HFE_EPCG ||
+                               s == HFE_ELOCAL;
+      if (!h->opt.adaptive || !recoverable || dt * h->opt.cutback < dt_min * (1.0 - 1e-9)) {
+        loc.bicgstab_solves = h->n_bicgstab - bicg0;
+        if (st) *st = loc;
+        return s;
       }
-      const bool slow = it >= 1 && nrm > 0.5 * prev;
-      if (!h->fp64 && it >= 2) {   // mixed: accept a stagnated residual below newton_stag_tol
-        // (only after solves at the tightest tolerance, so an inexact solve cannot stall it)
-        stall = (slow && last_tight) ? stall + 1 : 0;
-        if (stall >= 2 && nrm <= h->opt.newton_stag_tol * ref) { conv = true; break; }
-      }
-      prev = nrm;
-      if (it == h->opt.newton_maxit) break;
-      int64_t pit = 0;
-      cudaEventRecord(h->t0, h->s);
-      // inexact Newton: Eisenstat-Walker forcing (choice 2, gamma = 0.9, alpha = 2) with their
-      // safeguard, bounded below by pcg_rtol; the converged solution does not depend on it
-      if (h->opt.ew_forcing) {
-        double eta = 1e-3;
-        if (prev_solve > 0.0) {
-          const double ratio = nrm / prev_solve;
-          eta = 0.9 * ratio * ratio;
-          const double safe = 0.9 * eta_prev * eta_prev;
-          if (safe > 0.1) eta = std::max(eta, safe);
-        }
-        eta = std::min(eta, 0.5);
-        if (slow || force_tight) eta = h->opt.pcg_rtol;   // slow progress or final correction: solve tightly
-        eta = std::max(eta, h->opt.pcg_rtol);
-        h->pcg_rtol_now = eta;
-        eta_prev = eta;
-      }
-      prev_solve = nrm;
-      last_tight = !h->opt.ew_forcing || h->pcg_rtol_now <= h->opt.pcg_rtol * 1.0000001;
-      h->allow_truncated = true;
-      h->allow_indefinite = true;
-      h->pcg_truncated = false;
-      hfe_status sst = solve_any(h, h->R, -1.0, &pit);
-      h->allow_truncated = false;
-      h->allow_indefinite = false;
-      h->pcg_rtol_now = 0.0;
-      HFE_TRY(sst);
-      if (h->pcg_truncated) last_tight = false;
-      cudaEventRecord(h->t1, h->s);
-      cudaEventSynchronize(h->t1);
-      loc.solve_ms += elapsed(h->t0, h->t1);
-      loc.pcg_iters += h->h_sc->iters;
-      (void)pit;
-      if (h->fp64) add_update<double>(h->u, (const double*)h->vx, h->freem, h->n_dof, h->s);
-      else add_update<float>(h->u, (const float*)h->vx, h->freem, h->n_dof, h->s);
-      step_scale = 1.0;
-      backtracks = 0;
-      loc.newton_iters++;
+      ++cuts;
+      loc.cutbacks++;
+      ok_run = 0;
+      dt_try = dt * h->opt.cutback;
     }
-    if (!conv) {
-      loc.bicgstab_solves = h->n_bicgstab - bicg0;
-      if (st) *st = loc;
-      // leave the stored state at the last converged step
-      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u, h->u_start, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice,
-                                            h->s), "copy"));
-      HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "restore"));
-      return fail(h, HFE_ENEWTON, "Newton did not converge at step " + std::to_string(n) + ", |R| = " +
-                                      std::to_string(loc.last_residual));
-    }
-    if (hook) HFE_TRY(hook->before_commit(h, n));
-    if (sigma_out != nullptr && n == n_steps - 1) {
-      if (h->sigma == nullptr) {
-        if (cudaMalloc(&h->sigma, sizeof(double) * 6 * h->n_gp) != cudaSuccess) return fail(h, HFE_ENOMEM, "sigma");
-      }
-      HFE_TRY(sweep(h, h->u, t[n], HFE_SWEEP_RESIDUAL, h->R, h->sigma));
-      HFE_TRY(read_status(h));
-      HFE_TRY(copy_out(h, sigma_out, h->sigma, sizeof(double) * 6 * h->n_gp));
-    }
-    std::swap(h->hist, h->hist_trial);   // commit h_n = H(u_n, h_{n-1})
-    if (!h->fp64) launch_sigma_cache(h->hist, false, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
-    if (u_out_dev_or_host != nullptr) {
-      double* dst = u_out_dev_or_host + (size_t)n * h->n_dof;
-      if (u_out_dev) HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, h->u, 8 * h->n_dof, cudaMemcpyDeviceToDevice, h->s), "copy"));
-      else HFE_TRY(copy_out(h, dst, h->u, sizeof(double) * h->n_dof));
-    }
-    h->t_state = t[n];
-    h->pred_valid = true;
-    if (hook) HFE_TRY(hook->after_commit(h, n));
+    dt_carry = cuts > 0 ? dt_try : 0.0;
     loc.steps_done = n + 1;
   }
   if (hist_out) HFE_TRY(export_history(h, h->hist, hist_out));

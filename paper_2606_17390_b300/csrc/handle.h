@@ -113,8 +113,10 @@ namespace hfe {
 // Called by the Newton driver around each commit (used by the adjoint's forward pass).
 struct StepHook {
   virtual ~StepHook() {}
-  virtual hfe_status before_commit(hfe_handle* h, int step) = 0;
-  virtual hfe_status after_commit(hfe_handle* h, int step) = 0;
+  // t_new: load factor of the (sub)step being committed; marker: index of the requested
+  // load factor it reaches, -1 for an intermediate substep of adaptive stepping
+  virtual hfe_status before_commit(hfe_handle* h, double t_new) = 0;
+  virtual hfe_status after_commit(hfe_handle* h, double t_new, int marker) = 0;
 };
 
 // order the internal stream after the caller's stream, and the caller's after ours on exit

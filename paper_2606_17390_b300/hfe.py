@@ -47,14 +47,16 @@ class Options(C.Structure):
                 ("newton_maxit", C.c_int), ("newton_stag_tol", C.c_double), ("pcg_rtol", C.c_double),
                 ("pcg_maxit", C.c_int), ("pcg_check_every", C.c_int), ("precond", C.c_int),
                 ("local_maxit", C.c_int), ("local_tol", C.c_double), ("ckpt_every", C.c_int),
-                ("predictor", C.c_int), ("ew_forcing", C.c_int), ("pcg_persistent", C.c_int)]
+                ("predictor", C.c_int), ("ew_forcing", C.c_int), ("pcg_persistent", C.c_int),
+                ("adaptive", C.c_int), ("cutback", C.c_double), ("max_cutbacks", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int64), ("pcg_iters", C.c_int64), ("sweeps", C.c_int64),
                 ("plastic_gps", C.c_int64), ("local_fail", C.c_int64), ("max_local_iters", C.c_int32),
                 ("steps_done", C.c_int32), ("last_residual", C.c_double), ("sweep_ms", C.c_double),
-                ("solve_ms", C.c_double), ("total_ms", C.c_double), ("bicgstab_solves", C.c_int64)]
+                ("solve_ms", C.c_double), ("total_ms", C.c_double), ("bicgstab_solves", C.c_int64),
+                ("substeps", C.c_int64), ("cutbacks", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

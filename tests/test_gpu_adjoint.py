@@ -149,3 +149,26 @@ def test_config4_reduced_directional_fd_and_checkpoints():
             with hfe.from_inputs(mesh, bc, mat, precision=precision, theta=th, ckpt_every=k, **o) as s:
                 out.append(s.adjoint(ts[:8], u_gt)[1])
         assert np.array_equal(out[0], out[1]), precision
+
+
+def test_adjoint_through_adaptive_substeps():
+    """On the homogeneous config-0 problem (stretched to 25 %) J depends only on the
+    displacements at the requested load factors, which do not depend on the substeps, so the
+    discrete adjoint through whatever substeps adaptive stepping takes (newton_maxit = 3
+    forces them) must equal the oracle's adjoint with plain steps."""
+    mesh, _, mat, _ = inputs.config0_problem()
+    bc = inputs.roller_uniaxial_bcs(mesh, 0.25, axis=0)
+    ts = np.array([0.4, 1.0])
+    th = mat.theta_vector() * (1 + 0.05 * np.random.default_rng(2).uniform(-1, 1, 11))
+    th[0:2] = mat.theta_vector()[0:2]
+    rng = np.random.default_rng(5)
+    u_gt = 0.01 * rng.standard_normal((2, mesh.n_dof))
+    prob = solver.from_inputs(mesh, bc, mat, th)
+    us, hs, _ = solver.forward(prob, ts, rtol=1e-13)
+    go = solver.adjoint(prob, ts, us, hs, u_gt)
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", theta=th, newton_rtol=1e-12, pcg_rtol=1e-13,
+                         newton_maxit=3) as s:
+        J, g, st = s.adjoint(ts, u_gt)
+    assert st["cutbacks"] > 0
+    assert abs(J - solver.objective(us, u_gt)) < 1e-9 * J
+    _check(g[0], go)

@@ -127,3 +127,45 @@ def test_persistent_and_chunked_cg_agree(precision):
         us.append(u)
     tol = 1e-10 if precision == "fp64" else 1e-5
     assert _per_step_rel(us[0], us[1]) < tol
+
+
+def test_adaptive_stepping_closed_form_and_restore():
+    """Adaptive load stepping: on the homogeneous config-0 problem (here stretched to 25 %)
+    the solution at the requested load factors is the uniaxial closed form whatever substeps
+    are taken, so two requested steps (10 %, 25 %) with newton_maxit = 3, which forces
+    rejected attempts and substeps, must still match it to 1e-10 (FP64); without adaptive
+    stepping the same run fails and leaves the stored state at the last converged step."""
+    from tests.test_oracle_global import _uniaxial_closed_form
+    mesh, _, mat, _ = inputs.config0_problem()
+    bc = inputs.roller_uniaxial_bcs(mesh, 0.25, axis=0)
+    ts = np.array([0.4, 1.0])
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13, newton_maxit=3)
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", **opts) as s:
+        u, st = s.forward(ts)
+    assert st["cutbacks"] > 0 and st["substeps"] > 2, st
+    for k, t in enumerate(ts):
+        uex = _uniaxial_closed_form(5.0 * t, mesh)[0]      # closed form written for 0.05 t
+        assert np.abs(u[k] - uex).max() < 1e-10 * np.abs(uex).max()
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", adaptive=0, **opts) as s:
+        u1, _ = s.forward(np.array([0.001]))       # a small elastic first step converges
+        with pytest.raises(hfe.HfeError):
+            s.forward(ts[1:])
+        u_after, _ = s.get_state()
+        assert s.get_load() == pytest.approx(0.001)
+    assert np.array_equal(u_after, u1[0])
+
+
+def test_adaptive_stepping_plate_in_few_steps():
+    """The perforated plate at 100 x 50 x 2 in 10 requested steps: without adaptive stepping
+    the second step fails; with it the run completes through substeps and the final state is
+    in equilibrium (residual of the committed state below the Newton tolerance)."""
+    mesh, bc, mat, ts = inputs.config3_problem(100, 50, 2, n_steps=10)
+    with hfe.from_inputs(mesh, bc, mat, precision="mixed") as s:
+        u, st = s.forward(ts)
+        assert st["steps_done"] == 10 and st["substeps"] >= 10
+        rn = np.empty(1)
+        s.sweep(u[-1], 1.0, tangent=False, rnorm_out=rn)
+    assert np.isfinite(u).all()
+    # out-of-balance force of the committed state: Newton-tolerance level, against
+    # reaction forces of order E * 2 % * 100 mm^2 = 1.4e5 N
+    assert rn[0] < 1.0, rn
