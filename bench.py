@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
     ap.add_argument("--adjoint-nx", type=int, default=200, help="plate resolution of the adjoint ratio run (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
+    ap.add_argument("--forward-steps", type=int, default=10)
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
     args = ap.parse_args()
 
@@ -359,7 +361,24 @@ def main():
                                f"{m3.n_dof} dofs), {args.adjoint_steps} steps, 9 Swift/Hill parameters",
                    "forward_s": t_fwd, "gradient_call_s": t_adj, "reverse_s": ast["solve_ms"] * 1e-3,
                    "gradient_over_forward": t_adj / t_fwd, "reverse_over_forward": ast["solve_ms"] * 1e-3 / t_fwd,
-                   "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"]}
+                   "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"],
+                   "forward_substeps": fst["substeps"], "gradient_substeps": ast["substeps"]}
+
+    # end-to-end forward solve of the 100^3 clamped-platen compression (10 load steps, mixed):
+    # Newton, PCG and substep counts, and the in-solve Gauss-point update rate
+    forward = None
+    if args.forward_n > 0:
+        m2, bc2, mat2, t2 = inputs.config2_problem(args.forward_n, args.forward_steps)
+        with hfe.from_inputs(m2, bc2, mat2, precision=args.precision, stream=stream.cuda_stream) as s2:
+            t0 = time.perf_counter()
+            _, st2 = s2.forward(t2, want_u=False)
+            wall = time.perf_counter() - t0
+        forward = {"workload": f"hex8 cube {args.forward_n}^3 ({m2.n_dof} dofs), 10 % compression between clamped "
+                               f"platens, {args.forward_steps} load steps, {args.precision}",
+                   "wall_s": wall, "newton_iters": st2["newton_iters"], "pcg_iters": st2["pcg_iters"],
+                   "substeps": st2["substeps"], "cutbacks": st2["cutbacks"], "sweeps": st2["sweeps"],
+                   "sweep_s": st2["sweep_ms"] * 1e-3, "solve_s": st2["solve_ms"] * 1e-3,
+                   "in_solve_gp_per_s": st2["sweeps"] * 8 * m2.n_el / (st2["sweep_ms"] * 1e-3)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -378,7 +397,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
-                "pcg": pcg, "adjoint": adjoint,
+                "pcg": pcg, "adjoint": adjoint, "forward": forward,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

@@ -833,19 +833,31 @@ struct AdjHook : StepHook {
   hfe_status before_commit(hfe_handle* h, double t_new) override {
     if (h->fp64) return HFE_OK;
     const size_t ngp = h->n_gp;
-    HFE_TRY(sweep_ex(h, h->u, t_new, HFE_SWEEP_TANGENT, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
-    HFE_TRY(read_status(h));
-    HFE_TRY(check_sweep_status(h));
-    int64_t it = 0;
-    h->allow_indefinite = true;   // an indefinite tangent is solved by BiCGSTAB
-    const hfe_status pst = solve_sys(h, w->ls, w->R64, -1.0, &it);
-    h->allow_indefinite = false;
-    HFE_TRY(pst);
-    pcg_iters += h->h_sc->iters;
-    add_update<double>(h->u, (const double*)w->ls.vx, h->freem, h->n_dof, h->s);
-    HFE_TRY(sweep_ex(h, h->u, t_new, HFE_SWEEP_RESIDUAL, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
-    HFE_TRY(read_status(h));
-    HFE_TRY(check_sweep_status(h));
+    // FP64 refinement of the mixed-converged state: the FP64 residual (FP64 sweep with the FP64
+    // history), corrected with the mixed tangent of the last Newton iteration (still in the
+    // handle) solved to 1e-2 in FP32; each pass contracts the error by about
+    // max(1e-2, kappa eps_32).  Stops once the FP64 residual is 1e-3 of its first value (the
+    // accuracy one FP64 Newton iteration would reach) or after kPolishPasses passes.
+    constexpr int kPolishPasses = 4;
+    double r0 = -1.0;
+    for (int pass = 0;; ++pass) {
+      HFE_TRY(sweep_ex(h, h->u, t_new, HFE_SWEEP_RESIDUAL, w->R64, nullptr, w->ls.K, w->h_prev, w->h_trial, true));
+      free_norm(w->R64, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
+      HFE_TRY(read_status(h));
+      HFE_TRY(check_sweep_status(h));
+      const double rn = std::sqrt(h->h_sc->norm2);
+      if (r0 < 0.0) r0 = rn;
+      if (!(rn > 1e-3 * r0) || pass == kPolishPasses) break;
+      int64_t it = 0;
+      h->allow_indefinite = true;   // an indefinite tangent is solved by BiCGSTAB
+      h->pcg_rtol_now = 1e-2;
+      const hfe_status pst = solve_sys(h, h->ls, w->R64, -1.0, &it);
+      h->allow_indefinite = false;
+      h->pcg_rtol_now = 0.0;
+      HFE_TRY(pst);
+      pcg_iters += h->h_sc->iters;
+      add_update<float>(h->u, (const float*)h->ls.vx, h->freem, h->n_dof, h->s);
+    }
     const unsigned blocks = (unsigned)((8 * ngp + 255) / 256);
     hist64_to_mixed_kernel<<<blocks, 256, 0, h->s>>>(w->h_trial, h->hist_trial, (int64_t)ngp);
     return HFE_OK;

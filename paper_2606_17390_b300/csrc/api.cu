@@ -734,9 +734,12 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         // u_{n-1}); without them (first step, or after the state was set) the sweep at
         // (u_{n-1}, h_{n-1})
         if (!h->pred_valid) {
+          cudaEventRecord(h->t0, h->s);
           HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
+          cudaEventRecord(h->t1, h->s);
           HFE_TRY(read_status(h));
           loc.sweeps++;
+          loc.sweep_ms += elapsed(h->t0, h->t1);
           HFE_TRY(check_sweep_status(h));
         }
         h->pred_valid = false;

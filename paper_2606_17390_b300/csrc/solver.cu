@@ -435,6 +435,58 @@ __device__ __forceinline__ bool grid_allreduce(GridSync* gs, const double* part,
   return s_ok != 0;
 }
 
+// out = K in on the rows [n0, n1) (fixed rows 0; in is zero on fixed dofs), returning this
+// thread's share of out . w over those rows
+template <typename R>
+__device__ __forceinline__ double spmv_range(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
+                                             const R* __restrict__ vals, const uint8_t* __restrict__ freem,
+                                             const R* in, R* out, const R* w, int64_t n0, int64_t n1) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int kWarps = kBlock / 32;
+  double dot = 0.0;
+  for (int64_t r0 = n0 + warp; r0 < n1; r0 += 2 * kWarps) {
+    const int64_t r1 = r0 + kWarps;
+    const bool has1 = r1 < n1;
+    const int64_t b0 = rowptr[r0], e0 = rowptr[r0 + 1];
+    const int64_t b1 = has1 ? rowptr[r1] : 0, e1 = has1 ? rowptr[r1 + 1] : 0;
+    const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
+    R acc[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+    const int nmax = nb0 > nb1 ? nb0 : nb1;
+    for (int j = lane; j < nmax; j += 32) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int nb = t == 0 ? nb0 : nb1;
+        if (j < nb) {
+          const int64_t blk = (t == 0 ? b0 : b1) + j;
+          const int64_t col = cols[blk];
+          const R* v = vals + blk * 9;
+          const R x0 = in[3 * col], x1 = in[3 * col + 1], x2 = in[3 * col + 2];
+          acc[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
+          acc[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
+          acc[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc[t][i] = warp_sum_r(acc[t][i]);
+    if (lane < 6) {
+      const int t = lane / 3, i = lane % 3;
+      if (t == 0 || has1) {
+        const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
+        const R o = t == 0 ? (i == 0 ? acc[0][0] : (i == 1 ? acc[0][1] : acc[0][2]))
+                           : (i == 0 ? acc[1][0] : (i == 1 ? acc[1][1] : acc[1][2]));
+        const R od = freem[d] ? o : R(0);
+        out[d] = od;
+        dot += (double)od * (double)w[d];
+      }
+    }
+  }
+  return dot;
+}
+
 template <typename R>
 struct PersistArgs {
   const int64_t* rowptr;
@@ -445,6 +497,7 @@ struct PersistArgs {
   const double* b;
   double bscale, rtol2;
   R *x, *r, *z, *pa, *pb, *q;
+  const R* x0;    // initial guess (zero on the fixed dofs), nullptr = 0
   int64_t n_nodes, maxit;
   int block3;
   PcgScalars* sc;
@@ -484,16 +537,23 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
     ++red;
     return grid_allreduce(&sc->gs, pp, t0, t1);
   };
-  // r = b on the free dofs, x = 0, z = M^-1 r, p_prev = 0 (beta = 0 in the first iteration)
-  double rz = 0.0, rr = 0.0;
+  // x = x0 (or 0), r = b - K x0 on the free dofs, z = M^-1 r, p_prev = 0 (beta = 0 in the
+  // first iteration); convergence is measured against |b|, as for a zero start
+  if (a.x0 != nullptr) {
+    spmv_range(a.rowptr, a.cols, a.vals, a.freem, a.x0, a.q, a.x0, n0, n1);
+    __syncthreads();
+  }
+  double rz = 0.0, rr = 0.0, bb = 0.0, unused0 = 0.0;
   for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
     R rv[3], zv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int64_t d = 3 * n + i;
-      rv[i] = a.freem[d] ? (R)(a.bscale * a.b[d]) : R(0);
+      const R bd = a.freem[d] ? (R)(a.bscale * a.b[d]) : R(0);
+      bb += (double)bd * (double)bd;
+      rv[i] = a.x0 != nullptr ? bd - a.q[d] : bd;
       a.r[d] = rv[i];
-      a.x[d] = R(0);
+      a.x[d] = a.x0 != nullptr ? a.x0[d] : R(0);
       a.pa[d] = R(0);
     }
     precond_apply(a.minv, a.block3, n, rv, zv);
@@ -505,10 +565,16 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
     }
   }
   if (!allreduce(rz, rr, rz, rr)) return;
-  const double rr0 = rr;
+  if (!allreduce(bb, 0.0, bb, unused0)) return;
+  const double rr0 = bb;
   const double target = a.rtol2 * rr0;
-  int breakdown = (isfinite(rz) && isfinite(rr)) ? 0 : 1;
+  int breakdown = (isfinite(rz) && isfinite(rr) && isfinite(bb)) ? 0 : 1;
   int done = (!breakdown && rr <= target) ? 1 : 0;
+  if (!breakdown && bb == 0.0) {   // b = 0: x = 0 whatever the initial guess
+    for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) a.x[d] = R(0);
+    rr = 0.0;
+    done = 1;
+  }
   double beta = 0.0, pq = 0.0;
   int64_t it = 0;
   R* pprev = a.pa;
@@ -633,58 +699,6 @@ struct BicgArgs {
   PcgScalars* sc;
   double* part;
 };
-
-// out = K in on the rows [n0, n1) (fixed rows 0; in is zero on fixed dofs), returning this
-// thread's share of out . w over those rows
-template <typename R>
-__device__ __forceinline__ double spmv_range(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
-                                             const R* __restrict__ vals, const uint8_t* __restrict__ freem,
-                                             const R* in, R* out, const R* w, int64_t n0, int64_t n1) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  constexpr int kWarps = kBlock / 32;
-  double dot = 0.0;
-  for (int64_t r0 = n0 + warp; r0 < n1; r0 += 2 * kWarps) {
-    const int64_t r1 = r0 + kWarps;
-    const bool has1 = r1 < n1;
-    const int64_t b0 = rowptr[r0], e0 = rowptr[r0 + 1];
-    const int64_t b1 = has1 ? rowptr[r1] : 0, e1 = has1 ? rowptr[r1 + 1] : 0;
-    const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
-    R acc[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
-    const int nmax = nb0 > nb1 ? nb0 : nb1;
-    for (int j = lane; j < nmax; j += 32) {
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int nb = t == 0 ? nb0 : nb1;
-        if (j < nb) {
-          const int64_t blk = (t == 0 ? b0 : b1) + j;
-          const int64_t col = cols[blk];
-          const R* v = vals + blk * 9;
-          const R x0 = in[3 * col], x1 = in[3 * col + 1], x2 = in[3 * col + 2];
-          acc[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
-          acc[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
-          acc[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) acc[t][i] = warp_sum_r(acc[t][i]);
-    if (lane < 6) {
-      const int t = lane / 3, i = lane % 3;
-      if (t == 0 || has1) {
-        const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
-        const R o = t == 0 ? (i == 0 ? acc[0][0] : (i == 1 ? acc[0][1] : acc[0][2]))
-                           : (i == 0 ? acc[1][0] : (i == 1 ? acc[1][1] : acc[1][2]));
-        const R od = freem[d] ? o : R(0);
-        out[d] = od;
-        dot += (double)od * (double)w[d];
-      }
-    }
-  }
-  return dot;
-}
 
 template <typename R>
 __global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const BicgArgs<R> a) {
@@ -847,9 +861,9 @@ void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>
 template <typename R>
 cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
-                           double* part, int64_t part_slots, cudaStream_t s) {
+                           double* part, int64_t part_slots, cudaStream_t s, const R* x0) {
   // matrix bytes (values + columns) against the 126 MB L2: resident -> latency-bound form
-  const bool streams = (double)K.n_blocks * (9.0 * sizeof(R) + 4.0) > 96e6;
+  const bool streams = (double)K.n_blocks * (9.0 * sizeof(R) + 4.0) > 160e6;
   const void* fn = streams ? (const void*)pcg_persistent_kernel<R, 6> : (const void*)pcg_persistent_kernel<R, 4>;
   const int cap = streams ? 6 : 4;
   int dev = 0, n_sm = 0, per_sm = 0;
@@ -864,7 +878,7 @@ cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, Pc
   const int64_t useful = (K.n_nodes + kBlock / 32 - 1) / (kBlock / 32);   // a warp per row at least
   if (grid > useful) grid = useful;
   if (grid < 1) grid = 1;
-  PersistArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.z, v.p, v.p2, v.q,
+  PersistArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.z, v.p, v.p2, v.q, x0,
                    K.n_nodes, maxit, block3, sc, part};
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
@@ -939,10 +953,10 @@ template void pcg_iteration<double>(const Csr&, const double*, const uint8_t*, P
                                     double*, cudaStream_t);
 template cudaError_t pcg_persistent<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int,
                                             const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
-                                            cudaStream_t);
+                                            cudaStream_t, const float*);
 template cudaError_t pcg_persistent<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int,
                                              const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
-                                             cudaStream_t);
+                                             cudaStream_t, const double*);
 template cudaError_t bicgstab_persistent<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int,
                                                  const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
                                                  cudaStream_t);

@@ -63,12 +63,13 @@ template <typename R>
 void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3, PcgScalars* sc,
                    double* part, cudaStream_t s);
 // Whole PCG solve in one cooperative launch (grid barriers, no host round trips): x = K^-1 b
-// to |r| <= sqrt(rtol2) |r0| or maxit iterations; results in *sc (iters, rr, rr0, rz, pq,
-// breakdown, done, gs.timeout).  *sc must be zeroed before the launch.
+// to |r| <= sqrt(rtol2) |b| or maxit iterations, from x0 (nullptr = 0; must not alias v's
+// vectors); results in *sc (iters, rr, rr0 = |b|^2, rz, pq, breakdown, done, gs.timeout).
+// *sc must be zeroed before the launch.
 template <typename R>
 cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
-                           double* part, int64_t part_slots, cudaStream_t s);
+                           double* part, int64_t part_slots, cudaStream_t s, const R* x0 = nullptr);
 // Preconditioned BiCGSTAB in one cooperative launch for a symmetric indefinite (or
 // nonsymmetric) K with the same SPD block-Jacobi preconditioner: x (v.x) = K^-1 b; uses v.r,
 // v.rh, v.p, v.q (as v), v.y, v.p2 (as s), v.z, v.t.  Results in *sc as for pcg_persistent.
