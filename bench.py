@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
     ap.add_argument("--adjoint-nx", type=int, default=200, help="plate resolution of the adjoint ratio run (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--adjoint-config", type=int, default=3, choices=(3, 4),
+                    help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
@@ -343,12 +345,22 @@ def main():
     # reverse sweep
     adjoint = None
     if args.adjoint_nx > 0:
-        m3, bc3, mat3, t3 = inputs.config3_problem(args.adjoint_nx, args.adjoint_nx // 2,
-                                                   4 if args.adjoint_nx >= 200 else 2, args.adjoint_steps)
-        with hfe.from_inputs(m3, bc3, mat3, precision="mixed", stream=stream.cuda_stream) as s3:
+        nx = args.adjoint_nx
+        if args.adjoint_config == 4:
+            # per-element F, G, H, sigma0 fields (config 4); the gradient is taken at the
+            # spatially uniform mean parameters, the start of an inverse run
+            m3, bc3, mat3, th_true, t3 = inputs.config4_problem(nx, nx // 2, 4 if nx >= 200 else 2,
+                                                                args.adjoint_steps)
+            th_eval = np.tile(mat3.theta_vector(), (m3.n_el, 1))
+            what = "per-element F, G, H, sigma0 (4 x n_el parameters), Voce"
+        else:
+            m3, bc3, mat3, t3 = inputs.config3_problem(nx, nx // 2, 4 if nx >= 200 else 2, args.adjoint_steps)
+            th_true = mat3.theta_vector()
+            th_eval = inputs.perturbed_theta(th_true)
+            what = "9 Swift/Hill parameters"
+        with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th_true, stream=stream.cuda_stream) as s3:
             u_true, _ = s3.forward(t3)
         u_gt = u_true + inputs.noise(u_true.shape, 1e-3 * np.abs(u_true).max())
-        th_eval = inputs.perturbed_theta(mat3.theta_vector())
         with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th_eval, stream=stream.cuda_stream) as s3:
             s3.set_state(None, None)
             t0 = time.perf_counter()
@@ -357,8 +369,8 @@ def main():
             t0 = time.perf_counter()
             J3, g3, ast = s3.adjoint(t3, u_gt)
             t_adj = time.perf_counter() - t0
-        adjoint = {"workload": f"perforated plate {args.adjoint_nx}x{args.adjoint_nx // 2} ({m3.n_el} elements, "
-                               f"{m3.n_dof} dofs), {args.adjoint_steps} steps, 9 Swift/Hill parameters",
+        adjoint = {"workload": f"config {args.adjoint_config}: perforated plate {nx}x{nx // 2} ({m3.n_el} elements, "
+                               f"{m3.n_dof} dofs), {args.adjoint_steps} steps, {what}",
                    "forward_s": t_fwd, "gradient_call_s": t_adj, "reverse_s": ast["solve_ms"] * 1e-3,
                    "gradient_over_forward": t_adj / t_fwd, "reverse_over_forward": ast["solve_ms"] * 1e-3 / t_fwd,
                    "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"],
