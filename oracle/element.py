@@ -50,13 +50,18 @@ def gradients(Xe):
     return g, det * GP_W[None, :]
 
 
-def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tangent"):
+def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tangent", fbar=False):
     """All elements at once.
 
     X (n_nodes,3), conn (n_el,8), u (n_dof,), hist (n_el,8,7) history at t_n,
     theta (11,) or (n_el,11), Theta None/(3,3)/(n_el,3,3).
     Returns Re (n_el,24), Ke (n_el,24,24) if jacobians, h_new (n_el,8,7), the Gauss-point
     dict of material.gauss_point (arrays flattened over (el, gp)), g and wdet.
+
+    fbar: the F-bar element of Sec. 2.2.4 (Eq. Fbar): the constitutive model receives
+    Fbar = (Jbar / J)^(1/3) F with Jbar = (1/V_e) int_e J dV, the residual is
+    R^e_I = int P(Fbar) . grad0 N_I dV, and K^e = dR^e/dd^e follows by the chain rule through
+    Fbar (J at the point and Jbar of the element), which makes K non-symmetric.
     """
     conn = np.asarray(conn, dtype=np.int64)
     n_el = conn.shape[0]
@@ -64,6 +69,8 @@ def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tan
     ue = u.reshape(-1, 3)[conn]                        # (n_el, 8, 3)
     g, wdet = gradients(Xe)
     F = np.eye(3) + np.einsum("eai,egaj->egij", ue, g)  # F = I + sum_a u_a (x) g_a
+    if fbar:
+        return _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_el)
     theta = np.asarray(theta, dtype=np.float64)
     th = np.broadcast_to(theta if theta.ndim == 1 else theta[:, None, :], (n_el, 8, 11))
     if Theta is None:
@@ -80,5 +87,40 @@ def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tan
     if jacobians is not None:
         A = gp["A"].reshape(n_el, 8, 3, 3, 3, 3)
         Ke = np.einsum("eg,egaJ,egiJkL,egbL->eaibk", wdet, g, A, g).reshape(n_el, 24, 24)
+        out["Ke"] = Ke
+    return out
+
+
+def _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_el):
+    J = np.linalg.det(F)                                          # (n_el, 8)
+    Jbar = np.einsum("eg,eg->e", wdet, J) / wdet.sum(axis=1)      # volume average of J
+    s = np.cbrt(Jbar[:, None] / J)                                # (Jbar / J)^(1/3)
+    Fb = s[..., None, None] * F
+    theta = np.asarray(theta, dtype=np.float64)
+    th = np.broadcast_to(theta if theta.ndim == 1 else theta[:, None, :], (n_el, 8, 11))
+    if Theta is None:
+        Th = np.broadcast_to(np.eye(3), (n_el, 8, 3, 3))
+    else:
+        Theta = np.asarray(Theta, dtype=np.float64)
+        Th = np.broadcast_to(Theta if Theta.ndim == 2 else Theta[:, None], (n_el, 8, 3, 3))
+    gp = material.gauss_point(Fb.reshape(-1, 3, 3), hist[..., :6].reshape(-1, 6),
+                              hist[..., 6].reshape(-1), th.reshape(-1, 11), hardening,
+                              Th.reshape(-1, 3, 3), jacobians=jacobians)
+    P = gp["P"].reshape(n_el, 8, 3, 3)                            # P(Fbar)
+    Re = np.einsum("eg,egiJ,egaJ->eai", wdet, P, g).reshape(n_el, 24)
+    out = dict(Re=Re, h_new=gp["h_new"].reshape(n_el, 8, 7), gp=gp, g=g, wdet=wdet, F=F, Fbar=Fb, Jbar=Jbar)
+    if jacobians is not None:
+        A = gp["A"].reshape(n_el, 8, 3, 3, 3, 3)                  # dP/dFbar
+        Finv = np.linalg.inv(F)
+        # spatial gradients F^-T g_b (the derivative of J is J F^-T)
+        sg = np.einsum("egLk,egbL->egbk", Finv, g)
+        # dJbar/du_bk = (1/V) sum_q w det J0 J_q (F_q^-T g_b)_k
+        dJbar = np.einsum("eg,eg,egbk->ebk", wdet, J, sg) / wdet.sum(axis=1)[:, None, None]
+        # dFbar_mn / du_bk = s (delta_mk g_b,n - 1/3 F_mn (F^-T g_b)_k) + Fbar_mn / (3 Jbar) dJbar/du_bk
+        eye = np.eye(3)
+        dFb = (s[..., None, None, None, None]
+               * (np.einsum("mk,egbn->egmnbk", eye, g) - np.einsum("egmn,egbk->egmnbk", F, sg) / 3.0)
+               + np.einsum("egmn,ebk->egmnbk", Fb, dJbar) / (3.0 * Jbar)[:, None, None, None, None, None])
+        Ke = np.einsum("eg,egaJ,egiJmn,egmnbk->eaibk", wdet, g, A, dFb).reshape(n_el, 24, 24)
         out["Ke"] = Ke
     return out

@@ -43,6 +43,7 @@ class Problem:
     hardening: str
     Theta: np.ndarray | None = None
     f_ext: np.ndarray | None = None   # nodal dead load at t = 1 (n_dof,), optional
+    fbar: bool = False                # F-bar element (Eq. Fbar); K is then non-symmetric
 
     @property
     def n_dof(self):
@@ -53,11 +54,11 @@ class Problem:
         return self.conn.shape[0]
 
 
-def from_inputs(mesh, bc, mat, theta=None):
+def from_inputs(mesh, bc, mat, theta=None, fbar=False):
     th = mat.theta_vector() if theta is None else np.asarray(theta, dtype=np.float64)
     return Problem(X=mesh.X, conn=mesh.conn.astype(np.int64), fixed_dof=bc.dof,
                    fixed_val=bc.value, theta=th, hardening=mat.hardening,
-                   Theta=None if np.allclose(mat.Theta, np.eye(3)) else mat.Theta)
+                   Theta=None if np.allclose(mat.Theta, np.eye(3)) else mat.Theta, fbar=fbar)
 
 
 def element_dofs(conn):
@@ -86,7 +87,7 @@ def free_mask(prob):
 def residual(prob, u, hist, t=1.0, jacobians="tangent"):
     """R(u) = f_int(u; h_n) - t f_ext and, with jacobians, K = dR/du."""
     es = element.element_sweep(prob.X, prob.conn, u, hist, prob.theta, prob.hardening,
-                               prob.Theta, jacobians=jacobians)
+                               prob.Theta, jacobians=jacobians, fbar=prob.fbar)
     R = assemble_R(prob, es["Re"])
     if prob.f_ext is not None:
         R = R - t * prob.f_ext
@@ -186,6 +187,8 @@ def _dofs_from_F_cotangent(prob, es, Fbar):
 
 def adjoint(prob, t_steps, us, hs, u_gt, w=1.0, per_element=False):
     """dJ/dtheta by the discrete adjoint; (11,) for uniform theta, (n_el, 11) if per_element."""
+    if prob.fbar:
+        raise NotImplementedError("the adjoint of the F-bar element is not part of the oracle")
     free = free_mask(prob)
     n_el = prob.n_el
     N = len(t_steps)
@@ -212,6 +215,8 @@ def adjoint(prob, t_steps, us, hs, u_gt, w=1.0, per_element=False):
 
 def direct_sensitivity(prob, t_steps, us, hs, u_gt, dtheta, w=1.0):
     """dJ/dtheta . dtheta by forward (tangent) propagation; dtheta (11,) or (n_el, 11)."""
+    if prob.fbar:
+        raise NotImplementedError("the sensitivity of the F-bar element is not part of the oracle")
     free = free_mask(prob)
     n_el = prob.n_el
     dth = np.broadcast_to(np.asarray(dtheta, dtype=np.float64), (n_el, 11))

@@ -171,3 +171,52 @@ def test_adjoint_per_element_directional():
     assert abs(d_dir - np.sum(g * v)) < 1e-10 * np.abs(g * v).sum()
     fd = solver.fd_directional(prob, ts, u_gt, v, h=1e-6)
     assert abs(fd - np.sum(g * v)) < 1e-5 * abs(np.sum(g * v))
+
+
+@pytest.mark.parametrize("case", ["elastic", "plastic"])
+def test_fbar_element_tangent_vs_fd(case):
+    """F-bar element (Eq. Fbar): K^e = dR^e/dd^e against central differences of R^e on a
+    distorted element (the chain rule through J at the point and the element's Jbar; K^e is
+    not symmetric)."""
+    X, conn, u = _one_element_state(9, {"elastic": 1e-4, "plastic": 0.04}[case])
+    mat = inputs.config0_material()
+    hist = np.zeros((1, 8, 7))
+    if case != "elastic":
+        ep, al = inputs.random_history(8, 5, 0.005, 0.02)
+        hist[0, :, :6], hist[0, :, 6] = ep, al
+    es = element.element_sweep(X, conn, u, hist, mat.theta_vector(), "swift", fbar=True)
+    Ke = es["Ke"][0]
+    assert np.abs(Ke - Ke.T).max() > 1e-8 * np.abs(Ke).max()   # not symmetric
+    h = 1e-7
+    fd = np.empty((24, 24))
+    for j in range(24):
+        up, um = u.copy(), u.copy()
+        up[j] += h
+        um[j] -= h
+        fd[:, j] = (element.element_sweep(X, conn, up, hist, mat.theta_vector(), "swift", None, None, fbar=True)["Re"][0] -
+                    element.element_sweep(X, conn, um, hist, mat.theta_vector(), "swift", None, None, fbar=True)["Re"][0]) / (2 * h)
+    ed = solver.element_dofs(conn)[0]
+    assert np.abs(fd[:, ed] - Ke).max() < 1e-6 * np.abs(Ke).max()
+
+
+def test_fbar_equals_standard_for_affine_motion_and_closed_form():
+    """For an affine displacement J is uniform in the element, so Jbar = J, Fbar = F and the
+    F-bar residual and history equal the standard ones; the homogeneous uniaxial forward
+    (config 0) therefore keeps its closed form with the F-bar element."""
+    X, conn, _ = _one_element_state(11, 0.0)
+    G = 0.03 * np.random.default_rng(12).uniform(-1, 1, (3, 3))
+    u = (X @ G.T).ravel()
+    mat = inputs.config0_material()
+    ep, al = inputs.random_history(8, 13, 0.005, 0.02)
+    hist = np.zeros((1, 8, 7))
+    hist[0, :, :6], hist[0, :, 6] = ep, al
+    a = element.element_sweep(X, conn, u, hist, mat.theta_vector(), "swift")
+    b = element.element_sweep(X, conn, u, hist, mat.theta_vector(), "swift", fbar=True)
+    assert np.abs(a["Re"] - b["Re"]).max() < 1e-12 * np.abs(a["Re"]).max()
+    assert np.abs(a["h_new"] - b["h_new"]).max() < 1e-14
+    mesh, bc, mat, ts = inputs.config0_problem(n=3, n_steps=3)
+    prob = solver.from_inputs(mesh, bc, mat, fbar=True)
+    us, hs, _ = solver.forward(prob, ts, rtol=1e-13)
+    for n, t in enumerate(ts):
+        uex = _uniaxial_closed_form(t, mesh)[0]
+        assert np.abs(us[n] - uex).max() < 1e-11 * np.abs(uex).max()
