@@ -917,6 +917,7 @@ void launch_vjp(hfe_handle* h, AdjointWork* w, bool pass_a, const double* u, con
 hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const double* u_target, double wgt,
                        double* J_out, double* grad_out, hfe_stats* stats) {
   auto w0 = std::chrono::steady_clock::now();
+  if (h->opt.fbar) return fail(h, HFE_EINVAL, "adjoint: the F-bar element has no adjoint here");
   std::vector<double> t(t_in, t_in + n_steps);
   HFE_TRY(ensure_work(h, n_steps));
   AdjointWork* w = h->adj;

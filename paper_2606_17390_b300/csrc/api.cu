@@ -166,6 +166,7 @@ hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, d
   a.n_gp = h->n_gp;
   a.local_maxit = h->opt.local_maxit;
   a.local_tol = h->opt.local_tol;
+  a.fbar = h->opt.fbar;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->s), "memset"));
   launch_gp_sweep(a, fp64, mode, h->P.color_off, h->s);
   return HFE_OK;
@@ -334,8 +335,55 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   return HFE_OK;
 }
 
+// Non-symmetric K (F-bar element): preconditioned BiCGSTAB in one cooperative launch.
+template <typename R>
+hfe_status bicg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters_out) {
+  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  PcgVecs<R> v = vecs<R>(ls);
+  const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
+  precond_setup<R>(K, (const R*)ls.K, h->diag_slot, h->freem, v.minv, block3, h->bad, h->s);
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
+  const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
+  HFE_TRY(cuda_check(h, bicgstab_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
+                                               h->opt.pcg_maxit, h->sc, h->part, partial_slots(), h->s),
+                     "BiCGSTAB launch"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
+  HFE_TRY(read_status(h));
+  const PcgScalars& sc = *h->h_sc;
+  if (iters_out) *iters_out = sc.iters;
+  if (sc.gs.timeout) return fail(h, HFE_ECUDA, "BiCGSTAB: a grid barrier wait ran out");
+  if (!std::isfinite(sc.rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
+  if (sc.done) return HFE_OK;
+  if (sc.breakdown)
+    return fail(h, HFE_EPCG, "BiCGSTAB breakdown (" + std::string(sc.breakdown == 1 ? "rh.v = 0" : sc.breakdown == 3 ? "|t| = 0" :
+                                                                   sc.breakdown == 5 ? "too many restarts" : "non-finite") +
+                                 ") after " + std::to_string(sc.iters) + " iterations, |r|/|b| = " +
+                                 std::to_string(std::sqrt(sc.rr / sc.rr0)));
+  return fail(h, HFE_EPCG, "BiCGSTAB did not converge: |r|/|b| = " + std::to_string(std::sqrt(sc.rr / sc.rr0)));
+}
+
 hfe_status solve_sys(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters) {
-  return ls.fp64 ? pcg_solve<double>(h, ls, b, bscale, iters) : pcg_solve<float>(h, ls, b, bscale, iters);
+  if (!h->opt.fbar)
+    return ls.fp64 ? pcg_solve<double>(h, ls, b, bscale, iters) : pcg_solve<float>(h, ls, b, bscale, iters);
+  if (ls.fp64) return bicg_solve<double>(h, ls, b, bscale, iters);
+  // mixed path: BiCGSTAB diverges in FP32 on ill-conditioned meshes (its recurrences are not
+  // monotone), so the FP32 tangent is widened to FP64 and solved there; x back in FP32
+  LinSys& l64 = h->ls_fb64;
+  if (l64.K == nullptr) {
+    unsigned char* p = nullptr;
+    HFE_TRY(dalloc(h, &p, sizeof(double) * 9 * h->P.n_blocks)); l64.K = p;
+    for (void** v : {&l64.vx, &l64.vr, &l64.vz, &l64.vp, &l64.vq, &l64.vp2, &l64.vrh, &l64.vy, &l64.vt, &l64.vxt}) {
+      HFE_TRY(dalloc(h, &p, sizeof(double) * h->n_dof));
+      *v = p;
+    }
+    HFE_TRY(dalloc(h, &p, sizeof(double) * 9 * h->n_nodes)); l64.vminv = p;
+    l64.fp64 = true;
+  }
+  to_double((const float*)ls.K, (double*)l64.K, 9 * h->P.n_blocks, h->s);
+  HFE_TRY(bicg_solve<double>(h, l64, b, bscale, iters));
+  to_float((const double*)l64.vx, (float*)ls.vx, h->n_dof, h->s);
+  return HFE_OK;
 }
 
 hfe_status solve_any(hfe_handle* h, const double* b, double bscale, int64_t* iters) {
@@ -374,6 +422,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->adaptive = 1;
   o->cutback = 0.5;
   o->max_cutbacks = 8;
+  o->fbar = 0;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,

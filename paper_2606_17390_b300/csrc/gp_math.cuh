@@ -33,6 +33,7 @@ template <> struct Num<float> {
   static constexpr float dd1_series = 1e-3f;  // |x| below which log1p(x)/x uses its series
   static constexpr float dd2_tau = 1e-2f;     // relative spread below which f2 uses f''(m)/2
   __device__ static float log1p_(float x) { return log1pf(x); }
+  __device__ static float expm1_(float x) { return expm1f(x); }
   __device__ static float sqrt_(float x) { return sqrtf(x); }
   __device__ static float rsqrt_(float x) { return rsqrtf(x); }
   // FP32 quotients of the mixed path: the hardware reciprocal times a (within 2 ulp for the
@@ -45,6 +46,7 @@ template <> struct Num<double> {
   static constexpr double dd1_series = 1e-4;
   static constexpr double dd2_tau = 1e-5;
   __device__ static double log1p_(double x) { return log1p(x); }
+  __device__ static double expm1_(double x) { return expm1(x); }
   __device__ static double sqrt_(double x) { return sqrt(x); }
   __device__ static double rsqrt_(double x) { return rsqrt(x); }
   __device__ static double div(double a, double b) { return a / b; }

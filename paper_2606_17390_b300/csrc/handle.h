@@ -95,6 +95,7 @@ struct hfe_handle {
   DevStatus* h_status = nullptr;
   int* h_bad = nullptr;
   hfe::LinSys ls;              // the handle's own system (K and vectors above)
+  hfe::LinSys ls_fb64;         // F-bar on the mixed path: FP64 copy of K and FP64 Krylov vectors
   size_t device_bytes = 0;
   std::string err;
   std::vector<void*> allocs;

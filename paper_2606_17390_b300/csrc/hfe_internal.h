@@ -77,6 +77,7 @@ struct SweepArgs {
   int64_t n_gp;
   int local_maxit;
   double local_tol;
+  int fbar;                // F-bar element (Eq. Fbar)
 };
 
 void launch_material_setup(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,

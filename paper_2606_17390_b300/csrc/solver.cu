@@ -684,6 +684,9 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
 // on the right, for Newton corrections whose tangent turned out indefinite (CG met p.Kp <= 0).
 // Same row split, fixed-order reductions and fused barriers as the CG kernel: one plain
 // barrier and four barrier-reductions per iteration.
+constexpr int kBicgRestart = 200;       // iterations between true-residual restarts
+constexpr int kBicgMaxRestarts = 1000;
+
 template <typename R>
 struct BicgArgs {
   const int64_t* rowptr;
@@ -730,9 +733,11 @@ __global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const Bi
   if (!allreduce(rr, 0.0, rr, dummy)) return;
   const double rr0 = rr, target = a.rtol2 * rr0;
   double rho = rr, rho_old = 1.0, alpha = 1.0, omega = 1.0, rv_ = 0.0;
+  double rhh = rr;   // |rh|^2
   int breakdown = (isfinite(rr)) ? 0 : 1;
   int done = (!breakdown && rr <= target) ? 1 : 0;
   int64_t it = 0;
+  int restarts = 0;
   while (!done && !breakdown && it < a.maxit) {
     const double beta = (rho / rho_old) * (alpha / omega);
     // p = r + beta (p - omega v), y = M^-1 p on the own nodes
@@ -751,7 +756,7 @@ __global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const Bi
     if (!allreduce(0.0, 0.0, dummy, dummy)) return;   // y complete
     double d1 = spmv_range(a.rowptr, a.cols, a.vals, a.freem, a.y, a.v, a.rh, n0, n1);
     if (!allreduce(d1, 0.0, rv_, dummy)) return;
-    if (rv_ == 0.0 || !isfinite(rv_)) { breakdown = 1; break; }
+    if (rv_ == 0.0 || !isfinite(rv_)) { breakdown = 1; break; }        // rh . v
     alpha = rho / rv_;
     // x += alpha y, s = r - alpha v, z = M^-1 s
     double ss = 0.0;
@@ -771,7 +776,7 @@ __global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const Bi
     }
     if (!allreduce(ss, 0.0, ss, dummy)) return;
     ++it;
-    if (!isfinite(ss)) { breakdown = 1; break; }
+    if (!isfinite(ss)) { breakdown = 2; break; }
     if (ss <= target) { rr = ss; done = 1; break; }
     // t = K z; omega = (t.s) / (t.t)
     double ts = 0.0, tt = 0.0;
@@ -782,7 +787,7 @@ __global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const Bi
       for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) tt += (double)a.t[d] * (double)a.t[d];
     }
     if (!allreduce(ts, tt, ts, tt)) return;
-    if (!(tt > 0.0) || !isfinite(ts)) { breakdown = 1; break; }
+    if (!(tt > 0.0) || !isfinite(ts)) { breakdown = 3; break; }
     omega = ts / tt;
     // x += omega z, r = s - omega t; rho = rh.r, rr = r.r
     double rhr = 0.0;
@@ -795,9 +800,33 @@ __global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const Bi
       rr += (double)rv * (double)rv;
     }
     if (!allreduce(rhr, rr, rhr, rr)) return;
-    if (!isfinite(rr)) { breakdown = 1; break; }
+    if (!isfinite(rr)) { breakdown = 4; break; }
     if (rr <= target) { done = 1; break; }
-    if (omega == 0.0 || rhr == 0.0) { breakdown = 1; break; }
+    // restart on (near) breakdown - rh nearly orthogonal to r, or omega = 0 - and every
+    // kBicgRestart iterations: the true residual b - K x replaces the recurred one (which
+    // drifts, above all in FP32) and becomes the new shadow residual
+    const bool near = omega == 0.0 || fabs(rhr) <= 1e-10 * sqrt(rr * rhh);
+    if (near || it % kBicgRestart == 0) {
+      if (++restarts > kBicgMaxRestarts) { breakdown = 5; break; }
+      spmv_range(a.rowptr, a.cols, a.vals, a.freem, a.x, a.v, a.x, n0, n1);   // v <- K x (scratch)
+      __syncthreads();
+      double rr2 = 0.0;
+      for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) {
+        const R rv = a.freem[d] ? (R)(a.bscale * a.b[d]) - a.v[d] : R(0);
+        a.r[d] = rv;
+        a.rh[d] = rv;
+        a.p[d] = R(0);
+        a.v[d] = R(0);
+        rr2 += (double)rv * (double)rv;
+      }
+      if (!allreduce(rr2, 0.0, rr, dummy)) return;
+      if (!isfinite(rr)) { breakdown = 4; break; }
+      if (rr <= target) { done = 1; break; }
+      rhh = rr;
+      rho = rr;
+      rho_old = alpha = omega = 1.0;
+      continue;
+    }
     rho_old = rho;
     rho = rhr;
   }

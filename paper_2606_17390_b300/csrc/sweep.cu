@@ -32,14 +32,20 @@ constexpr int kElemsPerCta = 16;
 constexpr int kThreads = 128;
 // shared words per Gauss point: A 45 (major-symmetric) + pad 3, P 9 + pad 3, g 24; every
 // section starts on a 16-byte boundary, so phase 1 stores and phase 2 loads A and P as
-// 4-vectors
-constexpr int kGpStride = 84;
+// 4-vectors.  The F-bar element adds M = A : Fbar (9 + pad 3) and the vectors v_b (24) of
+// its rank-one tangent terms.
 constexpr int kOffP = 48;
 constexpr int kOffG = 60;
-// per element 680 = 8 mod 32 words: the 4 elements of a warp read g from banks offset by 0,
-// 8, 16, 24 in phase 2 (conflict-free scalar loads); the 8 Gauss points of one element (one
-// quarter-warp phase of a 16-byte store) start at 20 g mod 32 words: distinct bank quads
-constexpr int kElStride = 8 * kGpStride + 8;
+constexpr int kOffM = 84;
+constexpr int kOffV = 96;
+// per element 8 * stride + 8 = 8 mod 32 words: the 4 elements of a warp read g from banks
+// offset by 0, 8, 16, 24 in phase 2 (conflict-free scalar loads); the 8 Gauss points of one
+// element (one quarter-warp phase of a 16-byte store) start at 20 g (84) or 28 g (124) mod 32
+// words: distinct bank quads
+template <bool FBAR> struct Lay {
+  static constexpr int kGpStride = FBAR ? 124 : 84;
+  static constexpr int kElStride = 8 * kGpStride + 8;
+};
 
 // 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); completion
 // is awaited by cp_async_wait_all in the copying thread, then made visible by a barrier
@@ -180,9 +186,11 @@ template <> struct MatOf<double> { using T = MatRec; };
 // ----------------------------------------------------------------------------------------
 // UNIF: one material for all elements, passed by value so that its entries are kernel-
 // parameter (constant-bank) operands rather than loads.
-template <typename R, bool TANGENT, bool UNIF>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
+template <typename R, bool TANGENT, bool UNIF, bool FBAR>
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     gp_sweep_kernel(SweepArgs a, const typename MatOf<R>::T mrec, int64_t cbeg, int64_t ccount) {
+  constexpr int kGpStride = Lay<FBAR>::kGpStride;
+  constexpr int kElStride = Lay<FBAR>::kElStride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sNode = reinterpret_cast<R*>(smem_raw);                     // [16][8][6]: dX(3), du(3)
   R* sGp = sNode + kElemsPerCta * 8 * 6;                           // [16][kElStride]
@@ -315,6 +323,67 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? R(1) : R(0));
+    R* gp = sGp + (size_t)le * kElStride + g * kGpStride;
+    R fb_s = R(1);      // F-bar: (Jbar / J)^(1/3)
+    R fb_jbar = R(1);   // F-bar: det Fbar = Jbar
+    if constexpr (FBAR) {
+      // J - 1 from the invariants of H (no cancellation at small strain); the element average
+      // Jbar - 1 = sum_q w det J0_q (J_q - 1) / V_e over the element's 8 threads (Eq. Fbar)
+      const R I1 = H[0][0] + H[1][1] + H[2][2];
+      const R I2 = H[0][0] * H[1][1] + H[1][1] * H[2][2] + H[0][0] * H[2][2] - H[0][1] * H[1][0] -
+                   H[1][2] * H[2][1] - H[0][2] * H[2][0];
+      const R I3 = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) - H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                   H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+      const R jm1 = I1 + I2 + I3;
+      R wj = det0 * jm1, wv = det0;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        wj += __shfl_xor_sync(gmask, wj, o);
+        wv += __shfl_xor_sync(gmask, wv, o);
+      }
+      const R jbm1 = Num<R>::div(wj, wv);
+      const R sm1 = Num<R>::expm1_((Num<R>::log1p_(jbm1) - Num<R>::log1p_(jm1)) * R(1.0 / 3.0));
+      fb_s = R(1) + sm1;
+      fb_jbar = R(1) + jbm1;
+      if constexpr (TANGENT) {
+        // v_b = dJbar/du_b / (3 Jbar) - (1/3) F^-T g_b, with dJbar/du_b = (1/V) sum_q w det J0_q
+        // J_q F_q^-T g_b,q and J F^-T = cof(F): the non-symmetric rank-one part of K^e
+        R cof[3][3];
+        cof[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+        cof[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+        cof[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+        cof[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+        cof[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+        cof[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+        cof[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+        cof[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+        cof[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+        const R iJ = Num<R>::div(R(1), R(1) + jm1);
+        const R iV = Num<R>::div(R(1), wv);
+        const R i3jb = Num<R>::div(R(1), R(3) * fb_jbar);
+        R vv[24];
+#pragma unroll
+        for (int n = 0; n < 8; ++n)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const R cg = cof[k][0] * gN[n][0] + cof[k][1] * gN[n][1] + cof[k][2] * gN[n][2];   // (J F^-T g_n)_k
+            R b = det0 * cg;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) b += __shfl_xor_sync(gmask, b, o);
+            vv[n * 3 + k] = b * iV * i3jb - R(1.0 / 3.0) * cg * iJ;
+          }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) V4<R>::st(gp + kOffV + 4 * k, vv[4 * k], vv[4 * k + 1], vv[4 * k + 2], vv[4 * k + 3]);
+      }
+      // Fbar = s F enters the constitutive model: H <- Fbar - I = H + (s - 1) F
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          H[i][j] += sm1 * F[i][j];
+          F[i][j] *= fb_s;
+        }
+    }
     R Em[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -328,6 +397,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     R detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
              F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
     if (!(detF > R(0))) flag_detj = 1;
+    if constexpr (FBAR) {
+      if (!(fb_jbar > R(0))) flag_detj = 1;
+    }
 
     // ---- S3 log strain: E = Q diag(e) Q^T, C = I + 2E, eps = sum_a 1/2 log1p(2 e_a) n_a (x) n_a
     R ev[3], Q[3][3];
@@ -522,7 +594,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) Ft[i][j] = F[i][0] * Q[0][j] + F[i][1] * Q[1][j] + F[i][2] * Q[2][j];
-    R* gp = sGp + (size_t)le * kElStride + g * kGpStride;
     const R wd = det0;
     {
       R gq[24];
@@ -556,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
       for (int p = 0; p < 6; ++p) {
         const int i = pI(p), j = pJ(p);
         R s = P[i][0] * F[j][0] + P[i][1] * F[j][1] + P[i][2] * F[j][2];
-        a.sigma[gpi * 6 + p] = (double)Num<R>::div(s, detF);
+        a.sigma[gpi * 6 + p] = (double)Num<R>::div(s, FBAR ? fb_jbar : detF);
       }
     }
 
@@ -681,6 +752,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
           av[asym(P, Qi)] = wd * s;
         }
       av[45] = av[46] = av[47] = R(0);
+      if constexpr (FBAR) {
+        // K^e = sum_q [ g_a . (s A) . g_b + (M g_a) (x) v_b ] with M = w det J0 A : Fbar (the
+        // stored gradients are rotated, so Fbar enters as Fbar Q = Ft)
+        R mv[12];
+#pragma unroll
+        for (int P = 0; P < 9; ++P) {
+          R m = R(0);
+#pragma unroll
+          for (int Qi = 0; Qi < 9; ++Qi) m += av[asym(P, Qi)] * Ft[Qi / 3][Qi % 3];
+          mv[P] = m;
+        }
+        mv[9] = mv[10] = mv[11] = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) V4<R>::st(gp + kOffM + 4 * k, mv[4 * k], mv[4 * k + 1], mv[4 * k + 2], mv[4 * k + 3]);
+#pragma unroll
+        for (int k = 0; k < 45; ++k) av[k] *= fb_s;
+      }
 #pragma unroll
       for (int k = 0; k < 12; ++k) V4<R>::st(gp + 4 * k, av[4 * k], av[4 * k + 1], av[4 * k + 2], av[4 * k + 3]);
     }
@@ -779,6 +867,43 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
               for (int k = 0; k < 3; ++k) atomicAdd(dst + i * 3 + k, tr == 0 ? Kr[d][i * 3 + k] : Kr[d][k * 3 + i]);
           }
         }
+      }
+    }
+    if constexpr (FBAR) {
+      // the non-symmetric part: K_ab += sum_q (M_q g_a,q) (x) v_b,q for all 8 b, added after the
+      // symmetric writes of every block of this element (its 8 threads share the warp)
+      __syncwarp(gmask);
+      R ua[8][3];   // M_q g_a,q for the 8 points
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const R* Aq = G + q * kGpStride;
+        const R ga0 = Aq[kOffG + arow * 3], ga1 = Aq[kOffG + arow * 3 + 1], ga2 = Aq[kOffG + arow * 3 + 2];
+        R mv[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffM + 4 * k, mv + 4 * k);
+        ua[q][0] = mv[0] * ga0 + mv[1] * ga1 + mv[2] * ga2;
+        ua[q][1] = mv[3] * ga0 + mv[4] * ga1 + mv[5] * ga2;
+        ua[q][2] = mv[6] * ga0 + mv[7] * ga1 + mv[8] * ga2;
+      }
+#pragma unroll 1
+      for (int b = 0; b < 8; ++b) {
+        R C[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) C[c] = R(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const R* vb = G + q * kGpStride + kOffV + b * 3;
+          const R v0 = vb[0], v1 = vb[1], v2 = vb[2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            C[i * 3] += ua[q][i] * v0;
+            C[i * 3 + 1] += ua[q][i] * v1;
+            C[i * 3 + 2] += ua[q][i] * v2;
+          }
+        }
+        R* dst = Kv + (int64_t)(sl[arow * 8 + b] & 0x7fffffff) * 9;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) atomicAdd(dst + c, C[c]);
       }
     }
   } else {
@@ -1001,14 +1126,15 @@ void launch_hist_export(const void* hist, double* user, bool fp64, int64_t n_gp,
   else hist_export_kernel<float><<<blocks, threads, 0, s>>>(hist, user, n_gp);
 }
 
-template <typename R, bool TANGENT, bool UNIF>
+template <typename R, bool TANGENT, bool UNIF, bool FBAR>
 static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cudaStream_t s) {
   using MR = typename MatOf<R>::T;
-  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * kElStride) +
+  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * Lay<FBAR>::kElStride) +
                      sizeof(int32_t) * kElemsPerCta * 64;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF, FBAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr_done = true;
   }
   MR rec;
@@ -1018,20 +1144,21 @@ static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cu
     int64_t cnt = off[c + 1] - off[c];
     if (cnt <= 0) continue;
     unsigned blocks = (unsigned)((cnt + kElemsPerCta - 1) / kElemsPerCta);
-    gp_sweep_kernel<R, TANGENT, UNIF><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
+    gp_sweep_kernel<R, TANGENT, UNIF, FBAR><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
   }
+}
+
+template <typename R, bool FBAR>
+static void launch_mode(const SweepArgs& a, int mode, const std::vector<int64_t>& off, cudaStream_t s) {
+  const bool u = a.mat_host != nullptr;
+  if (mode == HFE_SWEEP_TANGENT) u ? launch_typed<R, true, true, FBAR>(a, off, s) : launch_typed<R, true, false, FBAR>(a, off, s);
+  else u ? launch_typed<R, false, true, FBAR>(a, off, s) : launch_typed<R, false, false, FBAR>(a, off, s);
 }
 
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
                      cudaStream_t s) {
-  const bool u = a.mat_host != nullptr;
-  if (fp64) {
-    if (mode == HFE_SWEEP_TANGENT) u ? launch_typed<double, true, true>(a, color_off, s) : launch_typed<double, true, false>(a, color_off, s);
-    else u ? launch_typed<double, false, true>(a, color_off, s) : launch_typed<double, false, false>(a, color_off, s);
-  } else {
-    if (mode == HFE_SWEEP_TANGENT) u ? launch_typed<float, true, true>(a, color_off, s) : launch_typed<float, true, false>(a, color_off, s);
-    else u ? launch_typed<float, false, true>(a, color_off, s) : launch_typed<float, false, false>(a, color_off, s);
-  }
+  if (fp64) a.fbar ? launch_mode<double, true>(a, mode, color_off, s) : launch_mode<double, false>(a, mode, color_off, s);
+  else a.fbar ? launch_mode<float, true>(a, mode, color_off, s) : launch_mode<float, false>(a, mode, color_off, s);
 }
 
 }  // namespace hfe

@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("pcg_maxit", C.c_int), ("pcg_check_every", C.c_int), ("precond", C.c_int),
                 ("local_maxit", C.c_int), ("local_tol", C.c_double), ("ckpt_every", C.c_int),
                 ("predictor", C.c_int), ("ew_forcing", C.c_int), ("pcg_persistent", C.c_int),
-                ("adaptive", C.c_int), ("cutback", C.c_double), ("max_cutbacks", C.c_int)]
+                ("adaptive", C.c_int), ("cutback", C.c_double), ("max_cutbacks", C.c_int), ("fbar", C.c_int)]
 
 
 class Stats(C.Structure):
