@@ -169,6 +169,7 @@ def main():
     ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
     ap.add_argument("--adjoint-nx", type=int, default=200, help="plate resolution of the adjoint ratio run (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--fbar-steps", type=int, default=20, help="timed F-bar tangent sweeps (0 = skip)")
     ap.add_argument("--adjoint-config", type=int, default=3, choices=(3, 4),
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
@@ -195,8 +196,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    def make(precision):
-        s = hfe.from_inputs(mesh, bc, mat, precision=precision, stream=stream.cuda_stream)
+    def make(precision, **opts):
+        s = hfe.from_inputs(mesh, bc, mat, precision=precision, stream=stream.cuda_stream, **opts)
         s.set_state(u, hist)
         return s
 
@@ -339,6 +340,16 @@ def main():
     else:
         solver.close()
 
+    # the F-bar element's tangent sweep on the same state (option fbar, non-symmetric K), for context
+    fbar = None
+    if args.fbar_steps > 0:
+        sfb = make(args.precision, fbar=1)
+        step(sfb)
+        msfb = timed(sfb, args.fbar_steps) / args.fbar_steps
+        fbar = {"value": world * 8 * mesh.n_el / (msfb * 1e-3), "ms_per_step": msfb, "steps": args.fbar_steps,
+                "over_standard": msfb / ms_step}
+        sfb.close()
+
     # adjoint/forward time ratio (second part of the metric) on the config-3 problem: perforated
     # plate, Swift parameters perturbed by +-20 %, noisy synthetic target; the gradient call runs
     # its own forward pass (mixed, each step ending with an FP64 Newton iteration) and the FP64
@@ -409,7 +420,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
-                "pcg": pcg, "adjoint": adjoint, "forward": forward,
+                "pcg": pcg, "adjoint": adjoint, "forward": forward, "fbar_sweep": fbar,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

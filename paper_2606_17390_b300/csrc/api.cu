@@ -953,32 +953,36 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   // cutback^max_cutbacks; after two accepted substeps in a row the increment grows back by
   // 1/cutback, clipped so that the requested load factors are hit exactly.  A reduced
   // increment carries over to the next interval.
-  double dt_carry = 0.0;
+  // Increments are handled as magnitudes along the direction of each interval, so loading
+  // and unloading intervals are stepped alike.
+  double inc_carry = 0.0;
   for (int n = 0; n < n_steps; ++n) {
     int cuts = 0, ok_run = 0;
-    double dt_try = t[n] - h->t_state;
-    const double dt_min = dt_try * std::pow(h->opt.cutback, (double)h->opt.max_cutbacks);
-    if (dt_carry > 0.0 && dt_carry < dt_try) dt_try = dt_carry;
+    const double span = t[n] - h->t_state;
+    const double dirn = span < 0.0 ? -1.0 : 1.0;
+    double inc_try = std::fabs(span);
+    const double inc_min = inc_try * std::pow(h->opt.cutback, (double)h->opt.max_cutbacks);
+    if (inc_carry > 0.0 && inc_carry < inc_try) inc_try = inc_carry;
     for (;;) {
-      const double remaining = t[n] - h->t_state;
-      const double dt = std::min(dt_try, remaining);
-      const bool hits = dt >= remaining * (1.0 - 1e-12);
-      const double t_new = hits ? t[n] : h->t_state + dt;
+      const double remaining = std::fabs(t[n] - h->t_state);
+      const double inc = std::min(inc_try, remaining);
+      const bool hits = inc >= remaining * (1.0 - 1e-12);
+      const double t_new = hits ? t[n] : h->t_state + dirn * inc;
       const hfe_status s = attempt(t_new, hits ? n : -1);
       if (s == HFE_OK) {
         loc.substeps++;
         if (hits) break;
         if (++ok_run >= 2) {
-          dt_try = dt / h->opt.cutback;
+          inc_try = inc / h->opt.cutback;
           ok_run = 0;
         } else {
-          dt_try = dt;
+          inc_try = inc;
         }
         continue;
       }
       const bool recoverable = s == HFE_ENEWTON || s == HFE_EDETJ || s == HFE_ENONFINITE || s == HFE_EPCG ||
                                s == HFE_ELOCAL;
-      if (!h->opt.adaptive || !recoverable || dt * h->opt.cutback < dt_min * (1.0 - 1e-9)) {
+      if (!h->opt.adaptive || !recoverable || inc * h->opt.cutback < inc_min * (1.0 - 1e-9)) {
         loc.bicgstab_solves = h->n_bicgstab - bicg0;
         if (st) *st = loc;
         return s;
@@ -986,9 +990,9 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       ++cuts;
       loc.cutbacks++;
       ok_run = 0;
-      dt_try = dt * h->opt.cutback;
+      inc_try = inc * h->opt.cutback;
     }
-    dt_carry = cuts > 0 ? dt_try : 0.0;
+    inc_carry = cuts > 0 ? inc_try : 0.0;
     loc.steps_done = n + 1;
   }
   if (hist_out) HFE_TRY(export_history(h, h->hist, hist_out));

@@ -1131,12 +1131,10 @@ static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cu
   using MR = typename MatOf<R>::T;
   const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * Lay<FBAR>::kElStride) +
                      sizeof(int32_t) * kElemsPerCta * 64;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF, FBAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr_done = true;
-  }
+  // the dynamic shared-memory limit is a per-device function attribute: set it on every call
+  // (a host-side call, no synchronisation) so that each device the handle runs on has it
+  cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF, FBAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
   MR rec;
   if (UNIF) memcpy(&rec, a.mat_host, sizeof(MR));   // host copy of the single record
   else memset(&rec, 0, sizeof(MR));

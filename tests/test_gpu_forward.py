@@ -169,3 +169,16 @@ def test_adaptive_stepping_plate_in_few_steps():
     # out-of-balance force of the committed state: Newton-tolerance level, against
     # reaction forces of order E * 2 % * 100 mm^2 = 1.4e5 N
     assert rn[0] < 1.0, rn
+
+
+def test_unloading_step_matches_oracle():
+    """Load factors need not increase: tension to 5 %, then back to 3 % (beyond the elastic
+    range 2 sigma_y / E, so the unloading yields in reverse), against the oracle's forward on
+    the same factors (FP64 1e-10)."""
+    mesh, bc, mat, _ = inputs.config0_problem(n=2)
+    ts = np.array([0.5, 1.0, 0.6])
+    us, hs, _ = solver.forward(solver.from_inputs(mesh, bc, mat), ts, rtol=1e-13)
+    assert np.abs(hs[3][..., 6] - hs[2][..., 6]).max() > 0.0           # reverse plastic flow
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", newton_rtol=1e-12, pcg_rtol=1e-13) as s:
+        u, st = s.forward(ts)
+    assert _per_step_rel(u, us) < 1e-10
