@@ -1,0 +1,249 @@
+"""Oracle, Barlat Yld2004-18p yield function and the closest-point projection driven by a
+trial stress (Eq. Phi_barlat, App. A.2, Eq. local_cpp, App. B, App. C).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): plain FP64 numpy, vectorised over a
+leading batch of independent material points and nothing else.
+
+* phi(T) = [1/4 sum_ij |s'_i - s''_j|^m]^(1/m), s'_i and s''_j the eigenvalues of
+  s' = C' : P : T_l and s'' = C'' : P : T_l (Eq. Phi_barlat), with P the deviatoric projector
+  and C', C'' the 6x6 matrices of App. A.2 acting on tensor components in the order
+  (11, 22, 33, 12, 23, 13): c44, c55, c66 scale the 12, 23, 13 shear components (reading R17).
+  T_l = Theta^T T Theta is the stress in the material frame (the columns of Theta are the
+  material axes); eigenvalues do not depend on the frame, so this is the paper's rotation of
+  C', C'' into the global frame.  `phi_eig` evaluates this definition with eigenvalues.
+* For an even integer m the double sum is a polynomial in power traces,
+  sum_ij (a_i - b_j)^m = sum_k binom(m, k) (-1)^(m-k) tr(A^k) tr(B^(m-k)),
+  evaluated after shifting A and B by the same multiple of I (the sum only sees
+  differences a_i - b_j), which keeps the alternating sum well conditioned.  `phi_poly` and
+  its gradient `flow` (N = dphi/dT, Eq. ep_evol) need no eigenvalues and take complex
+  arguments, so the Jacobian of G follows by complex step.
+* `cpp` solves G(y) = 0 for y = [T (6), alpha, dgamma] (Eq. local_cpp) with
+  G_T = T - T_tr + dgamma E : N(T), G_alpha = alpha - alpha_n - W dgamma with W = 1 for this
+  model (Eq. alpha_update), G_f = phi(T) - sigma_y(alpha) (Eq. yield_final), isotropic E.
+  Newton (Eq. local_solver) from y0 = [T_tr, alpha_n, 0] (reading R7), optionally with the
+  line search of App. B (Goldstein test Eq. goldstein_full, quadratic model Eq. alpha_init and
+  Eq. alpha_update_ls, safeguard Eq. alpha_safeguard; reading R9 on the order), converged
+  when the scaled residual norm of reading R8 is <= tol.
+* `cpp_tangent` gives dT/dT_tr at the converged point by implicit differentiation (App. D):
+  J_G dy = [dT_tr; 0; 0].
+
+Parity pins (tests/test_oracle_barlat.py): phi_poly against phi_eig; flow against central
+differences of phi_eig; the isotropic reductions (all 18 coefficients 1: von Mises for
+m = 2 and m = 4, uniaxial and pure-shear closed forms for any even m); homogeneity and
+pressure insensitivity; the von Mises radial return in closed form; the projection against
+a direct minimisation of the complementary energy over the yield set; the paper's printed
+step length of the third line-search iteration (App. B).
+"""
+from __future__ import annotations
+
+from math import comb
+
+import numpy as np
+
+from .material import LS_BETA, LS_ETA, LS_JMAX, LOCAL_TOL, _scaled_norm, complex_step_jacobian
+
+VOIGT = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2))
+W_SHEAR = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])    # X : Y = sum_a w_a X_a Y_a
+
+# deviatoric projector on tensor components (App. A.2)
+P_DEV = np.array([[2, -1, -1, 0, 0, 0], [-1, 2, -1, 0, 0, 0], [-1, -1, 2, 0, 0, 0],
+                  [0, 0, 0, 3, 0, 0], [0, 0, 0, 0, 3, 0], [0, 0, 0, 0, 0, 3]], dtype=np.float64) / 3.0
+
+
+def transform_matrix(c):
+    """The 6x6 matrix of App. A.2 from (c12, c13, c21, c23, c31, c32, c44, c55, c66)."""
+    c12, c13, c21, c23, c31, c32, c44, c55, c66 = c
+    C = np.zeros((6, 6))
+    C[0, 1], C[0, 2] = -c12, -c13
+    C[1, 0], C[1, 2] = -c21, -c23
+    C[2, 0], C[2, 1] = -c31, -c32
+    C[3, 3], C[4, 4], C[5, 5] = c44, c55, c66
+    return C
+
+
+def voigt(T):
+    """(..., 3, 3) -> (..., 6) components in the order (11, 22, 33, 12, 23, 13)."""
+    return np.stack([T[..., i, j] for i, j in VOIGT], axis=-1)
+
+
+def tensor(v):
+    """(..., 6) components -> symmetric (..., 3, 3)."""
+    T = np.zeros(v.shape[:-1] + (3, 3), dtype=v.dtype)
+    for a, (i, j) in enumerate(VOIGT):
+        T[..., i, j] = v[..., a]
+        T[..., j, i] = v[..., a]
+    return T
+
+
+class Barlat:
+    """Yld2004-18p with coefficients c1 = C' and c2 = C'' (9 each), even integer m, optional
+    material frame Theta (3x3, columns = material axes)."""
+
+    def __init__(self, c1, c2, m, Theta=None):
+        self.C1 = transform_matrix(c1)
+        self.C2 = transform_matrix(c2)
+        self.m = int(m)
+        if self.m != m or self.m < 2 or self.m % 2:
+            raise ValueError("the power-trace form needs an even integer exponent m >= 2")
+        self.Theta = np.eye(3) if Theta is None else np.asarray(Theta, dtype=np.float64)
+
+    def transformed(self, T):
+        """s' and s'' (..., 3, 3) for stress components T (..., 6) in the global frame."""
+        Tg = tensor(T)
+        Tl = np.swapaxes(self.Theta, -1, -2) @ Tg @ self.Theta
+        s = voigt(Tl) @ P_DEV.T
+        return tensor(s @ self.C1.T), tensor(s @ self.C2.T)
+
+    # -- the definition -------------------------------------------------------------------
+    def phi_eig(self, T):
+        A, B = self.transformed(np.asarray(T, dtype=np.float64))
+        a = np.linalg.eigvalsh(A)
+        b = np.linalg.eigvalsh(B)
+        S = np.sum(np.abs(a[..., :, None] - b[..., None, :]) ** self.m, axis=(-2, -1))
+        return (0.25 * S) ** (1.0 / self.m)
+
+    # -- the polynomial form (complex arguments allowed) --------------------------------
+    def _shifted_powers(self, T):
+        A, B = self.transformed(T)
+        c = (np.trace(A, axis1=-2, axis2=-1) + np.trace(B, axis1=-2, axis2=-1)) / 6.0
+        I = np.eye(3)
+        A = A - c[..., None, None] * I
+        B = B - c[..., None, None] * I
+        PA = [np.broadcast_to(I, A.shape).astype(A.dtype)]
+        PB = [np.broadcast_to(I, B.shape).astype(B.dtype)]
+        for _ in range(self.m):
+            PA.append(PA[-1] @ A)
+            PB.append(PB[-1] @ B)
+        tA = [np.trace(X, axis1=-2, axis2=-1) for X in PA]
+        tB = [np.trace(X, axis1=-2, axis2=-1) for X in PB]
+        return PA, PB, tA, tB
+
+    def _S(self, tA, tB):
+        m = self.m
+        return sum(comb(m, k) * (-1) ** (m - k) * tA[k] * tB[m - k] for k in range(m + 1))
+
+    def phi_poly(self, T):
+        _, _, tA, tB = self._shifted_powers(T)
+        return (0.25 * self._S(tA, tB)) ** (1.0 / self.m)
+
+    def flow(self, T):
+        """(N, phi): N = dphi/dT as tensor components (..., 6), dphi = N : dT.
+
+        dS = sum_k binom(m,k)(-1)^(m-k) [k tr(B^(m-k)) A^(k-1) : dA + (m-k) tr(A^k) B^(m-k-1) : dB]
+        with dA = C' P dT_l and dB = C'' P dT_l (the shift is a fixed multiple of I here: S does
+        not change with it), dT_l = Theta^T dT Theta; phi = (S/4)^(1/m)."""
+        m = self.m
+        PA, PB, tA, tB = self._shifted_powers(T)
+        S = self._S(tA, tB)
+        GA = sum(comb(m, k) * (-1) ** (m - k) * k * tB[m - k][..., None, None] * PA[k - 1]
+                 for k in range(1, m + 1))
+        GB = sum(comb(m, k) * (-1) ** (m - k) * (m - k) * tA[k][..., None, None] * PB[m - k - 1]
+                 for k in range(0, m))
+        # X : tensor(C v) = (w X_voigt) . (C v) with v = P voigt(dT_l)
+        gl = (voigt(GA) * W_SHEAR) @ self.C1 @ P_DEV + (voigt(GB) * W_SHEAR) @ self.C2 @ P_DEV
+        Nl = tensor(gl / W_SHEAR)                                   # dS/dT_l as a tensor
+        Ng = self.Theta @ Nl @ np.swapaxes(self.Theta, -1, -2)       # back to the global frame
+        phi = (0.25 * S) ** (1.0 / m)
+        return voigt(Ng) * (0.25 / m) * phi[..., None] ** (1 - m), phi
+
+
+def lame(E, nu):
+    return E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+
+
+def elastic(E, nu, e):
+    """E : e on tensor components (isotropic: lambda tr(e) I + 2 mu e)."""
+    lam, mu = lame(E, nu)
+    out = 2 * mu * e
+    out[..., :3] += lam * np.sum(e[..., :3], axis=-1, keepdims=True)
+    return out
+
+
+def sigma_y(hardening, h, alpha):
+    """Swift K (eps0 + alpha)^n or Voce sigma0 + Q (1 - exp(-b alpha)) (Eq. Hard, W = 1);
+    perfect plasticity is Voce with Q = 0."""
+    if hardening == "swift":
+        K, e0, n = h
+        return K * (e0 + alpha) ** n
+    s0, Q, b = h
+    return s0 + Q * (1.0 - np.exp(-b * alpha))
+
+
+def residual(model, E, nu, hardening, h, y, Ttr, alpn):
+    """G(y) of Eq. local_cpp for y = [T (6), alpha, dgamma] (..., 8)."""
+    N, phi = model.flow(y[..., :6])
+    GT = y[..., :6] - Ttr + y[..., 7:8] * elastic(E, nu, N)
+    Ga = y[..., 6] - alpn - y[..., 7]
+    Gf = phi - sigma_y(hardening, h, y[..., 6])
+    return np.concatenate([GT, Ga[..., None], Gf[..., None]], axis=-1)
+
+
+def cpp(model, E, nu, hardening, h, Ttr, alpn, line_search=True, kmax=40, tol=LOCAL_TOL,
+        beta=LS_BETA, eta=LS_ETA, jmax=LS_JMAX, trace=None):
+    """Plastic corrector for a batch of trial stresses Ttr (B, 6) with alpha_n (B,).
+
+    Returns (y (B, 8), iterations (B,), converged (B,)).  Every point is treated as plastic
+    (the caller tests f_tr).  `trace`, a list, receives per Newton iteration a dict with the
+    active indices, psi(0), psi(1) and the step length taken."""
+    Ttr = np.asarray(Ttr, dtype=np.float64)
+    alpn = np.asarray(alpn, dtype=np.float64)
+    Bn = Ttr.shape[0]
+
+    def G_of(yy, idx):
+        return residual(model, E, nu, hardening, h, yy, Ttr[idx], alpn[idx])
+
+    y = np.concatenate([Ttr, alpn[:, None], np.zeros((Bn, 1))], axis=1)
+    sref = np.maximum(sigma_y(hardening, h, alpn), np.sqrt(np.sum(Ttr * Ttr, axis=-1)))
+    iters = np.zeros(Bn, dtype=np.int64)
+    conv = np.zeros(Bn, dtype=bool)
+    active = np.arange(Bn)
+    for k in range(kmax + 1):
+        G = G_of(y[active], active)
+        bad = ~np.all(np.isfinite(G), axis=1)
+        done = (_scaled_norm(G, sref[active]) <= tol) & ~bad
+        conv[active[done]] = True
+        keep = ~(done | bad)
+        active, G = active[keep], G[keep]
+        if active.size == 0 or k == kmax:
+            break
+        iters[active] += 1
+        idx = active
+        J = complex_step_jacobian(lambda yy: G_of(yy, idx), y[active], 8)
+        dy = np.linalg.solve(J, -G[..., None])[..., 0]
+        zeta = np.ones(active.size)
+        psi0 = 0.5 * np.sum(G * G, axis=1)
+        psi1 = np.full(active.size, np.nan)
+        if line_search:
+            G1 = G_of(y[active] + dy, active)
+            psi1 = 0.5 * np.sum(G1 * G1, axis=1)
+            need = np.nonzero(~(psi1 < (1.0 - 2.0 * beta) * psi0))[0]        # Eq. goldstein_full
+            if need.size:
+                z = psi0[need] / (psi0[need] + psi1[need])                     # Eq. alpha_init
+                open_ = np.ones(need.size, dtype=bool)
+                for _ in range(jmax + 1):
+                    sel = need[open_]
+                    Gz = G_of(y[active[sel]] + z[open_, None] * dy[sel], active[sel])
+                    psiz = 0.5 * np.sum(Gz * Gz, axis=1)
+                    ok = psiz < (1.0 - 2.0 * beta * z[open_]) * psi0[sel]      # Eq. goldstein_full
+                    znew = psi0[sel] / (psi0[sel] + psiz)                        # Eq. alpha_update_ls
+                    zo = z[open_]
+                    z[open_] = np.where(ok, zo, np.maximum(eta * zo, znew))      # Eq. alpha_safeguard
+                    open_[np.nonzero(open_)[0][ok]] = False
+                    if not open_.any():
+                        break
+                zeta[need] = z
+        if trace is not None:
+            trace.append(dict(active=active.copy(), psi0=psi0, psi1=psi1, zeta=zeta.copy()))
+        y[active] = y[active] + zeta[:, None] * dy
+    return y, iters, conv
+
+
+def cpp_tangent(model, E, nu, hardening, h, y, Ttr, alpn):
+    """dT/dT_tr (B, 6, 6) at converged points by implicit differentiation (App. D): with
+    dG/dT_tr = [-I; 0; 0], J_G dy/dT_tr = [I; 0; 0].  Column b is the response to a change of
+    component b of T_tr (for a shear component both symmetric entries move)."""
+    Ttr = np.asarray(Ttr, dtype=np.float64)
+    J = complex_step_jacobian(lambda yy: residual(model, E, nu, hardening, h, yy, Ttr, alpn), y, 8)
+    rhs = np.zeros((y.shape[0], 8, 6))
+    rhs[:, :6, :] = np.eye(6)
+    return np.linalg.solve(J, rhs)[:, :6, :]

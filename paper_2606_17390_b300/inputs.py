@@ -359,3 +359,68 @@ def random_history(n: int, seed: int, eps_scale: float = 0.02, alpha_max: float 
     ep[:, :3] -= ep[:, :3].mean(axis=1, keepdims=True)
     alpha = alpha_max * rng.uniform(0.0, 1.0, size=n)
     return ep, alpha
+
+
+# ------------------------------------------------------------------ Barlat material points
+@dataclasses.dataclass
+class BarlatMaterial:
+    """Yld2004-18p parameters: c1 = (c'12, c'13, c'21, c'23, c'31, c'32, c'44, c'55, c'66),
+    c2 the same for c'', even exponent m, isotropic E and nu, hardening law and parameters
+    ((sigma0, Q, b) for Voce, (K, eps0, n) for Swift), material frame Theta (columns = axes)."""
+    c1: tuple
+    c2: tuple
+    m: int
+    E: float
+    nu: float
+    hardening: str = "voce"
+    h: tuple = (1.0, 0.0, 0.0)
+    Theta: np.ndarray = None
+
+
+def barlat_verification_material() -> BarlatMaterial:
+    """The Yld2004-18p verification parameters of the paper's table (m = 8, E = 1000,
+    nu = 0.3, sigma0 = 1, perfect plasticity = Voce with Q = 0)."""
+    return BarlatMaterial(
+        c1=(-0.069888, 0.936408, 0.079143, 1.003060, 0.524741, 1.363180, 1.023770, 1.069060, 0.954322),
+        c2=(0.981171, 0.476741, 0.575316, 0.866827, 1.145010, -0.079294, 1.051660, 1.147100, 1.404620),
+        m=8, E=1000.0, nu=0.3, hardening="voce", h=(1.0, 0.0, 0.0))
+
+
+def principal_plane_directions(angle) -> np.ndarray:
+    """Unit deviatoric directions of the principal-stress (pi) plane as stress components
+    (..., 6) of a diagonal stress: sqrt(2/3) (cos a, cos(a - 2 pi/3), cos(a + 2 pi/3))."""
+    a = np.asarray(angle, dtype=np.float64)
+    d = np.zeros(a.shape + (6,))
+    s = math.sqrt(2.0 / 3.0)
+    d[..., 0] = s * np.cos(a)
+    d[..., 1] = s * np.cos(a - 2.0 * math.pi / 3.0)
+    d[..., 2] = s * np.cos(a + 2.0 * math.pi / 3.0)
+    return d
+
+
+def pi_plane_sample(n: int = 16000, seed: int = 17390, scale_max: float = 30.0):
+    """The line-search robustness map's trial states: n points of the pi plane between the
+    yield surface and the same surface scaled by scale_max, as (angle (n,), scale (n,)) drawn
+    uniformly from [0, 2 pi) x (1, scale_max].  The trial stress of a point is
+    scale * sigma_y(alpha_n) * d(angle) / phi(d(angle)), d = principal_plane_directions: the
+    scaling to the yield surface is the method's arithmetic and is done by each side."""
+    rng = np.random.default_rng(seed)
+    angle = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    scale = scale_max - (scale_max - 1.0) * rng.uniform(0.0, 1.0, size=n)   # (1, scale_max]
+    return angle, scale
+
+
+def random_stresses(n: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Random stress components (n, 6), uniform in [-scale, scale]."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.uniform(-1.0, 1.0, size=(n, 6))
+
+
+def random_rotation(seed: int) -> np.ndarray:
+    """A random proper rotation (3, 3) (QR of a Gaussian matrix, signs fixed)."""
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((3, 3)))
+    Q = Q * np.sign(np.diag(R))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    return Q
