@@ -262,6 +262,92 @@ hfe_status hfe_adjoint(hfe_handle* h, int n_steps, const double* t, const double
 hfe_status hfe_free_norm_static(const double* r, const uint8_t* free_mask, int64_t n_dof, double* norm_out,
                                 void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Barlat Yld2004-18p material points (no handle, no mesh)
+ *
+ * phi(T) = [1/4 sum_ij |s'_i - s''_j|^m]^(1/m) with s'_i, s''_j the eigenvalues of
+ * s' = C' : P : T_l and s'' = C'' : P : T_l, P the deviatoric projector, T_l = Theta^T T Theta
+ * the stress in the material frame (Eq. Phi_barlat, App. A.2).  C' and C'' are the 6x6
+ * matrices of App. A.2 on the components (11, 22, 33, 12, 23, 13): off-diagonal normal
+ * entries -c12, -c13, -c21, -c23, -c31, -c32 and the shear diagonal c44, c55, c66 acting on
+ * the 12, 23, 13 components.  Associative flow N = dphi/dT with W = 1 (alpha-rate =
+ * gamma-rate), yield function f = phi(T) - sigma_y(alpha) (Eq. ep_evol, Eq. alpha_update,
+ * Eq. yield_final), isotropic log-space elasticity E, nu (Eq. T).
+ *
+ *   c1[9], c2[9]: (c12, c13, c21, c23, c31, c32, c44, c55, c66) of C' and C'';
+ *   m: the exponent, an even integer 2 <= m <= HFE_BARLAT_MAX_M;
+ *   hardening, h[3]: HFE_HARDENING_SWIFT (K, eps0, n) or HFE_HARDENING_VOCE (sigma0, Q, b);
+ *     perfect plasticity is Voce with Q = 0;
+ *   Theta[9]: row-major 3x3 whose columns are the material axes (orthonormal to 1e-10;
+ *     the identity for material axes = global axes). */
+#define HFE_BARLAT_MAX_M 32
+typedef struct {
+  double c1[9];
+  double c2[9];
+  int m;
+  double E, nu;
+  int hardening;
+  double h[3];
+  double Theta[9];
+} hfe_barlat_material;
+
+/* Local closest-point projection controls (App. B, App. C): at most kmax Newton iterations,
+ * line_search = 1 for App. B's line search (0 = standard Newton), at most jmax + 1 merit
+ * evaluations after the full step, Goldstein constant beta, safeguard eta, and convergence
+ * when sqrt(|G_T / s|^2 + G_alpha^2 + (G_f / s)^2) <= tol with s = max(sigma_y(alpha_n),
+ * |T_tr|).  precision HFE_PRECISION_FP64: every iteration in double;
+ * HFE_PRECISION_MIXED: the same iteration in float down to a scaled residual of 1e-5 (at
+ * most kmax iterations), then at most 6 double Newton iterations to tol (the FP32 phase
+ * hitting kmax reports HFE_CPP_MAXIT), the elastic test in float outside |f_tr| <= 1e-5 s and
+ * in double inside.  Defaults (hfe_default_cpp_options): kmax 40, line_search 1, jmax 10,
+ * beta 1e-4, eta 0.1, tol 1e-13, precision HFE_PRECISION_FP64. */
+typedef struct {
+  int kmax;
+  int line_search;
+  int jmax;
+  double beta, eta, tol;
+  int precision;
+} hfe_cpp_options;
+void hfe_default_cpp_options(hfe_cpp_options* opt);
+
+/* phi_out[i] = phi(T[i]) and, if N_out is not NULL, N_out[i*6 .. i*6+5] = dphi/dT as tensor
+ * components (dphi = N : dT), for n stresses T[n*6] (components as above).  All arrays are
+ * device memory of the current device owned by the caller; queued on cuda_stream (NULL =
+ * legacy default stream), no synchronisation.  A pure pressure gives phi = 0 up to the
+ * rounding of the deviatoric projection; T = 0 gives phi = 0 and N = 0; a non-finite stress
+ * gives NaN.  Errors: HFE_EINVAL for an invalid material (odd or out-of-range m,
+ * E <= 0, nu outside (-1, 0.5), unknown hardening, non-finite values, Theta not orthonormal),
+ * n < 0, NULL or non-device pointers (nothing is launched); HFE_ECUDA if the launch fails. */
+hfe_status hfe_barlat_phi(const hfe_barlat_material* mat, const double* T, int64_t n, double* phi_out,
+                          double* N_out, void* cuda_stream);
+
+/* Per-point outcome of hfe_barlat_return_map. */
+#define HFE_CPP_CONVERGED 0   /* plastic, the residual test passed */
+#define HFE_CPP_ELASTIC 1     /* f_tr = phi(T_tr) - sigma_y(alpha_n) <= 0: T = T_tr */
+#define HFE_CPP_MAXIT 2       /* kmax Newton iterations without convergence: the last iterate */
+#define HFE_CPP_SINGULAR 3    /* the Newton matrix was singular: the last iterate */
+#define HFE_CPP_NONFINITE 4   /* a non-finite input or residual (or phi = 0 inside the iteration) */
+
+/* Elastic predictor / plastic corrector for n material points driven by trial stresses
+ * (App. C): for each i, from T_trial[i*6..] and alpha_n[i], the elastic test and, if
+ * plastic, Newton on G(y) = 0, y = [T, alpha, dgamma] (Eq. local_cpp) from
+ * y0 = [T_trial, alpha_n, 0], with the App. B line search when opt->line_search.
+ * Outputs: T_out[n*6], alpha_out[n], dgamma_out[n], iters_out[n] (Newton iterations taken),
+ * status_out[n] (HFE_CPP_*), and, if tangent_out is not NULL, tangent_out[n*36] =
+ * dT/dT_trial row-major per point ([a*6 + c] = dT_a / dT_trial_c, a shear component moving
+ * both symmetric entries) by implicit differentiation of the converged local system (App. D);
+ * the identity for elastic points.  opt NULL = the defaults.  Every array is device memory of
+ * the current device, owned by the caller; queued on cuda_stream (NULL = legacy default
+ * stream), no synchronisation, no allocation.  One thread per point.
+ * Errors: as hfe_barlat_phi, plus HFE_EINVAL for options out of range (kmax outside
+ * [0, 100000], jmax outside [0, 1000], beta outside (0, 0.5), eta outside (0, 1), tol <= 0,
+ * unknown precision).
+ * Per-point failures are reported in status_out, not as an error. */
+hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, const hfe_cpp_options* opt, const double* T_trial,
+                                 const double* alpha_n, int64_t n, double* T_out, double* alpha_out,
+                                 double* dgamma_out, int32_t* iters_out, int8_t* status_out, double* tangent_out,
+                                 void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

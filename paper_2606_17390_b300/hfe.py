@@ -320,3 +320,91 @@ def free_norm_static(r, free_mask, norm_out, stream=None):
         else:
             msg = "CUDA error in set-up or launch"
         raise HfeError(st, "hfe_free_norm_static: " + msg)
+
+
+# ---------------------------------------------------------------- Barlat material points
+CPP_STATUS = {0: "converged", 1: "elastic", 2: "maxit", 3: "singular", 4: "nonfinite"}
+BARLAT_MAX_M = 32   # HFE_BARLAT_MAX_M of include/hfe.h
+
+
+class BarlatMaterialC(C.Structure):
+    _fields_ = [("c1", C.c_double * 9), ("c2", C.c_double * 9), ("m", C.c_int), ("E", C.c_double),
+                ("nu", C.c_double), ("hardening", C.c_int), ("h", C.c_double * 3), ("Theta", C.c_double * 9)]
+
+
+class CppOptions(C.Structure):
+    _fields_ = [("kmax", C.c_int), ("line_search", C.c_int), ("jmax", C.c_int), ("beta", C.c_double),
+                ("eta", C.c_double), ("tol", C.c_double), ("precision", C.c_int)]
+
+
+def barlat_material(mat) -> BarlatMaterialC:
+    """hfe_barlat_material from an object with c1, c2, m, E, nu, hardening ('swift'|'voce'),
+    h and Theta (None = identity), e.g. inputs.BarlatMaterial."""
+    s = BarlatMaterialC()
+    s.c1[:] = [float(v) for v in mat.c1]
+    s.c2[:] = [float(v) for v in mat.c2]
+    s.m = int(mat.m)
+    s.E, s.nu = float(mat.E), float(mat.nu)
+    s.hardening = HARDENING[mat.hardening]
+    s.h[:] = [float(v) for v in mat.h]
+    Th = np.eye(3) if getattr(mat, "Theta", None) is None else np.asarray(mat.Theta, dtype=np.float64)
+    s.Theta[:] = [float(v) for v in Th.reshape(9)]
+    return s
+
+
+def _check(st, name):
+    if st != 0:
+        raise HfeError(st, name + (": invalid argument (material, options, sizes, or pointers not on the "
+                                   "current device)" if st == -1 else ": CUDA error"))
+
+
+def barlat_phi(mat, T, with_N=False, stream=None):
+    """phi (and N = dphi/dT if with_N) for stresses T, a float64 CUDA tensor [n, 6], through
+    hfe_barlat_phi.  Returns phi [n] (and N [n, 6]) as CUDA tensors, queued on `stream`
+    (a cudaStream_t handle or None for the legacy default stream)."""
+    import torch
+    L = lib()
+    f = L.hfe_barlat_phi
+    f.argtypes = [C.POINTER(BarlatMaterialC), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    n = int(T.shape[0])
+    phi = torch.empty(n, dtype=torch.float64, device=T.device)
+    N = torch.empty((n, 6), dtype=torch.float64, device=T.device) if with_N else None
+    m = barlat_material(mat)
+    _check(f(C.byref(m), _ptr(T), n, _ptr(phi), _ptr(N), stream), "hfe_barlat_phi")
+    return (phi, N) if with_N else phi
+
+
+def cpp_options(line_search=True, kmax=40, jmax=10, beta=1e-4, eta=0.1, tol=1e-13, precision="fp64") -> CppOptions:
+    return CppOptions(int(kmax), int(bool(line_search)), int(jmax), float(beta), float(eta), float(tol),
+                      PRECISION[precision])
+
+
+def barlat_return_map(mat, T_trial, alpha_n, tangent=False, stream=None, out=None, **options):
+    """Elastic predictor / plastic corrector for n trial stresses T_trial (float64 CUDA [n, 6])
+    with alpha_n (float64 CUDA [n]) through hfe_barlat_return_map; options as cpp_options.
+    Returns a dict of CUDA tensors T [n, 6], alpha [n], dgamma [n], iters (int32) [n],
+    status (int8) [n] and, if tangent, tangent [n, 6, 6] = dT/dT_trial.  `out`, a dict of
+    such tensors, is written in place instead of allocating."""
+    import torch
+    L = lib()
+    f = L.hfe_barlat_return_map
+    f.argtypes = [C.POINTER(BarlatMaterialC), C.POINTER(CppOptions), C.c_void_p, C.c_void_p, C.c_int64,
+                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    n = int(T_trial.shape[0])
+    dev = T_trial.device
+    if out is None:
+        out = dict(T=torch.empty((n, 6), dtype=torch.float64, device=dev),
+                   alpha=torch.empty(n, dtype=torch.float64, device=dev),
+                   dgamma=torch.empty(n, dtype=torch.float64, device=dev),
+                   iters=torch.empty(n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int8, device=dev))
+        if tangent:
+            out["tangent"] = torch.empty((n, 6, 6), dtype=torch.float64, device=dev)
+    m = barlat_material(mat)
+    o = cpp_options(**options)
+    st = f(C.byref(m), C.byref(o), _ptr(T_trial), _ptr(alpha_n), n, _ptr(out["T"]), _ptr(out["alpha"]),
+           _ptr(out["dgamma"]), _ptr(out["iters"]), _ptr(out["status"]), _ptr(out.get("tangent")), stream)
+    _check(st, "hfe_barlat_return_map")
+    return out
