@@ -134,6 +134,69 @@ def cpu_oracle_rate(mesh, mat, u, hist, target_s=12.0, seed=0):
     return 8 * k / dt, f"oracle tangent sweep + assembly of {k} random elements ({8 * k} Gauss points) of the same state", 1, dt
 
 
+def barlat_map_section(reps, stream, dev, with_cpu):
+    """Device time of hfe_barlat_return_map on the App. B robustness map and on a 64-times
+    larger batch (CUDA events on the launching stream, after 3 warm-up launches), outcome
+    counts, and the oracle's rate on a bounded sample of the same map."""
+    import torch
+    from paper_2606_17390_b300 import hfe
+    mat = inputs.barlat_verification_material()
+    n = 16000
+    angle, scale = inputs.pi_plane_sample(n)
+    with torch.cuda.stream(stream):
+        d = torch.from_numpy(inputs.principal_plane_directions(angle)).to(dev)
+        phi = hfe.barlat_phi(mat, d, stream=stream.cuda_stream)
+        Tt = (torch.from_numpy(scale).to(dev)[:, None] / phi[:, None]) * d
+        a0 = torch.zeros(n, dtype=torch.float64, device=dev)
+        big_T, big_a = Tt.repeat(64, 1).contiguous(), a0.repeat(64).contiguous()
+
+    def run(T, a, reps_, **kw):
+        with torch.cuda.stream(stream):
+            out = hfe.barlat_return_map(mat, T, a, stream=stream.cuda_stream, **kw)
+            for _ in range(3):
+                hfe.barlat_return_map(mat, T, a, stream=stream.cuda_stream, out=out, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps_):
+                hfe.barlat_return_map(mat, T, a, stream=stream.cuda_stream, out=out, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps_
+        st = out["status"].cpu().numpy()
+        it = out["iters"].cpu().numpy()
+        conv = st == 0
+        return {"ms": ms, "points_per_s": T.shape[0] / (ms * 1e-3), "converged": int(conv.sum()),
+                "at_kmax": int((st == 2).sum()), "other": int((~conv & (st != 2)).sum()),
+                "mean_iters_converged": float(it[conv].mean()) if conv.any() else None,
+                "launches": 2 if kw.get("precision") == "mixed" else 1}
+
+    sec = {"workload": "line-search robustness map: 16,000 seeded pi-plane trial states between the yield surface "
+                       "and 30 times it; Yld2004-18p verification parameters (m = 8, E = 1000, nu = 0.3, "
+                       "sigma0 = 1, perfect plasticity); k_max 40, beta 1e-4, eta 0.1, tol 1e-13; inputs are "
+                       "0.8 MB (compute-bound, L2 irrelevant)"}
+    for prec in ("mixed", "fp64"):
+        for ls in (True, False):
+            sec[f"{prec}_{'line_search' if ls else 'newton'}"] = run(Tt, a0, reps, precision=prec, line_search=ls)
+        sec[f"{prec}_line_search_1M"] = run(big_T, big_a, max(2, reps // 10), precision=prec, line_search=True)
+    if with_cpu:
+        from oracle import barlat as BA
+        model = BA.Barlat(mat.c1, mat.c2, mat.m)
+        dd = inputs.principal_plane_directions(angle)
+        To = (scale / model.phi_poly(dd))[:, None] * dd
+        t0 = time.perf_counter()
+        _, _, conv_o = BA.cpp(model, mat.E, mat.nu, mat.hardening, mat.h, To, np.zeros(n), kmax=40)
+        dt = time.perf_counter() - t0
+        sec["cpu_baseline"] = {"points_per_s": n / dt, "cores": 1, "kind": "oracle", "seconds": dt,
+                               "converged": int(conv_o.sum()),
+                               "sample": "the oracle's closest-point projection with the line search on the whole "
+                                         "16,000-point map (FP64 numpy, vectorised over the points, 1 thread)"}
+        k = n
+        sec["mixed_over_oracle"] = sec["mixed_line_search"]["points_per_s"] / (k / dt)
+        sec["fp64_over_oracle"] = sec["fp64_line_search"]["points_per_s"] / (k / dt)
+    return sec
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -175,6 +238,8 @@ def main():
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
+    ap.add_argument("--barlat-reps", type=int, default=20,
+                    help="timed launches of the Barlat line-search map (0 = skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -403,6 +468,14 @@ def main():
                    "sweep_s": st2["sweep_ms"] * 1e-3, "solve_s": st2["solve_ms"] * 1e-3,
                    "in_solve_gp_per_s": st2["sweeps"] * 8 * m2.n_el / (st2["sweep_ms"] * 1e-3)}
 
+    # Barlat Yld2004-18p material points: the line-search robustness map (16,000 pi-plane trial
+    # states between the yield surface and 30 times it, the verification parameters, perfect
+    # plasticity, k_max 40), with and without the line search, FP64 and mixed, plus a
+    # 1,024,000-point batch (the map 64 times) for throughput; the oracle on a bounded sample
+    barlat = None
+    if args.barlat_reps > 0:
+        barlat = barlat_map_section(args.barlat_reps, stream, dev, rank == 0 and not args.no_cpu_baseline)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist)
@@ -421,6 +494,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
                 "pcg": pcg, "adjoint": adjoint, "forward": forward, "fbar_sweep": fbar,
+                "barlat_map": barlat,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

@@ -30,8 +30,10 @@
 // at the returned state.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "gp_math.cuh"
 #include "hfe.h"
@@ -52,7 +54,7 @@ constexpr int kPolishMax = 6;
 
 // phase outcomes (the first five are the HFE_CPP_* codes)
 constexpr int kConverged = HFE_CPP_CONVERGED, kElastic = HFE_CPP_ELASTIC, kMaxit = HFE_CPP_MAXIT,
-              kSingular = HFE_CPP_SINGULAR, kNonfinite = HFE_CPP_NONFINITE, kAmbiguous = 5;
+              kSingular = HFE_CPP_SINGULAR, kNonfinite = HFE_CPP_NONFINITE, kAmbiguous = 6;
 
 // X : Y = sum_p w(p) X_p Y_p over the six components
 template <typename R>
@@ -326,11 +328,15 @@ __device__ __forceinline__ bool lu_solve6(R A[6][6], R X[6][NR]) {
     for (int r = k + 1; r < 6; ++r)
       if (fabs(A[r][k]) > best) { best = fabs(A[r][k]); piv = r; }
     if (!(best > R(0))) return false;
-    if (piv != k) {
+    // row exchange with compile-time indices only (keeps A and X in registers)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) { const R t = A[k][c]; A[k][c] = A[piv][c]; A[piv][c] = t; }
+    for (int r = k + 1; r < 6; ++r) {
+      if (r == piv) {
 #pragma unroll
-      for (int c = 0; c < NR; ++c) { const R t = X[k][c]; X[k][c] = X[piv][c]; X[piv][c] = t; }
+        for (int c = 0; c < 6; ++c) { const R t = A[k][c]; A[k][c] = A[r][c]; A[r][c] = t; }
+#pragma unroll
+        for (int c = 0; c < NR; ++c) { const R t = X[k][c]; X[k][c] = X[r][c]; X[r][c] = t; }
+      }
     }
     const R inv = R(1) / A[k][k];
 #pragma unroll
@@ -381,210 +387,358 @@ __device__ __forceinline__ R psi_of(const R G[8]) {
 // place) with the App. B line search, until the scaled residual is <= tol, or k reaches kend.
 // elastic_test: 0 none, 1 f_tr <= 0 is elastic (the exact test, taken at the first
 // evaluation), 2 banded (f_tr < -band elastic, |f_tr| <= band undecided: kAmbiguous).
+//
+// Every pass of the loop evaluates G at one trial point, so that the lanes of a warp, which
+// sit at different stages of their own iterations, share that evaluation; a lane whose trial
+// is accepted (or that starts) goes on, in the same pass, to its convergence test and its
+// next Newton direction.  With the full step accepted, one Newton iteration is one pass.
 template <typename R>
 __device__ __forceinline__ int cpp_phase(const BarlatDev& P, R y[8], const R Ttr[6], R alpn, R isref, R tol,
                                          int kend, int& k, int elastic_test) {
   const Scal<R>& cs = scal<R>(P);
-  R dy[8], G[8], dphi[6];
-  Spec<R> s;
-  int mode = 0;          // 0: at a Newton iterate; 1: testing the full step; 2: line-search trial j
+  R dy[8];
+  // trial of this pass: y itself (kAt), the full step (kFull), a line-search step (kLine)
+  constexpr int kAt = 0, kFull = 1, kLine = 2;
+  int mode = kAt;
   int j = 0;
   R z = R(1), psi0 = R(0);
-  bool have_G = false;   // G, s, dphi already hold the values at y (an accepted, tested trial)
+#pragma unroll
+  for (int p = 0; p < 8; ++p) dy[p] = R(0);
   const int guard = (kend - k + 1) * (P.jmax + 3) + 2;
   for (int it = 0; it < guard; ++it) {
-    R yt[8];
+    R yt[8], G[8], dphi[6];
+    Spec<R> s;
+    const R zt = (mode == kAt) ? R(0) : z;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) yt[p] = (mode == 0) ? y[p] : fma(z, dy[p], y[p]);
-    R Gt[8], dphit[6];
-    Spec<R> st;
-    bool fin = true;
-    if (!(mode == 0 && have_G)) {
-      fin = residual<R>(P, yt, Ttr, alpn, Gt, st, dphit);
-    } else {
+    for (int p = 0; p < 8; ++p) yt[p] = fma(zt, dy[p], y[p]);
+    const bool fin = residual<R>(P, yt, Ttr, alpn, G, s, dphi);
+    if (mode != kAt) {
+      const R psit = fin ? psi_of<R>(G) : R(INFINITY);
+      const R zc = (mode == kFull) ? R(1) : z;
+      if (!(psit < (R(1) - R(2) * cs.beta * zc) * psi0)) {   // Eq. goldstein_full fails
+        if (mode == kFull) {
+          z = psi0 / (psi0 + psit);                          // Eq. alpha_init
+          mode = kLine;
+          j = 0;
+        } else {
+          z = fmax(cs.eta * z, psi0 / (psi0 + psit));        // Eq. alpha_update_ls, Eq. alpha_safeguard
+          if (++j > P.jmax) {                                // j_max exhausted: take the last step untested
 #pragma unroll
-      for (int p = 0; p < 8; ++p) Gt[p] = G[p];
-#pragma unroll
-      for (int p = 0; p < 6; ++p) dphit[p] = dphi[p];
-      st = s;
-    }
-    if (mode == 0) {
-#pragma unroll
-      for (int p = 0; p < 8; ++p) G[p] = Gt[p];
-#pragma unroll
-      for (int p = 0; p < 6; ++p) dphi[p] = dphit[p];
-      s = st;
-      have_G = false;
-      if (elastic_test != 0) {   // elastic predictor test (App. C): f_tr = phi(T_tr) - sigma_y(alpha_n)
-        const R f = G[7];
-        const int et = elastic_test;
-        elastic_test = 0;
-        if (isfinite(f)) {
-          if (et == 1 && f <= R(0)) return kElastic;
-          if (et == 2) {
-            const R band = R(kElasticBand) / isref;
-            if (f < -band) return kElastic;
-            if (f <= band) return kAmbiguous;
+            for (int p = 0; p < 8; ++p) y[p] = fma(z, dy[p], y[p]);
+            mode = kAt;
           }
         }
-      }
-      if (!fin) return kNonfinite;
-      R r2 = R(0);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) r2 += (G[p] * isref) * (G[p] * isref);
-      r2 += G[6] * G[6] + (G[7] * isref) * (G[7] * isref);
-      if (sqrt(r2) <= tol) return kConverged;
-      if (k >= kend) return kMaxit;
-      // Newton direction: J dy = -G by block elimination (G_alpha is linear in y)
-      R H[6][6], A6[6][6], X[6][2], EN[6], N[6];
-      phi_hessian<R>(P, s, dphi, H);
-      build_A6<R>(P, H, y[7], A6);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) N[p] = dphi[p] / kWf<R>(p);
-      elastic<R>(P, N, EN);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) { X[p][0] = G[p]; X[p][1] = EN[p]; }
-      R hs;
-      sigma_y<R>(P, y[6], &hs);
-      bool okj = lu_solve6<R, 2>(A6, X);
-      R nx1 = R(0), nx2 = R(0);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) { nx1 += dphi[p] * X[p][0]; nx2 += dphi[p] * X[p][1]; }
-      const R den = nx2 + hs;
-      okj = okj && den != R(0) && isfinite(den);
-      if (!okj) return kSingular;
-      const R ddg = (G[7] + hs * G[6] - nx1) / den;
-#pragma unroll
-      for (int p = 0; p < 6; ++p) dy[p] = -X[p][0] - X[p][1] * ddg;
-      dy[6] = ddg - G[6];
-      dy[7] = ddg;
-      ++k;
-      if (!P.line_search) {
-#pragma unroll
-        for (int p = 0; p < 8; ++p) y[p] += dy[p];
         continue;
       }
-      psi0 = psi_of<R>(G);
-      z = R(1);
-      mode = 1;
-      continue;
+      // the tested step is accepted: its residual is the new iterate's
+#pragma unroll
+      for (int p = 0; p < 8; ++p) y[p] = yt[p];
+      mode = kAt;
     }
-    const R psit = fin ? psi_of<R>(Gt) : R(INFINITY);
-    if (mode == 1) {
-      if (!(psit < (R(1) - R(2) * cs.beta) * psi0)) {      // Eq. goldstein_full at zeta = 1
-        z = psi0 / (psi0 + psit);                          // Eq. alpha_init
-        mode = 2;
-        j = 0;
-        continue;
+    if (elastic_test != 0) {   // elastic predictor test (App. C): f_tr = phi(T_tr) - sigma_y(alpha_n)
+      const R f = G[7];
+      const int et = elastic_test;
+      elastic_test = 0;
+      if (isfinite(f)) {
+        if (et == 1 && f <= R(0)) return kElastic;
+        if (et == 2) {
+          const R band = R(kElasticBand) / isref;
+          if (f < -band) return kElastic;
+          if (f <= band) return kAmbiguous;
+        }
       }
-    } else if (!(psit < (R(1) - R(2) * cs.beta * z) * psi0)) {   // Eq. goldstein_full
-      z = fmax(cs.eta * z, psi0 / (psi0 + psit));          // Eq. alpha_update_ls, Eq. alpha_safeguard
-      if (++j <= P.jmax) continue;
-      // j_max exhausted: the last step length is taken untested
-#pragma unroll
-      for (int p = 0; p < 8; ++p) y[p] = fma(z, dy[p], y[p]);
-      mode = 0;
-      continue;
     }
-    // the tested step is accepted: its residual is the next iterate's
+    if (!fin) return kNonfinite;
+    R r2 = R(0);
 #pragma unroll
-    for (int p = 0; p < 8; ++p) y[p] = yt[p];
+    for (int p = 0; p < 6; ++p) r2 += (G[p] * isref) * (G[p] * isref);
+    r2 += G[6] * G[6] + (G[7] * isref) * (G[7] * isref);
+    if (sqrt(r2) <= tol) return kConverged;
+    if (k >= kend) return kMaxit;
+    // Newton direction: J dy = -G by block elimination (G_alpha is linear in y)
+    R H[6][6], A6[6][6], X[6][2], EN[6], N[6];
+    phi_hessian<R>(P, s, dphi, H);
+    build_A6<R>(P, H, y[7], A6);
 #pragma unroll
-    for (int p = 0; p < 8; ++p) G[p] = Gt[p];
+    for (int p = 0; p < 6; ++p) N[p] = dphi[p] / kWf<R>(p);
+    elastic<R>(P, N, EN);
 #pragma unroll
-    for (int p = 0; p < 6; ++p) dphi[p] = dphit[p];
-    s = st;
-    have_G = fin;
-    mode = 0;
+    for (int p = 0; p < 6; ++p) { X[p][0] = G[p]; X[p][1] = EN[p]; }
+    R hs;
+    sigma_y<R>(P, y[6], &hs);
+    bool okj = lu_solve6<R, 2>(A6, X);
+    R nx1 = R(0), nx2 = R(0);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) { nx1 += dphi[p] * X[p][0]; nx2 += dphi[p] * X[p][1]; }
+    const R den = nx2 + hs;
+    okj = okj && den != R(0) && isfinite(den);
+    if (!okj) return kSingular;
+    const R ddg = (G[7] + hs * G[6] - nx1) / den;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) dy[p] = -X[p][0] - X[p][1] * ddg;
+    dy[6] = ddg - G[6];
+    dy[7] = ddg;
+    ++k;
+    if (!P.line_search) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) y[p] += dy[p];
+      continue;   // mode stays kAt: the next pass evaluates the new iterate
+    }
+    psi0 = psi_of<R>(G);
+    z = R(1);
+    mode = kFull;
   }
   return kMaxit;
 }
 
-__global__ void __launch_bounds__(kThreads) barlat_cpp_kernel(BarlatDev prm, const double* __restrict__ Ttr_g,
-                                                              const double* __restrict__ alpn_g, int64_t n,
-                                                              double* __restrict__ T_out,
-                                                              double* __restrict__ alpha_out,
-                                                              double* __restrict__ dg_out,
-                                                              int32_t* __restrict__ it_out,
-                                                              int8_t* __restrict__ st_out,
-                                                              double* __restrict__ tan_out) {
-  __shared__ BarlatDev P;
-  if (threadIdx.x == 0) P = prm;
-  __syncthreads();
-  const int64_t pt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (pt >= n) return;
-
+// Per-point inputs shared by the kernels: the trial stress, alpha_n, whether they are finite,
+// and 1/s of the convergence test, s = max(sigma_y(alpha_n), |T_tr|).
+struct PointIn {
   double Ttr[6];
+  double alpn;
+  double isref;
+  bool finite;
+};
+
+__device__ __forceinline__ void load_point(const BarlatDev& P, const double* __restrict__ Ttr_g,
+                                           const double* __restrict__ alpn_g, int64_t pt, PointIn& q) {
 #pragma unroll
-  for (int p = 0; p < 6; ++p) Ttr[p] = Ttr_g[pt * 6 + p];
-  const double alpn = alpn_g[pt];
-  bool finite_in = isfinite(alpn);
+  for (int p = 0; p < 6; ++p) q.Ttr[p] = Ttr_g[pt * 6 + p];
+  q.alpn = alpn_g[pt];
+  bool fin = isfinite(q.alpn);
 #pragma unroll
-  for (int p = 0; p < 6; ++p) finite_in = finite_in && isfinite(Ttr[p]);
+  for (int p = 0; p < 6; ++p) fin = fin && isfinite(q.Ttr[p]);
+  q.finite = fin;
   double ds0;
-  double sref = sigma_y<double>(P, alpn, &ds0);
-  {
-    double nt = 0.0;
+  double sref = sigma_y<double>(P, q.alpn, &ds0);
+  double nt = 0.0;
 #pragma unroll
-    for (int p = 0; p < 6; ++p) nt = fma(Ttr[p], Ttr[p], nt);
-    sref = fmax(sref, sqrt(nt));
-  }
-  const double isref = 1.0 / sref;
+  for (int p = 0; p < 6; ++p) nt = fma(q.Ttr[p], q.Ttr[p], nt);
+  q.isref = 1.0 / fmax(sref, sqrt(nt));
+}
 
-  double y[8];
-#pragma unroll
-  for (int p = 0; p < 6; ++p) y[p] = Ttr[p];
-  y[6] = alpn;
-  y[7] = 0.0;
-  int k = 0;
-  int status = kNonfinite;
-  if (finite_in && P.precision == HFE_PRECISION_MIXED) {
-    float yf[8], Tf[6];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) yf[p] = (float)y[p];
-#pragma unroll
-    for (int p = 0; p < 6; ++p) Tf[p] = (float)Ttr[p];
-    const int r = cpp_phase<float>(P, yf, Tf, (float)alpn, (float)isref, kTolSwitch, P.kmax, k, 2);
-    if (r == kElastic) {
-      status = kElastic;
-    } else if (r == kMaxit) {
-#pragma unroll
-      for (int p = 0; p < 8; ++p) y[p] = (double)yf[p];
-      status = kMaxit;
-    } else if (r == kConverged) {   // FP64 polish from the FP32 iterate
-#pragma unroll
-      for (int p = 0; p < 8; ++p) y[p] = (double)yf[p];
-      status = cpp_phase<double>(P, y, Ttr, alpn, isref, P.tol, k + kPolishMax, k, 0);
-    } else {                        // undecided elastic test or an FP32 failure: FP64 from the start
-      k = 0;
-      status = cpp_phase<double>(P, y, Ttr, alpn, isref, P.tol, P.kmax, k, r == kAmbiguous ? 1 : 0);
-    }
-  } else if (finite_in) {
-    status = cpp_phase<double>(P, y, Ttr, alpn, isref, P.tol, P.kmax, k, 1);
-  }
-
-  if (status == kElastic) {
-#pragma unroll
-    for (int p = 0; p < 6; ++p) y[p] = Ttr[p];
-    y[6] = alpn;
-    y[7] = 0.0;
-  }
+__device__ __forceinline__ void store_point(int64_t pt, const double y[8], int k, int status,
+                                            double* __restrict__ T_out, double* __restrict__ alpha_out,
+                                            double* __restrict__ dg_out, int32_t* __restrict__ it_out,
+                                            int8_t* __restrict__ st_out) {
 #pragma unroll
   for (int p = 0; p < 6; ++p) T_out[pt * 6 + p] = y[p];
   alpha_out[pt] = y[6];
   dg_out[pt] = y[7];
   it_out[pt] = k;
   st_out[pt] = (int8_t)status;
-  if (tan_out == nullptr) return;
-  // dT/dT_tr (App. D) at the returned state, in FP64: J z = [e_c; 0; 0] for each component c
+}
+
+// Persistent lane scheduling.  The grid holds as many threads as the GPU keeps resident;
+// warp w owns the points [n w / W, n (w + 1) / W).  Each lane works on one point at a time
+// for at most `chunk` Newton iterations per round; a lane whose point is finished takes the
+// next unclaimed point of its warp (ranked by a ballot), so that the lanes of a warp are not
+// held by the slowest point of a fixed group.  A round ends at a Newton iterate (cpp_phase
+// returns kMaxit there when k reaches its bound), and the next round starts from that iterate
+// with the same state, so the result does not depend on `chunk`.
+struct LaneSched {
+  int64_t cursor, hi;
+  int lane;
+};
+
+__device__ __forceinline__ LaneSched lane_sched(int64_t n) {
+  const int64_t wid = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int64_t W = ((int64_t)gridDim.x * kThreads) >> 5;
+  LaneSched L;
+  L.cursor = n * wid / W;
+  L.hi = n * (wid + 1) / W;
+  L.lane = threadIdx.x & 31;
+  return L;
+}
+
+// Claims points for the lanes with pt == -1 (in lane order); pt = -2 once the warp's range
+// is exhausted.  Returns false when every lane of the warp is done.  All 32 lanes call it.
+__device__ __forceinline__ bool lane_claim(LaneSched& L, int64_t& pt) {
+  const unsigned need = __ballot_sync(0xffffffffu, pt == -1);
+  if (pt == -1) {
+    const int64_t c = L.cursor + __popc(need & ((1u << L.lane) - 1u));
+    pt = (c < L.hi) ? c : -2;
+  }
+  L.cursor += __popc(need);
+  return !__all_sync(0xffffffffu, pt == -2);
+}
+
+// Mixed precision, first kernel: the FP32 phase (registers bounded for 5 resident blocks per
+// SM: the spills cost less than the latency hidden by the extra warps, measured on the
+// 16,000-point map and on a 64 times larger batch).  Its results go to the output arrays:
+// kConverged (the scaled residual reached kTolSwitch; the FP64 finish follows), kElastic,
+// kMaxit and kNonfinite (final), or kRestart (an undecided elastic test or an FP32 failure:
+// the FP64 kernel starts this point again).
+constexpr int kRestart = 5;
+
+__global__ void __launch_bounds__(kThreads, 5) barlat_fp32_kernel(BarlatDev prm, const double* __restrict__ Ttr_g,
+                                                               const double* __restrict__ alpn_g, int64_t n,
+                                                               int chunk, double* __restrict__ T_out,
+                                                               double* __restrict__ alpha_out,
+                                                               double* __restrict__ dg_out,
+                                                               int32_t* __restrict__ it_out,
+                                                               int8_t* __restrict__ st_out) {
+  __shared__ BarlatDev P;
+  if (threadIdx.x == 0) P = prm;
+  __syncthreads();
+  LaneSched L = lane_sched(n);
+  int64_t pt = -1;
+  float yf[8], Tf[6], alf = 0.f, isf = 0.f;
+  int k = 0, test = 0;
+  bool fresh = true;   // the lane's point has not started a round yet
+  while (lane_claim(L, pt)) {
+    if (pt < 0) continue;
+    if (fresh) {
+      PointIn q;
+      load_point(P, Ttr_g, alpn_g, pt, q);
+      if (!q.finite) {
+        double y0[8];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) y0[p] = q.Ttr[p];
+        y0[6] = q.alpn;
+        y0[7] = 0.0;
+        store_point(pt, y0, 0, kNonfinite, T_out, alpha_out, dg_out, it_out, st_out);
+        pt = -1;
+        continue;
+      }
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        Tf[p] = (float)q.Ttr[p];
+        yf[p] = Tf[p];
+      }
+      alf = (float)q.alpn;
+      yf[6] = alf;
+      yf[7] = 0.f;
+      isf = (float)q.isref;
+      k = 0;
+      test = 2;
+      fresh = false;
+    }
+    const int k0 = k;
+    const int r = cpp_phase<float>(P, yf, Tf, alf, isf, kTolSwitch, min(k + chunk, P.kmax), k, test);
+    test = 0;
+    if (r == kMaxit && k < P.kmax && k > k0) continue;   // end of a round: the point goes on
+    double y[8];
+    int status;
+    if (r == kConverged || r == kMaxit) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) y[p] = (double)yf[p];
+      status = r;
+    } else {
+      PointIn q;
+      load_point(P, Ttr_g, alpn_g, pt, q);
+#pragma unroll
+      for (int p = 0; p < 6; ++p) y[p] = q.Ttr[p];
+      y[6] = q.alpn;
+      y[7] = 0.0;
+      status = (r == kElastic) ? kElastic : kRestart;
+    }
+    store_point(pt, y, k, status, T_out, alpha_out, dg_out, it_out, st_out);
+    pt = -1;
+    fresh = true;
+  }
+}
+
+// FP64 kernel: the whole projection (full != 0: precision FP64), or the finish of the mixed
+// path from the FP32 results in the output arrays (full == 0).  Elastic points get T = T_tr.
+// Same lane scheduling as the FP32 kernel.  MINB: resident blocks per SM the register
+// allocation is bounded for (3 for the whole FP64 projection, 1 for the short finish; both
+// measured on the 16,000-point map and on a 64 times larger batch).
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) barlat_fp64_kernel(BarlatDev prm, const double* __restrict__ Ttr_g,
+                                                               const double* __restrict__ alpn_g, int64_t n,
+                                                               int full, int chunk, double* __restrict__ T_out,
+                                                               double* __restrict__ alpha_out,
+                                                               double* __restrict__ dg_out,
+                                                               int32_t* __restrict__ it_out,
+                                                               int8_t* __restrict__ st_out) {
+  __shared__ BarlatDev P;
+  if (threadIdx.x == 0) P = prm;
+  __syncthreads();
+  LaneSched L = lane_sched(n);
+  int64_t pt = -1;
+  PointIn q;
+  double y[8];
+  int k = 0, kend_pt = 0, test = 0;
+  bool fresh = true;   // the lane's point has not started a round yet
+  while (lane_claim(L, pt)) {
+    if (pt < 0) continue;
+    if (fresh) {
+      const int code = full ? kRestart : (int)st_out[pt];
+      if (code == kMaxit || code == kNonfinite) {   // final after the FP32 phase
+        pt = -1;
+        continue;
+      }
+      load_point(P, Ttr_g, alpn_g, pt, q);
+      if (code == kConverged) {   // FP64 Newton finish from the FP32 iterate
+#pragma unroll
+        for (int p = 0; p < 6; ++p) y[p] = T_out[pt * 6 + p];
+        y[6] = alpha_out[pt];
+        y[7] = dg_out[pt];
+        k = it_out[pt];
+        kend_pt = k + kPolishMax;
+        test = 0;
+      } else {
+#pragma unroll
+        for (int p = 0; p < 6; ++p) y[p] = q.Ttr[p];
+        y[6] = q.alpn;
+        y[7] = 0.0;
+        k = 0;
+        kend_pt = P.kmax;
+        test = 1;
+      }
+      if (code == kElastic || !q.finite) {
+        store_point(pt, y, 0, code == kElastic ? kElastic : kNonfinite, T_out, alpha_out, dg_out, it_out, st_out);
+        pt = -1;
+        continue;
+      }
+      fresh = false;
+    }
+    const int k0 = k;
+    int status = cpp_phase<double>(P, y, q.Ttr, q.alpn, q.isref, P.tol, min(k + chunk, kend_pt), k, test);
+    test = 0;
+    if (status == kMaxit && k < kend_pt && k > k0) continue;   // end of a round: the point goes on
+    if (status == kElastic) {
+#pragma unroll
+      for (int p = 0; p < 6; ++p) y[p] = q.Ttr[p];
+      y[6] = q.alpn;
+      y[7] = 0.0;
+    }
+    store_point(pt, y, k, status, T_out, alpha_out, dg_out, it_out, st_out);
+    pt = -1;
+    fresh = true;
+  }
+}
+
+// dT/dT_tr (App. D) at the returned state, in FP64: J z = [e_c; 0; 0] for each component c;
+// the identity for elastic and failed points.
+__global__ void __launch_bounds__(kThreads) barlat_tangent_kernel(BarlatDev prm, const double* __restrict__ Ttr_g,
+                                                                  const double* __restrict__ alpn_g, int64_t n,
+                                                                  const double* __restrict__ T_out,
+                                                                  const double* __restrict__ alpha_out,
+                                                                  const double* __restrict__ dg_out,
+                                                                  const int8_t* __restrict__ st_out,
+                                                                  double* __restrict__ tan_out) {
+  __shared__ BarlatDev P;
+  if (threadIdx.x == 0) P = prm;
+  __syncthreads();
+  const int64_t pt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (pt >= n) return;
+  const int status = st_out[pt];
   double Tg[6][6];
   bool okt = status == kConverged || status == kMaxit;
   if (okt) {
-    double G[8], dphi[6];
+    PointIn q;
+    load_point(P, Ttr_g, alpn_g, pt, q);
+    double y[8], G[8], dphi[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) y[p] = T_out[pt * 6 + p];
+    y[6] = alpha_out[pt];
+    y[7] = dg_out[pt];
     Spec<double> s;
-    okt = residual<double>(P, y, Ttr, alpn, G, s, dphi);
-    double H[6][6], A6[6][6], X[6][7], EN[6], N[6];
+    okt = residual<double>(P, y, q.Ttr, q.alpn, G, s, dphi);
     if (okt) {
+      double H[6][6], A6[6][6], X[6][7], EN[6], N[6];
       phi_hessian<double>(P, s, dphi, H);
       build_A6<double>(P, H, y[7], A6);
 #pragma unroll
@@ -617,7 +771,7 @@ __global__ void __launch_bounds__(kThreads) barlat_cpp_kernel(BarlatDev prm, con
       }
     }
   }
-  if (!okt) {   // elastic (and failed) points: the elastic response dT = dT_tr
+  if (!okt) {
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
@@ -737,6 +891,33 @@ hfe_status make_params(const hfe_barlat_material* mat, BarlatDev* P) {
   return HFE_OK;
 }
 
+constexpr int kChunk = 8;   // Newton iterations per round of the persistent kernels
+constexpr int kMaxDevices = 64;
+std::mutex g_occ_mutex;
+int g_occ32[kMaxDevices] = {}, g_occ64[kMaxDevices] = {}, g_occ64f[kMaxDevices] = {};
+
+// Blocks of the persistent kernels that the device keeps resident at once (SM count x
+// blocks per SM), looked up once per device.
+cudaError_t resident_blocks(int dev, int* g32, int* g64, int* g64f) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_occ_mutex);
+  if (g_occ32[dev] == 0) {
+    int sms = 0, b32 = 0, b64 = 0, b64f = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, barlat_fp32_kernel, kThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, barlat_fp64_kernel<3>, kThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64f, barlat_fp64_kernel<1>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    g_occ32[dev] = std::max(1, sms * b32);
+    g_occ64[dev] = std::max(1, sms * b64);
+    g_occ64f[dev] = std::max(1, sms * b64f);
+  }
+  *g32 = g_occ32[dev];
+  *g64 = g_occ64[dev];
+  *g64f = g_occ64f[dev];
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" void hfe_default_cpp_options(hfe_cpp_options* o) {
@@ -803,7 +984,25 @@ extern "C" hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, cons
   if (tangent_out != nullptr && !on_device(tangent_out, dev)) return HFE_EINVAL;
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   if (blocks > 0x7fffffffLL) return HFE_EINVAL;
-  barlat_cpp_kernel<<<(unsigned)blocks, kThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
-      P, T_trial, alpha_n, n, T_out, alpha_out, dgamma_out, iters_out, status_out, tangent_out);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const bool mixed = P.precision == HFE_PRECISION_MIXED;
+  int g32 = 0, g64 = 0, g64f = 0;
+  if (resident_blocks(dev, &g32, &g64, &g64f) != cudaSuccess) return HFE_ECUDA;
+  // one point per lane while the batch fits in the resident threads; otherwise rounds of
+  // kChunk iterations with lane refill
+  auto grid = [&](int resident) { return (unsigned)std::min<int64_t>(blocks, resident); };
+  auto chunk = [&](int resident) { return blocks > resident ? kChunk : (1 << 30); };
+  if (mixed) {
+    barlat_fp32_kernel<<<grid(g32), kThreads, 0, s>>>(P, T_trial, alpha_n, n, chunk(g32), T_out, alpha_out,
+                                                      dgamma_out, iters_out, status_out);
+    barlat_fp64_kernel<1><<<grid(g64f), kThreads, 0, s>>>(P, T_trial, alpha_n, n, 0, chunk(g64f), T_out, alpha_out,
+                                                          dgamma_out, iters_out, status_out);
+  } else {
+    barlat_fp64_kernel<3><<<grid(g64), kThreads, 0, s>>>(P, T_trial, alpha_n, n, 1, chunk(g64), T_out, alpha_out,
+                                                         dgamma_out, iters_out, status_out);
+  }
+  if (tangent_out != nullptr)
+    barlat_tangent_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(P, T_trial, alpha_n, n, T_out, alpha_out,
+                                                               dgamma_out, status_out, tangent_out);
   return cudaGetLastError() == cudaSuccess ? HFE_OK : HFE_ECUDA;
 }
