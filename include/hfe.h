@@ -279,7 +279,14 @@ hfe_status hfe_free_norm_static(const double* r, const uint8_t* free_mask, int64
  *   hardening, h[3]: HFE_HARDENING_SWIFT (K, eps0, n) or HFE_HARDENING_VOCE (sigma0, Q, b);
  *     perfect plasticity is Voce with Q = 0;
  *   Theta[9]: row-major 3x3 whose columns are the material axes (orthonormal to 1e-10;
- *     the identity for material axes = global axes). */
+ *     the identity for material axes = global axes);
+ *   orthotropic, d[9]: 0 = isotropic elasticity from E, nu; 1 = the orthotropic E of nine
+ *     stiffness coefficients in the material frame (Eq. T): d = (E1111, E2222, E3333, E1122,
+ *     E1133, E2233, E1212, E2323, E1313) with the minor and major symmetries, rotated by
+ *     Theta (E_g,ijkl = Theta_ia Theta_jb Theta_kc Theta_ld E_l,abcd); E and nu are then
+ *     unused by the return map but must still be valid.  d1, d2, d3, d7, d8, d9 > 0.
+ * Voce hardening for this model is Eq. Hard as printed: sigma_y = sigma0 + sqrt(2/3) Q
+ * (1 - exp(-b alpha)) (the Hill-48 handle path places sqrt(2/3) in f instead). */
 #define HFE_BARLAT_MAX_M 32
 typedef struct {
   double c1[9];
@@ -289,6 +296,8 @@ typedef struct {
   int hardening;
   double h[3];
   double Theta[9];
+  int orthotropic;
+  double d[9];
 } hfe_barlat_material;
 
 /* Local closest-point projection controls (App. B, App. C): at most kmax Newton iterations,

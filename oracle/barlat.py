@@ -19,7 +19,8 @@ leading batch of independent material points and nothing else.
   arguments, so the Jacobian of G follows by complex step.
 * `cpp` solves G(y) = 0 for y = [T (6), alpha, dgamma] (Eq. local_cpp) with
   G_T = T - T_tr + dgamma E : N(T), G_alpha = alpha - alpha_n - W dgamma with W = 1 for this
-  model (Eq. alpha_update), G_f = phi(T) - sigma_y(alpha) (Eq. yield_final), isotropic E.
+  model (Eq. alpha_update), G_f = phi(T) - sigma_y(alpha) (Eq. yield_final); E isotropic
+  (E, nu) or orthotropic from nine coefficients in the material frame (`orthotropic_tensor`).
   Newton (Eq. local_solver) from y0 = [T_tr, alpha_n, 0] (reading R7), optionally with the
   line search of App. B (Goldstein test Eq. goldstein_full, quadratic model Eq. alpha_init and
   Eq. alpha_update_ls, safeguard Eq. alpha_safeguard; reading R9 on the order), converged
@@ -151,8 +152,27 @@ def lame(E, nu):
     return E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
 
 
+def orthotropic_tensor(d, Theta=None):
+    """The fourth-order elasticity tensor (3, 3, 3, 3) from nine stiffness coefficients in the
+    material frame (Eq. T; reading R22): d = (E1111, E2222, E3333, E1122, E1133, E2233, E1212,
+    E2323, E1313) with the minor and major symmetries, rotated into the global frame as
+    E_g,ijkl = Theta_ia Theta_jb Theta_kc Theta_ld E_l,abcd (columns of Theta = material axes)."""
+    d1, d2, d3, d4, d5, d6, d7, d8, d9 = d
+    El = np.zeros((3, 3, 3, 3))
+    El[0, 0, 0, 0], El[1, 1, 1, 1], El[2, 2, 2, 2] = d1, d2, d3
+    for (a, b), v in (((0, 1), d4), ((0, 2), d5), ((1, 2), d6)):
+        El[a, a, b, b] = El[b, b, a, a] = v
+    for (a, b), v in (((0, 1), d7), ((1, 2), d8), ((0, 2), d9)):
+        El[a, b, a, b] = El[a, b, b, a] = El[b, a, a, b] = El[b, a, b, a] = v
+    Q = np.eye(3) if Theta is None else np.asarray(Theta, dtype=np.float64)
+    return np.einsum("ia,jb,kc,ld,abcd->ijkl", Q, Q, Q, Q, El)
+
+
 def elastic(E, nu, e):
-    """E : e on tensor components (isotropic: lambda tr(e) I + 2 mu e)."""
+    """E : e on tensor components: isotropic lambda tr(e) I + 2 mu e for a number E (with nu),
+    or the contraction with a fourth-order tensor E (3, 3, 3, 3) (nu unused)."""
+    if np.ndim(E) == 4:
+        return voigt(np.einsum("ijkl,...kl->...ij", E, tensor(e)))
     lam, mu = lame(E, nu)
     out = 2 * mu * e
     out[..., :3] += lam * np.sum(e[..., :3], axis=-1, keepdims=True)
@@ -160,13 +180,14 @@ def elastic(E, nu, e):
 
 
 def sigma_y(hardening, h, alpha):
-    """Swift K (eps0 + alpha)^n or Voce sigma0 + Q (1 - exp(-b alpha)) (Eq. Hard, W = 1);
-    perfect plasticity is Voce with Q = 0."""
+    """Swift K (eps0 + alpha)^n, or Voce as Eq. Hard prints it, sigma0 + sqrt(2/3) Q
+    (1 - exp(-b alpha)) (W = 1 and f = phi - sigma_y for this model; reading R19); perfect
+    plasticity is Voce with Q = 0."""
     if hardening == "swift":
         K, e0, n = h
         return K * (e0 + alpha) ** n
     s0, Q, b = h
-    return s0 + Q * (1.0 - np.exp(-b * alpha))
+    return s0 + np.sqrt(2.0 / 3.0) * Q * (1.0 - np.exp(-b * alpha))
 
 
 def residual(model, E, nu, hardening, h, y, Ttr, alpn):

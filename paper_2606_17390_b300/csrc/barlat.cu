@@ -70,11 +70,12 @@ struct Scal {
 struct BarlatDev {
   double LA[6][6];  // LA[b][p]: component p of s' for a unit component b of the global stress
   double LB[6][6];  // the same for s''
-  float LAf[6][6], LBf[6][6];
+  double EE[6][6];  // orthotropic E on components: (E : X)_p = sum_q EE[p][q] X_q
+  float LAf[6][6], LBf[6][6], EEf[6][6];
   Scal<double> sd;
   Scal<float> sf;
   double tol;
-  int m, hardening, kmax, jmax, line_search, precision;
+  int m, hardening, kmax, jmax, line_search, precision, ortho;
 };
 
 template <typename R>
@@ -86,6 +87,11 @@ template <typename R>
 __device__ __forceinline__ R tabB(const BarlatDev& P, int b, int p) {
   if constexpr (sizeof(R) == 4) return P.LBf[b][p];
   else return P.LB[b][p];
+}
+template <typename R>
+__device__ __forceinline__ R tabE(const BarlatDev& P, int p, int q) {
+  if constexpr (sizeof(R) == 4) return P.EEf[p][q];
+  else return P.EE[p][q];
 }
 template <typename R>
 __device__ __forceinline__ const Scal<R>& scal(const BarlatDev& P) {
@@ -287,9 +293,19 @@ __device__ __forceinline__ void phi_hessian(const BarlatDev& P, const Spec<R>& s
     }
 }
 
-// E : X for isotropic E on components
+// E : X on components (isotropic lambda tr(X) I + 2 mu X, or the orthotropic table)
 template <typename R>
 __device__ __forceinline__ void elastic(const BarlatDev& P, const R X[6], R out[6]) {
+  if (P.ortho) {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      R v = R(0);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v = fma(tabE<R>(P, p, q), X[q], v);
+      out[p] = v;
+    }
+    return;
+  }
   const Scal<R>& c = scal<R>(P);
   const R tr = c.lam * (X[0] + X[1] + X[2]);
 #pragma unroll
@@ -366,6 +382,18 @@ __device__ __forceinline__ bool lu_solve6(R A[6][6], R X[6][NR]) {
 template <typename R>
 __device__ __forceinline__ void build_A6(const BarlatDev& P, const R H[6][6], R dg, R A6[6][6]) {
   const Scal<R>& cs = scal<R>(P);
+  if (P.ortho) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      R dN[6], EdN[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) dN[q] = H[q][c] / kWf<R>(q);
+      elastic<R>(P, dN, EdN);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) A6[a][c] = (a == c ? R(1) : R(0)) + dg * EdN[a];
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     const R tr = cs.lam * (H[0][c] + H[1][c] + H[2][c]);
@@ -829,6 +857,8 @@ bool finite_all(const double* v, int n) {
   return true;
 }
 
+constexpr int I6[6] = {0, 1, 2, 0, 1, 0}, J6[6] = {0, 1, 2, 1, 2, 2};   // component p -> (i, j)
+
 hfe_status make_params(const hfe_barlat_material* mat, BarlatDev* P) {
   if (mat == nullptr) return HFE_EINVAL;
   if (mat->m < 2 || mat->m > HFE_BARLAT_MAX_M || (mat->m % 2) != 0) return HFE_EINVAL;
@@ -836,6 +866,12 @@ hfe_status make_params(const hfe_barlat_material* mat, BarlatDev* P) {
   if (mat->hardening != HFE_HARDENING_SWIFT && mat->hardening != HFE_HARDENING_VOCE) return HFE_EINVAL;
   if (!finite_all(mat->c1, 9) || !finite_all(mat->c2, 9) || !finite_all(mat->h, 3) || !finite_all(mat->Theta, 9))
     return HFE_EINVAL;
+  if (mat->orthotropic != 0) {
+    if (!finite_all(mat->d, 9)) return HFE_EINVAL;
+    const int diag[6] = {0, 1, 2, 6, 7, 8};
+    for (int t : diag)
+      if (!(mat->d[t] > 0.0)) return HFE_EINVAL;
+  }
   // Theta must be orthonormal (columns = material axes)
   const double* Q = mat->Theta;
   for (int a = 0; a < 3; ++a)
@@ -847,7 +883,6 @@ hfe_status make_params(const hfe_barlat_material* mat, BarlatDev* P) {
   double C1[6][6], C2[6][6];
   transform6(mat->c1, C1);
   transform6(mat->c2, C2);
-  static const int I6[6] = {0, 1, 2, 0, 1, 0}, J6[6] = {0, 1, 2, 1, 2, 2};
   for (int b = 0; b < 6; ++b) {
     // unit component b of the global stress (both symmetric entries for a shear component)
     double E[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
@@ -883,8 +918,41 @@ hfe_status make_params(const hfe_barlat_material* mat, BarlatDev* P) {
     }
   P->sd.lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
   P->sd.mu = mat->E / (2.0 * (1.0 + mat->nu));
+  P->ortho = mat->orthotropic != 0;
+  if (P->ortho) {
+    // E_l from the nine coefficients (E1111, E2222, E3333, E1122, E1133, E2233, E1212, E2323,
+    // E1313) with the minor and major symmetries; E_g,ijkl = Q_ia Q_jb Q_kc Q_ld E_l,abcd
+    const double* d = mat->d;
+    double El[3][3][3][3] = {};
+    El[0][0][0][0] = d[0];
+    El[1][1][1][1] = d[1];
+    El[2][2][2][2] = d[2];
+    const int na[3] = {0, 0, 1}, nb[3] = {1, 2, 2};
+    const double dn[3] = {d[3], d[4], d[5]};
+    const int sa[3] = {0, 1, 0}, sb[3] = {1, 2, 2};
+    const double ds[3] = {d[6], d[7], d[8]};
+    for (int t = 0; t < 3; ++t) {
+      El[na[t]][na[t]][nb[t]][nb[t]] = El[nb[t]][nb[t]][na[t]][na[t]] = dn[t];
+      const int a = sa[t], b = sb[t];
+      El[a][b][a][b] = El[a][b][b][a] = El[b][a][a][b] = El[b][a][b][a] = ds[t];
+    }
+    for (int p = 0; p < 6; ++p)
+      for (int q = 0; q < 6; ++q) {
+        const int i = I6[p], j = J6[p], k = I6[q], l = J6[q];
+        double v = 0.0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c)
+              for (int e = 0; e < 3; ++e)
+                v += Q[i * 3 + a] * Q[j * 3 + b] * Q[k * 3 + c] * Q[l * 3 + e] * El[a][b][c][e];
+        // acting on components: the kl and lk entries of X both equal X_q
+        P->EE[p][q] = v * (k == l ? 1.0 : 2.0);
+        P->EEf[p][q] = (float)P->EE[p][q];
+      }
+  }
   P->sd.h0 = mat->h[0];
-  P->sd.h1 = mat->h[1];
+  // Voce as Eq. Hard prints it for this model: sigma0 + sqrt(2/3) Q (1 - exp(-b alpha))
+  P->sd.h1 = mat->hardening == HFE_HARDENING_VOCE ? 0.81649658092772603273 * mat->h[1] : mat->h[1];
   P->sd.h2 = mat->h[2];
   P->m = mat->m;
   P->hardening = mat->hardening;

@@ -329,7 +329,8 @@ BARLAT_MAX_M = 32   # HFE_BARLAT_MAX_M of include/hfe.h
 
 class BarlatMaterialC(C.Structure):
     _fields_ = [("c1", C.c_double * 9), ("c2", C.c_double * 9), ("m", C.c_int), ("E", C.c_double),
-                ("nu", C.c_double), ("hardening", C.c_int), ("h", C.c_double * 3), ("Theta", C.c_double * 9)]
+                ("nu", C.c_double), ("hardening", C.c_int), ("h", C.c_double * 3), ("Theta", C.c_double * 9),
+                ("orthotropic", C.c_int), ("d", C.c_double * 9)]
 
 
 class CppOptions(C.Structure):
@@ -339,7 +340,8 @@ class CppOptions(C.Structure):
 
 def barlat_material(mat) -> BarlatMaterialC:
     """hfe_barlat_material from an object with c1, c2, m, E, nu, hardening ('swift'|'voce'),
-    h and Theta (None = identity), e.g. inputs.BarlatMaterial."""
+    h, Theta (None = identity) and optionally d (nine orthotropic stiffness coefficients in the
+    material frame; None = isotropic E, nu), e.g. inputs.BarlatMaterial."""
     s = BarlatMaterialC()
     s.c1[:] = [float(v) for v in mat.c1]
     s.c2[:] = [float(v) for v in mat.c2]
@@ -349,6 +351,9 @@ def barlat_material(mat) -> BarlatMaterialC:
     s.h[:] = [float(v) for v in mat.h]
     Th = np.eye(3) if getattr(mat, "Theta", None) is None else np.asarray(mat.Theta, dtype=np.float64)
     s.Theta[:] = [float(v) for v in Th.reshape(9)]
+    d = getattr(mat, "d", None)
+    s.orthotropic = 0 if d is None else 1
+    s.d[:] = [0.0] * 9 if d is None else [float(v) for v in d]
     return s
 
 

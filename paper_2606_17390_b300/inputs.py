@@ -365,8 +365,9 @@ def random_history(n: int, seed: int, eps_scale: float = 0.02, alpha_max: float 
 @dataclasses.dataclass
 class BarlatMaterial:
     """Yld2004-18p parameters: c1 = (c'12, c'13, c'21, c'23, c'31, c'32, c'44, c'55, c'66),
-    c2 the same for c'', even exponent m, isotropic E and nu, hardening law and parameters
-    ((sigma0, Q, b) for Voce, (K, eps0, n) for Swift), material frame Theta (columns = axes)."""
+    c2 the same for c'', even exponent m, isotropic E and nu (or nine orthotropic stiffness
+    coefficients d in the material frame), hardening law and parameters ((sigma0, Q, b) for
+    Voce, (K, eps0, n) for Swift), material frame Theta (columns = axes)."""
     c1: tuple
     c2: tuple
     m: int
@@ -375,6 +376,7 @@ class BarlatMaterial:
     hardening: str = "voce"
     h: tuple = (1.0, 0.0, 0.0)
     Theta: np.ndarray = None
+    d: tuple = None   # orthotropic stiffness (E1111, E2222, E3333, E1122, E1133, E2233, E1212, E2323, E1313)
 
 
 def barlat_verification_material() -> BarlatMaterial:

@@ -254,3 +254,48 @@ def test_elastic_empty_nonfinite_and_rejections():
     # the mixed path reports non-finite inputs the same way
     st_m = hfe.barlat_return_map(mat, bad * 10.0, a0, precision="mixed")["status"].cpu().numpy()
     assert st_m[2] == hfe_status("nonfinite") and st_m[3] == hfe_status("nonfinite")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_orthotropic_elasticity_and_voce_against_oracle(precision):
+    """An orthotropic, rotated E (nine coefficients in the material frame) with Voce hardening
+    (Q > 0, alpha_n > 0) in a rotated Barlat frame: stress, alpha, dgamma and the tangent
+    against the oracle; the isotropic coefficients through the orthotropic table give the
+    (E, nu) result."""
+    mat = inputs.barlat_verification_material()
+    mat.Theta = inputs.random_rotation(101)
+    mat.h = (1.0, 0.6, 15.0)
+    mat.d = (2.0e3, 1.4e3, 1.1e3, 0.5e3, 0.45e3, 0.4e3, 0.35e3, 0.3e3, 0.25e3)
+    Eg = BA.orthotropic_tensor(mat.d, mat.Theta)   # the elasticity frame is the material frame
+    model = _oracle_model(mat)
+    n = 96
+    rng = np.random.default_rng(103)
+    alpn = rng.uniform(0.0, 0.05, n)
+    T = inputs.random_stresses(n, seed=104, scale=1.0)
+    sy = BA.sigma_y("voce", mat.h, alpn)
+    Ttr = T * (sy * rng.uniform(1.05, 6.0, n) / model.phi_poly(T))[:, None]
+    y, it_o, conv_o = BA.cpp(model, Eg, None, "voce", mat.h, Ttr, alpn, kmax=60)
+    assert conv_o.all()
+    D_o = BA.cpp_tangent(model, Eg, None, "voce", mat.h, y, Ttr, alpn)
+    out = hfe.barlat_return_map(mat, _cuda(Ttr), _cuda(alpn), tangent=True, kmax=60, precision=precision)
+    assert (out["status"].cpu().numpy() == hfe_status("converged")).all()
+    sc = np.abs(Ttr).max()
+    assert np.abs(out["T"].cpu().numpy() - y[:, :6]).max() <= 1e-11 * sc
+    assert np.abs(out["alpha"].cpu().numpy() - y[:, 6]).max() <= 1e-12
+    assert np.abs(out["dgamma"].cpu().numpy() - y[:, 7]).max() <= 1e-11 * np.abs(y[:, 7]).max()
+    assert np.abs(out["tangent"].cpu().numpy() - D_o).max() <= 1e-8 * np.abs(D_o).max()
+    # isotropic coefficients through the orthotropic table = the (E, nu) path
+    lam, mu = BA.lame(mat.E, mat.nu)
+    iso = inputs.barlat_verification_material()
+    iso.Theta, iso.h = mat.Theta, mat.h
+    iso_d = inputs.barlat_verification_material()
+    iso_d.Theta, iso_d.h = mat.Theta, mat.h
+    iso_d.d = (lam + 2 * mu,) * 3 + (lam,) * 3 + (mu,) * 3
+    a = hfe.barlat_return_map(iso, _cuda(Ttr), _cuda(alpn), precision=precision)
+    b = hfe.barlat_return_map(iso_d, _cuda(Ttr), _cuda(alpn), precision=precision)
+    assert np.abs(a["T"].cpu().numpy() - b["T"].cpu().numpy()).max() <= 1e-12 * sc
+    # a non-positive stiffness coefficient is rejected
+    bad = inputs.barlat_verification_material()
+    bad.d = (0.0,) + mat.d[1:]
+    with pytest.raises(hfe.HfeError):
+        hfe.barlat_return_map(bad, _cuda(Ttr), _cuda(alpn))

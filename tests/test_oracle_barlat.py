@@ -254,3 +254,61 @@ def test_pi_plane_map_sample_line_search_converges_plain_newton_does_not():
     _, it_nw, conv_nw = _cpp(model, mat, Ttr, np.zeros(200), line_search=False, kmax=40)
     assert conv_ls.all() and it_ls.max() <= 40
     assert (~conv_nw).sum() >= 40
+
+
+def test_orthotropic_elasticity_reductions_and_symmetries():
+    """Isotropic coefficients (lambda + 2 mu, lambda, mu) give lambda tr(e) I + 2 mu e in any
+    frame; the tensor has the minor and major symmetries; rotating the frame and the strain
+    together leaves the energy e : E : e unchanged; in the material frame a diagonal strain
+    gives the stiffness matrix times the strain (closed form)."""
+    E, nu = 70000.0, 0.33
+    lam, mu = BA.lame(E, nu)
+    e = inputs.random_stresses(16, seed=80, scale=1e-3)
+    iso = BA.orthotropic_tensor((lam + 2 * mu,) * 3 + (lam,) * 3 + (mu,) * 3, inputs.random_rotation(81))
+    assert np.abs(BA.elastic(iso, None, e) - BA.elastic(E, nu, e)).max() <= 1e-12 * E * 1e-3
+    d = (210e3, 150e3, 120e3, 60e3, 50e3, 40e3, 30e3, 25e3, 20e3)
+    Th = inputs.random_rotation(82)
+    Eg = BA.orthotropic_tensor(d, Th)
+    for perm in ("jikl", "ijlk", "klij"):
+        assert np.abs(np.einsum("ijkl->" + perm, Eg) - Eg).max() <= 1e-9 * 210e3
+    Q = inputs.random_rotation(83)
+    Eq = BA.orthotropic_tensor(d, Q @ Th)
+    eg = BA.tensor(e)
+    eq = Q @ eg @ Q.T
+    w1 = np.einsum("nij,ijkl,nkl->n", eg, Eg, eg)
+    w2 = np.einsum("nij,ijkl,nkl->n", eq, Eq, eq)
+    assert np.abs(w1 - w2).max() <= 1e-12 * np.abs(w1).max()
+    El = BA.orthotropic_tensor(d)
+    diag = np.array([1e-3, -2e-3, 0.5e-3, 0, 0, 0])
+    C = np.array([[d[0], d[3], d[4]], [d[3], d[1], d[5]], [d[4], d[5], d[2]]])
+    assert np.allclose(BA.elastic(El, None, diag[None])[0, :3], C @ diag[:3], rtol=1e-14, atol=0)
+    shear = np.array([0, 0, 0, 1e-3, 2e-3, 3e-3])   # tensor components e12, e23, e13
+    assert np.allclose(BA.elastic(El, None, shear[None])[0, 3:], 2 * np.array([d[6], d[7], d[8]]) * shear[3:],
+                       rtol=1e-14, atol=0)
+
+
+def test_orthotropic_projection_is_the_energy_minimiser():
+    """With an orthotropic, rotated E the converged stress still minimises the complementary
+    energy (T_tr - T) : E^-1 : (T_tr - T) over phi <= sigma0 (perfect plasticity)."""
+    mat = inputs.barlat_verification_material()
+    model = _model(mat, inputs.random_rotation(91))
+    d = (2.0e3, 1.4e3, 1.1e3, 0.5e3, 0.45e3, 0.4e3, 0.35e3, 0.3e3, 0.25e3)
+    Eg = BA.orthotropic_tensor(d, inputs.random_rotation(92))
+    angle, scale = inputs.pi_plane_sample(4, seed=93, scale_max=8.0)
+    Ttr = _trial_states(model, mat, angle, scale, np.zeros(4))
+    y, it, conv = BA.cpp(model, Eg, None, mat.hardening, mat.h, Ttr, np.zeros(4))
+    assert conv.all()
+    S6 = np.linalg.inv(np.array([[Eg[i, j, k, l] * (1 if k == l else 2) for (k, l) in BA.VOIGT]
+                                 for (i, j) in BA.VOIGT]))   # component compliance
+
+    def energy(T, p):
+        dT = Ttr[p] - T
+        return 0.5 * np.sum(BA.W_SHEAR * dT * (S6 @ dT)) * 1e3
+
+    for p in range(4):
+        T0 = Ttr[p] / model.phi_eig(Ttr[p:p + 1])[0]
+        res = minimize(lambda x: energy(x, p), T0, method="SLSQP",
+                       constraints=[dict(type="ineq", fun=lambda x: 1.0 - model.phi_eig(x[None, :])[0])],
+                       options=dict(ftol=1e-16, maxiter=1000))
+        assert np.abs(res.x - y[p, :6]).max() <= 2e-5 * np.abs(Ttr[p]).max()
+        assert energy(y[p, :6], p) <= res.fun * (1 + 1e-9)
