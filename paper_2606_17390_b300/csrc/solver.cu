@@ -436,52 +436,70 @@ __device__ __forceinline__ bool grid_allreduce(GridSync* gs, const double* part,
 }
 
 // out = K in on the rows [n0, n1) (fixed rows 0; in is zero on fixed dofs), returning this
-// thread's share of out . w over those rows
+// thread's share of out . w over those rows.  Eight lanes per block row (four rows per warp
+// and pass): each lane takes two blocks of a 16-block chunk of its row and issues the
+// column, value and x loads of both before the arithmetic; the row sum is a three-level
+// shuffle within the eight lanes.  (A warp per row, one block per lane and a five-level
+// shuffle per row left the memory pipeline short of loads in flight: 0.38 against 0.34 ms
+// per CG iteration at 3.09M dofs.)
 template <typename R>
 __device__ __forceinline__ double spmv_range(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ cols,
                                              const R* __restrict__ vals, const uint8_t* __restrict__ freem,
                                              const R* in, R* out, const R* w, int64_t n0, int64_t n1) {
+  constexpr int kG = 8;                  // lanes per block row
+  constexpr int kRows = 32 / kG;         // block rows per warp and pass
+  constexpr int kWarps = kBlock / 32;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  constexpr int kWarps = kBlock / 32;
+  const int grp = lane / kG, gl = lane % kG;
   double dot = 0.0;
-  for (int64_t r0 = n0 + warp; r0 < n1; r0 += 2 * kWarps) {
-    const int64_t r1 = r0 + kWarps;
-    const bool has1 = r1 < n1;
-    const int64_t b0 = rowptr[r0], e0 = rowptr[r0 + 1];
-    const int64_t b1 = has1 ? rowptr[r1] : 0, e1 = has1 ? rowptr[r1 + 1] : 0;
-    const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
-    R acc[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
-    const int nmax = nb0 > nb1 ? nb0 : nb1;
-    for (int j = lane; j < nmax; j += 32) {
+  for (int64_t base = n0 + (int64_t)warp * kRows; base < n1; base += (int64_t)kWarps * kRows) {
+    const int64_t r = base + grp;
+    const bool has = r < n1;
+    int64_t b = 0, e = 0;
+    if (has) {
+      b = rowptr[r];
+      e = rowptr[r + 1];
+    }
+    R a0 = R(0), a1 = R(0), a2 = R(0);
+    for (int64_t c = b; c < e; c += 2 * kG) {
+      // up to four blocks per lane, all loads issued before the arithmetic
+      int64_t col[2];
+      bool ok[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const int nb = t == 0 ? nb0 : nb1;
-        if (j < nb) {
-          const int64_t blk = (t == 0 ? b0 : b1) + j;
-          const int64_t col = cols[blk];
-          const R* v = vals + blk * 9;
-          const R x0 = in[3 * col], x1 = in[3 * col + 1], x2 = in[3 * col + 2];
-          acc[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
-          acc[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
-          acc[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
-        }
+        const int64_t k = c + gl + t * kG;
+        ok[t] = k < e;
+        col[t] = ok[t] ? (int64_t)cols[k] : 0;
+      }
+      R v[2][9], x[2][3];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int64_t k = c + gl + t * kG;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[t][q] = ok[t] ? vals[k * 9 + q] : R(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) x[t][q] = ok[t] ? in[3 * col[t] + q] : R(0);
+      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        a0 += v[t][0] * x[t][0] + v[t][1] * x[t][1] + v[t][2] * x[t][2];
+        a1 += v[t][3] * x[t][0] + v[t][4] * x[t][1] + v[t][5] * x[t][2];
+        a2 += v[t][6] * x[t][0] + v[t][7] * x[t][1] + v[t][8] * x[t][2];
       }
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) acc[t][i] = warp_sum_r(acc[t][i]);
-    if (lane < 6) {
-      const int t = lane / 3, i = lane % 3;
-      if (t == 0 || has1) {
-        const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
-        const R o = t == 0 ? (i == 0 ? acc[0][0] : (i == 1 ? acc[0][1] : acc[0][2]))
-                           : (i == 0 ? acc[1][0] : (i == 1 ? acc[1][1] : acc[1][2]));
-        const R od = freem[d] ? o : R(0);
-        out[d] = od;
-        dot += (double)od * (double)w[d];
-      }
+    for (int o = kG / 2; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (has && gl < 3) {
+      const int64_t d = 3 * r + gl;
+      const R o = gl == 0 ? a0 : (gl == 1 ? a1 : a2);
+      const R od = freem[d] ? o : R(0);
+      out[d] = od;
+      dot += (double)od * (double)w[d];
     }
   }
   return dot;
@@ -516,9 +534,10 @@ __device__ __forceinline__ void precond_apply(const R* minv, int block3, int64_t
   }
 }
 
-// MINB = CTAs per SM the registers are budgeted for: 4 (64 registers) when the matrix stays
-// in L2 and the solve is latency-bound, 6 (40 registers, more warps in flight) when it
-// streams from HBM.
+// MINB = CTAs per SM the registers are budgeted for: 4 (64 registers) for FP32 blocks, 3 for
+// FP64 blocks (two double blocks per lane in flight).  With the eight-lanes-per-row SpMV
+// below, 4 is faster than 6 (40 registers, which spills) at every size measured, from the
+// 222k-dof plate to 3.09M dofs.
 template <typename R, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const PersistArgs<R> a) {
   const int64_t n0 = (int64_t)blockIdx.x * a.n_nodes / gridDim.x;
@@ -583,44 +602,58 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
   const int warp = threadIdx.x >> 5;
   constexpr int kWarps = kBlock / 32;
   while (!done && !breakdown && it < a.maxit) {
-    // q = K p with p = z + beta p_prev (rows without the Dirichlet columns: p is zero there)
+    // q = K p with p = z + beta p_prev (rows without the Dirichlet columns: p is zero there),
+    // eight lanes per block row as in spmv_range
     const R bt = (R)beta;
     double dot = 0.0;
-    for (int64_t r0 = n0 + warp; r0 < n1; r0 += 2 * kWarps) {
-      const int64_t r1 = r0 + kWarps;
-      const bool has1 = r1 < n1;
-      const int64_t b0 = a.rowptr[r0], e0 = a.rowptr[r0 + 1];
-      const int64_t b1 = has1 ? a.rowptr[r1] : 0, e1 = has1 ? a.rowptr[r1 + 1] : 0;
-      const int nb0 = (int)(e0 - b0), nb1 = (int)(e1 - b1);
-      R acc[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
-      const int nmax = nb0 > nb1 ? nb0 : nb1;
-      for (int j = lane; j < nmax; j += 32) {
+    {
+      constexpr int kG = 8;                  // lanes per block row
+      constexpr int kRows = 32 / kG;         // block rows per warp and pass
+      const int grp = lane / kG, gl = lane % kG;
+      for (int64_t base = n0 + (int64_t)warp * kRows; base < n1; base += (int64_t)kWarps * kRows) {
+        const int64_t r = base + grp;
+        const bool has = r < n1;
+        int64_t b = 0, e = 0;
+        if (has) {
+          b = a.rowptr[r];
+          e = a.rowptr[r + 1];
+        }
+        R a0 = R(0), a1 = R(0), a2 = R(0);
+        for (int64_t c = b; c < e; c += 2 * kG) {
+          int64_t col[2];
+          bool ok[2];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          const int nb = t == 0 ? nb0 : nb1;
-          if (j < nb) {
-            const int64_t blk = (t == 0 ? b0 : b1) + j;
-            const int64_t col = a.cols[blk];
-            const R* v = a.vals + blk * 9;
-            const R x0 = a.z[3 * col] + bt * pprev[3 * col];
-            const R x1 = a.z[3 * col + 1] + bt * pprev[3 * col + 1];
-            const R x2 = a.z[3 * col + 2] + bt * pprev[3 * col + 2];
-            acc[t][0] += v[0] * x0 + v[1] * x1 + v[2] * x2;
-            acc[t][1] += v[3] * x0 + v[4] * x1 + v[5] * x2;
-            acc[t][2] += v[6] * x0 + v[7] * x1 + v[8] * x2;
+          for (int t = 0; t < 2; ++t) {
+            const int64_t k = c + gl + t * kG;
+            ok[t] = k < e;
+            col[t] = ok[t] ? (int64_t)a.cols[k] : 0;
+          }
+          R v[2][9], x[2][3];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int64_t k = c + gl + t * kG;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v[t][q] = ok[t] ? a.vals[k * 9 + q] : R(0);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              x[t][q] = ok[t] ? a.z[3 * col[t] + q] + bt * pprev[3 * col[t] + q] : R(0);
+          }
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            a0 += v[t][0] * x[t][0] + v[t][1] * x[t][1] + v[t][2] * x[t][2];
+            a1 += v[t][3] * x[t][0] + v[t][4] * x[t][1] + v[t][5] * x[t][2];
+            a2 += v[t][6] * x[t][0] + v[t][7] * x[t][1] + v[t][8] * x[t][2];
           }
         }
-      }
 #pragma unroll
-      for (int t = 0; t < 2; ++t)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) acc[t][i] = warp_sum_r(acc[t][i]);
-      if (lane < 6) {
-        const int t = lane / 3, i = lane % 3;
-        if (t == 0 || has1) {
-          const int64_t d = 3 * (t == 0 ? r0 : r1) + i;
-          const R o = t == 0 ? (i == 0 ? acc[0][0] : (i == 1 ? acc[0][1] : acc[0][2]))
-                             : (i == 0 ? acc[1][0] : (i == 1 ? acc[1][1] : acc[1][2]));
+        for (int o = kG / 2; o > 0; o >>= 1) {
+          a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+          a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+          a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (has && gl < 3) {
+          const int64_t d = 3 * r + gl;
+          const R o = gl == 0 ? a0 : (gl == 1 ? a1 : a2);
           const R pd = a.z[d] + bt * pprev[d];
           const R qd = a.freem[d] ? o : R(0);
           pcur[d] = pd;
@@ -704,7 +737,7 @@ struct BicgArgs {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kBlock, 4) bicgstab_persistent_kernel(const BicgArgs<R> a) {
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 8 ? 3 : 4) bicgstab_persistent_kernel(const BicgArgs<R> a) {
   const int64_t n0 = (int64_t)blockIdx.x * a.n_nodes / gridDim.x;
   const int64_t n1 = (int64_t)(blockIdx.x + 1) * a.n_nodes / gridDim.x;
   PcgScalars* sc = a.sc;
@@ -891,10 +924,9 @@ template <typename R>
 cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
                            double* part, int64_t part_slots, cudaStream_t s, const R* x0) {
-  // matrix bytes (values + columns) against the 126 MB L2: resident -> latency-bound form
-  const bool streams = (double)K.n_blocks * (9.0 * sizeof(R) + 4.0) > 160e6;
-  const void* fn = streams ? (const void*)pcg_persistent_kernel<R, 6> : (const void*)pcg_persistent_kernel<R, 4>;
-  const int cap = streams ? 6 : 4;
+  constexpr int kMinb = sizeof(R) == 8 ? 3 : 4;   // FP64 blocks need the registers of 3 CTAs per SM
+  const void* fn = (const void*)pcg_persistent_kernel<R, kMinb>;
+  const int cap = kMinb;
   int dev = 0, n_sm = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -904,7 +936,7 @@ cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, Pc
   // buffers hold 2 x 2 doubles per CTA
   int64_t grid = (int64_t)n_sm * (per_sm < cap ? per_sm : cap);
   if (grid > part_slots / 4) grid = part_slots / 4;
-  const int64_t useful = (K.n_nodes + kBlock / 32 - 1) / (kBlock / 32);   // a warp per row at least
+  const int64_t useful = (K.n_nodes + kBlock / 8 - 1) / (kBlock / 8);   // an 8-lane group per row at least
   if (grid > useful) grid = useful;
   if (grid < 1) grid = 1;
   PersistArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.z, v.p, v.p2, v.q, x0,
@@ -926,7 +958,7 @@ cudaError_t bicgstab_persistent(const Csr& K, const R* vals, const uint8_t* free
   if (e != cudaSuccess) return e;
   int64_t grid = (int64_t)n_sm * (per_sm < 4 ? per_sm : 4);
   if (grid > part_slots / 4) grid = part_slots / 4;
-  const int64_t useful = (K.n_nodes + kBlock / 32 - 1) / (kBlock / 32);
+  const int64_t useful = (K.n_nodes + kBlock / 8 - 1) / (kBlock / 8);   // an 8-lane group per row at least
   if (grid > useful) grid = useful;
   if (grid < 1) grid = 1;
   BicgArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.rh, v.p, v.q, v.y, v.p2, v.z,
