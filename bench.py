@@ -40,7 +40,7 @@ LOAD = 0.5
 # FP32 flops per Gauss point of the tangent sweep counted from the formulation (kinematics
 # 0.6k, eigen-decomposition 0.5k, return mapping and recovery 0.7k, post-processor and
 # rotated gradients 0.4k, algorithmic tangent in the eigenbasis of C 1.7k, dP/dF 1.0k,
-# element contraction with the symmetric K^e 3.4k); see the design doc.
+# element contraction with the symmetric K^e 3.4k).
 ALG_FLOPS_PER_GP = 8.3e3
 # algorithmic DRAM bytes per element of a mixed tangent sweep (one node per element on a
 # large structured mesh): conn 32, nodal X (FP32) 12 and u (FP64) 24, history in and out

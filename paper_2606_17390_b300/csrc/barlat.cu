@@ -559,10 +559,10 @@ __device__ __forceinline__ void store_point(int64_t pt, const double y[8], int k
 
 // Persistent lane scheduling.  The grid holds as many threads as the GPU keeps resident;
 // warp w owns the points [n w / W, n (w + 1) / W).  Each lane works on one point at a time
-// for at most `chunk` Newton iterations per round; a lane whose point is finished takes the
+// for at most `chunk` Newton iterations per turn; a lane whose point is finished takes the
 // next unclaimed point of its warp (ranked by a ballot), so that the lanes of a warp are not
-// held by the slowest point of a fixed group.  A round ends at a Newton iterate (cpp_phase
-// returns kMaxit there when k reaches its bound), and the next round starts from that iterate
+// held by the slowest point of a fixed group.  A turn ends at a Newton iterate (cpp_phase
+// returns kMaxit there when k reaches its bound), and the next turn starts from that iterate
 // with the same state, so the result does not depend on `chunk`.
 struct LaneSched {
   int64_t cursor, hi;
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 5) barlat_fp32_kernel(BarlatDev prm,
   int64_t pt = -1;
   float yf[8], Tf[6], alf = 0.f, isf = 0.f;
   int k = 0, test = 0;
-  bool fresh = true;   // the lane's point has not started a round yet
+  bool fresh = true;   // the lane's point has not started a turn yet
   while (lane_claim(L, pt)) {
     if (pt < 0) continue;
     if (fresh) {
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 5) barlat_fp32_kernel(BarlatDev prm,
     const int k0 = k;
     const int r = cpp_phase<float>(P, yf, Tf, alf, isf, kTolSwitch, min(k + chunk, P.kmax), k, test);
     test = 0;
-    if (r == kMaxit && k < P.kmax && k > k0) continue;   // end of a round: the point goes on
+    if (r == kMaxit && k < P.kmax && k > k0) continue;   // end of a turn: the point goes on
     double y[8];
     int status;
     if (r == kConverged || r == kMaxit) {
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, MINB) barlat_fp64_kernel(BarlatDev p
   PointIn q;
   double y[8];
   int k = 0, kend_pt = 0, test = 0;
-  bool fresh = true;   // the lane's point has not started a round yet
+  bool fresh = true;   // the lane's point has not started a turn yet
   while (lane_claim(L, pt)) {
     if (pt < 0) continue;
     if (fresh) {
@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, MINB) barlat_fp64_kernel(BarlatDev p
     const int k0 = k;
     int status = cpp_phase<double>(P, y, q.Ttr, q.alpn, q.isref, P.tol, min(k + chunk, kend_pt), k, test);
     test = 0;
-    if (status == kMaxit && k < kend_pt && k > k0) continue;   // end of a round: the point goes on
+    if (status == kMaxit && k < kend_pt && k > k0) continue;   // end of a turn: the point goes on
     if (status == kElastic) {
 #pragma unroll
       for (int p = 0; p < 6; ++p) y[p] = q.Ttr[p];
@@ -959,7 +959,7 @@ hfe_status make_params(const hfe_barlat_material* mat, BarlatDev* P) {
   return HFE_OK;
 }
 
-constexpr int kChunk = 8;   // Newton iterations per round of the persistent kernels
+constexpr int kChunk = 8;   // Newton iterations per turn of the persistent kernels
 constexpr int kMaxDevices = 64;
 std::mutex g_occ_mutex;
 int g_occ32[kMaxDevices] = {}, g_occ64[kMaxDevices] = {}, g_occ64f[kMaxDevices] = {};
@@ -1056,7 +1056,7 @@ extern "C" hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, cons
   const bool mixed = P.precision == HFE_PRECISION_MIXED;
   int g32 = 0, g64 = 0, g64f = 0;
   if (resident_blocks(dev, &g32, &g64, &g64f) != cudaSuccess) return HFE_ECUDA;
-  // one point per lane while the batch fits in the resident threads; otherwise rounds of
+  // one point per lane while the batch fits in the resident threads; otherwise turns of
   // kChunk iterations with lane refill
   auto grid = [&](int resident) { return (unsigned)std::min<int64_t>(blocks, resident); };
   auto chunk = [&](int resident) { return blocks > resident ? kChunk : (1 << 30); };
