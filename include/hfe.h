@@ -137,8 +137,8 @@ typedef struct {
                              cutback^max_cutbacks (default 8: 1/256 of the interval) */
   int fbar;               /* 1: F-bar element (Sec. 2.2.4, Eq. Fbar): the constitutive model gets
                              Fbar = (Jbar/J)^(1/3) F, Jbar the element average of J; K is then
-                             non-symmetric and every Krylov solve is BiCGSTAB.  hfe_adjoint
-                             returns HFE_EINVAL for it.  0 (default): the standard element */
+                             non-symmetric and every Krylov solve is BiCGSTAB (hfe_adjoint solves
+                             with the transposed blocks).  0 (default): the standard element */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */

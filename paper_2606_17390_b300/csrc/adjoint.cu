@@ -3,7 +3,8 @@
 // states (u^n, h^n), R^n(u^n, h^{n-1}, theta) = 0 and h^n = H(u^n, h^{n-1}, theta).  With
 // mu^N = 0, for n = N..1:
 //   ubar   = dJ^n/du^n + (dH^n/du^n)^T mu^n                        (pass A)
-//   K_n^T lambda^n = -ubar   (free dofs; K_n is symmetric)          (FP64 CG)
+//   K_n^T lambda^n = -ubar   (free dofs; FP64 CG, K_n symmetric; with the F-bar element
+//                             K_n is not, and BiCGSTAB solves with its transposed blocks)
 //   mu^{n-1} = (dR^n/dh^{n-1})^T lambda^n + (dH^n/dh^{n-1})^T mu^n  (passes A and B)
 //   g += (dR^n/dtheta)^T lambda^n + (dH^n/dtheta)^T mu^n
 // All per-Gauss-point partials are vector-Jacobian products of (P, h_new) with respect to
@@ -58,6 +59,7 @@ struct VjpArgs {
   int64_t n_gp;
   int local_maxit;
   double local_tol;
+  int fbar;                  // F-bar element (Eq. Fbar)
 };
 
 // d sigma_y / d(h1, h2, h3) at alpha: Swift (K, eps0, n), Voce (sigma0, Q, b)
@@ -237,6 +239,39 @@ __global__ void __launch_bounds__(kAdjThreads) gp_vjp_kernel(VjpArgs a, int64_t 
         H[i][j] = s;
         F[i][j] = s + (i == j ? 1.0 : 0.0);
       }
+    // F-bar element (Eq. Fbar), as in the sweep: Jbar - 1 = sum_q det J0_q (J_q - 1) / V_e over
+    // the element's 8 threads, s = (Jbar / J)^(1/3), and the constitutive chain below runs on
+    // s F.  The standard F, J and the element sums are kept for the pull-back in pass A.
+    double F0[3][3], fb_s = 1.0, fb_jbar = 1.0, fb_j = 1.0, fb_det0 = det0, fb_vol = 1.0;
+    if (a.fbar) {
+      const double I1 = H[0][0] + H[1][1] + H[2][2];
+      const double I2 = H[0][0] * H[1][1] + H[1][1] * H[2][2] + H[0][0] * H[2][2] - H[0][1] * H[1][0] -
+                        H[1][2] * H[2][1] - H[0][2] * H[2][0];
+      const double I3 = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
+                        H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                        H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+      const double jm1 = I1 + I2 + I3;
+      double wj = det0 * jm1, wv = det0;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        wj += __shfl_xor_sync(gmask, wj, o);
+        wv += __shfl_xor_sync(gmask, wv, o);
+      }
+      const double jbm1 = wj / wv;
+      const double sm1 = expm1((log1p(jbm1) - log1p(jm1)) * (1.0 / 3.0));
+      fb_s = 1.0 + sm1;
+      fb_jbar = 1.0 + jbm1;
+      fb_j = 1.0 + jm1;
+      fb_vol = wv;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          F0[i][j] = F[i][j];
+          H[i][j] += sm1 * F[i][j];
+          F[i][j] *= fb_s;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -595,6 +630,34 @@ __global__ void __launch_bounds__(kAdjThreads) gp_vjp_kernel(VjpArgs a, int64_t 
     }
     if (PASS_A) a.hbar[6 * ng + gpi] = anbar;
     else a.hbar[6 * ng + gpi] += anbar;
+    if (PASS_A && a.fbar) {
+      // pull the cotangent of s F back to F (the element's 8 threads): with c_q = G_q : F_q,
+      // Fbar_q = s_q G_q - c_q s_q / (3 J_q) cof(F_q) + (sum_r c_r s_r) / (3 Jbar) det J0_q / V cof(F_q)
+      double cof[3][3];
+      cof[0][0] = F0[1][1] * F0[2][2] - F0[1][2] * F0[2][1];
+      cof[0][1] = F0[1][2] * F0[2][0] - F0[1][0] * F0[2][2];
+      cof[0][2] = F0[1][0] * F0[2][1] - F0[1][1] * F0[2][0];
+      cof[1][0] = F0[0][2] * F0[2][1] - F0[0][1] * F0[2][2];
+      cof[1][1] = F0[0][0] * F0[2][2] - F0[0][2] * F0[2][0];
+      cof[1][2] = F0[0][1] * F0[2][0] - F0[0][0] * F0[2][1];
+      cof[2][0] = F0[0][1] * F0[1][2] - F0[0][2] * F0[1][1];
+      cof[2][1] = F0[0][2] * F0[1][0] - F0[0][0] * F0[1][2];
+      cof[2][2] = F0[0][0] * F0[1][1] - F0[0][1] * F0[1][0];
+      double c = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c += Fbar[i][j] * F0[i][j];
+      const double cs = c * fb_s;
+      double sum = cs;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(gmask, sum, o);
+      const double k = -cs / (3.0 * fb_j) + sum / (3.0 * fb_jbar) * fb_det0 / fb_vol;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Fbar[i][j] = fb_s * Fbar[i][j] + k * cof[i][j];
+    }
     double* sg = sGp[le][g];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -640,6 +703,21 @@ __global__ void __launch_bounds__(kAdjThreads) gp_vjp_kernel(VjpArgs a, int64_t 
       a.thbar[(int64_t)e * 11 + q] += s;
     }
   }
+}
+
+// KT = K^T in the (structurally symmetric) block pattern: block (i, j) transposed goes to the
+// slot of block (j, i)
+__global__ void transpose_blocks_kernel(const double* __restrict__ K, const int64_t* __restrict__ tslot,
+                                        double* __restrict__ KT, int64_t n_blocks) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blocks) return;
+  const int64_t t = tslot[b];
+  const double* src = K + 9 * b;
+  double* dst = KT + 9 * t;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dst[3 * i + j] = src[3 * j + i];
 }
 
 // J^n = w ||u - ugt||^2 (all dofs) and rhs = -2 w (u - ugt) on free dofs; deterministic sum
@@ -703,6 +781,10 @@ struct AdjointWork {
   double *mu = nullptr, *hbar = nullptr, *thbar = nullptr, *ubar = nullptr, *rhs = nullptr, *R64 = nullptr;
   double *ugt = nullptr, *Jn = nullptr, *part = nullptr;
   unsigned* ticket = nullptr;
+  // F-bar element: K is not symmetric; K^T (values in the same block pattern) and the map
+  // from each block (i, j) to the slot of block (j, i)
+  double* KT = nullptr;
+  int64_t* tslot = nullptr;
   ~AdjointWork() {
     for (void* p : mem) cudaFree(p);
     if (ls.graph) cudaGraphExecDestroy(ls.graph);
@@ -902,6 +984,7 @@ void launch_vjp(hfe_handle* h, AdjointWork* w, bool pass_a, const double* u, con
   a.n_gp = h->n_gp;
   a.local_maxit = h->opt.local_maxit;
   a.local_tol = h->opt.local_tol;
+  a.fbar = h->opt.fbar != 0;
   const auto& off = h->P.color_off;
   for (size_t c = 0; c + 1 < off.size(); ++c) {
     const int64_t cnt = off[c + 1] - off[c];
@@ -914,13 +997,34 @@ void launch_vjp(hfe_handle* h, AdjointWork* w, bool pass_a, const double* u, con
 
 }  // namespace
 
+// The transpose map of the block pattern (host, once per work area) and room for K^T.
+hfe_status ensure_transpose(hfe_handle* h, AdjointWork* w) {
+  if (w->tslot != nullptr) return HFE_OK;
+  const Pattern& P = h->P;
+  std::vector<int64_t> ts((size_t)P.n_blocks, -1);
+  for (int64_t i = 0; i < h->n_nodes; ++i)
+    for (int64_t b = P.rowptr[i]; b < P.rowptr[i + 1]; ++b) {
+      const int64_t j = P.cols[b];
+      for (int64_t c = P.rowptr[j]; c < P.rowptr[j + 1]; ++c)
+        if (P.cols[c] == i) {
+          ts[b] = c;
+          break;
+        }
+      if (ts[b] < 0) return fail(h, HFE_EINVAL, "adjoint: the block pattern is not structurally symmetric");
+    }
+  HFE_TRY(aalloc(h, w, &w->tslot, (size_t)P.n_blocks));
+  HFE_TRY(aalloc(h, w, &w->KT, 9 * (size_t)P.n_blocks));
+  return cuda_check(h, cudaMemcpy(w->tslot, ts.data(), ts.size() * sizeof(int64_t), cudaMemcpyHostToDevice),
+                    "copy");
+}
+
 hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const double* u_target, double wgt,
                        double* J_out, double* grad_out, hfe_stats* stats) {
   auto w0 = std::chrono::steady_clock::now();
-  if (h->opt.fbar) return fail(h, HFE_EINVAL, "adjoint: the F-bar element has no adjoint here");
   std::vector<double> t(t_in, t_in + n_steps);
   HFE_TRY(ensure_work(h, n_steps));
   AdjointWork* w = h->adj;
+  if (h->opt.fbar) HFE_TRY(ensure_transpose(h, w));
   const size_t ndof = h->n_dof, ngp = h->n_gp;
   // forward pass from the zero state
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, ndof * sizeof(double), h->s), "memset"));
@@ -973,7 +1077,14 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
     HFE_TRY(read_status(h));
     HFE_TRY(check_sweep_status(h));
     h->allow_indefinite = true;   // K^T lambda = rhs (K symmetric; BiCGSTAB if indefinite)
+    void* Kn = w->ls.K;
+    if (h->opt.fbar) {            // F-bar: K is not symmetric, BiCGSTAB on the transposed blocks
+      const int64_t nb = h->P.n_blocks;
+      transpose_blocks_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, h->s>>>((const double*)Kn, w->tslot, w->KT, nb);
+      w->ls.K = w->KT;
+    }
     const hfe_status ast = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
+    w->ls.K = Kn;
     h->allow_indefinite = false;
     HFE_TRY(ast);
     adj_pcg += h->h_sc->iters;

@@ -2,7 +2,8 @@
 one tangent sweep on a distorted mesh with a mixed elastic/plastic state (residual, the
 non-symmetric tangent through the exported block-CSR, trial history), whole forward runs
 solved with BiCGSTAB (the homogeneous closed form, and a reduced perforated plate against the
-oracle's forward), and the adjoint refused."""
+oracle's forward), and the discrete adjoint (BiCGSTAB on the transposed tangent) against
+central differences of the oracle's F-bar forward solve."""
 import numpy as np
 import pytest
 
@@ -60,8 +61,50 @@ def test_fbar_forward_closed_form_and_plate(precision):
     assert infos[-1]["plastic"] > 0
     with hfe.from_inputs(mesh, bc, mat, precision=precision, fbar=1, **opts) as s:
         u, st = s.forward(ts)
-        with pytest.raises(hfe.HfeError) as e:
-            s.adjoint(ts, us)
-        assert e.value.status == -1
     for n in range(len(ts)):
         assert np.abs(u[n] - us[n]).max() < tol * np.abs(us[n]).max(), (n, np.abs(u[n] - us[n]).max())
+
+
+@pytest.fixture(scope="module")
+def fbar_fd_gradient():
+    """The rotated Voce problem of the adjoint tests with the F-bar element: target = the
+    oracle's F-bar forward at theta_true plus seeded noise; at theta = theta_true (1 + 0.1 U),
+    dJ/dtheta_q by central differences of J over the oracle's FP64 forward (h = 1e-6 |theta_q|)."""
+    mesh = inputs.box_mesh(4, 2, 1, 4.0, 2.0, 1.0)
+    bc = inputs.clamp_displace_bcs(mesh, (0.08, 0.02, 0.0))
+    mat = inputs.config1_material()
+    a = np.deg2rad(30.0)
+    mat.Theta = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1.0]])
+    ts = inputs.load_factors(4)
+    th_true = mat.theta_vector()
+    u_gt, _, infos = solver.forward(solver.from_inputs(mesh, bc, mat, th_true, fbar=True), ts, rtol=1e-13)
+    assert all(i["plastic"] > 0 for i in infos)
+    rng = np.random.default_rng(4)
+    u_gt = u_gt + 1e-3 * np.abs(u_gt).max() * rng.standard_normal(u_gt.shape)
+    th = th_true * (1 + 0.1 * rng.uniform(-1, 1, 11))
+
+    def J(t):
+        us, _, _ = solver.forward(solver.from_inputs(mesh, bc, mat, t, fbar=True), ts, rtol=1e-13)
+        return solver.objective(us, u_gt)
+
+    fd = np.empty(11)
+    for q in range(11):
+        e = np.zeros(11)
+        e[q] = 1e-6 * abs(th[q])
+        fd[q] = (J(th + e) - J(th - e)) / (2 * e[q])
+    return mesh, bc, mat, ts, u_gt, th, J(th), fd
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fbar_adjoint_vs_oracle_finite_differences(fbar_fd_gradient, precision):
+    mesh, bc, mat, ts, u_gt, th, Jo, fd = fbar_fd_gradient
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, theta=th, fbar=1, **opts) as s:
+        J, g, st = s.adjoint(ts, u_gt)
+    g = g[0]
+    assert abs(J - Jo) < 1e-8 * Jo
+    assert np.linalg.norm(g - fd) < 1e-6 * np.linalg.norm(fd), (g, fd)
+    # per component: central differences carry the forward's convergence noise (about 1e-13 J)
+    # divided by h, ~1e-12 absolute here, which is the floor for the smallest components
+    big = np.abs(fd) > 1e-3 * np.abs(fd).max()
+    assert np.all(np.abs(g[big] - fd[big]) < 1e-6 * np.abs(fd[big]) + 1e-7 * np.abs(fd).max()), (g, fd)
