@@ -102,6 +102,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the process group (x itself on one process): the job's
+    time is its slowest rank's.  Any backend (NCCL on GPUs, gloo on the host)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the (max-over-ranks) time."""
+    return world * units_per_rank / seconds
+
+
 def workload(n):
     mesh, bc, mat, _ = inputs.config2_problem(n=n)
     u, hist = inputs.compression_state(mesh, LOAD)
@@ -226,7 +242,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--n", type=int, default=100, help="cube edge in elements (100 = 3.09M dofs)")
+    ap.add_argument("--n", "--cube-n", dest="n", type=int, default=100,
+                    help="cube edge in elements (100 = 3.09M dofs); --cube-n is the same option under "
+                         "torch.distributed.run, whose own options make --n ambiguous")
     ap.add_argument("--fp64-steps", type=int, default=5, help="steps of the FP64 comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
@@ -291,18 +309,15 @@ def main():
             step(s)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         return ms
 
     with ClockSampler(local) as clk:
         ms_total = timed(solver, args.steps)
     ms_step = ms_total / args.steps
-    value = world * 8 * mesh.n_el / (ms_step * 1e-3)
+    value = whole_job_rate(world, 8 * mesh.n_el, ms_step * 1e-3)
 
     # the same sweep without the tangent and assembly (residual and history only), for context
     def step_res(s):
@@ -354,12 +369,8 @@ def main():
     for _ in range(k_e2e):
         solver.sweep(u_h, LOAD, tangent=True, R_out=R_h, rnorm_out=rn_h, stats=False)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / k_e2e
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * 8 * mesh.n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * mesh.n_dof,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e, dist, dev)
+    e2e = {"value": whole_job_rate(world, 8 * mesh.n_el, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 8 * mesh.n_dof,
            "d2h_bytes_per_step": 8 * mesh.n_dof + 8, "ms_per_step": 1e3 * e2e_s}
 
     # the linear solve of the Newton step on the same mesh: block-Jacobi PCG with the BSR SpMV
