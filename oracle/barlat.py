@@ -268,3 +268,76 @@ def cpp_tangent(model, E, nu, hardening, h, y, Ttr, alpn):
     rhs = np.zeros((y.shape[0], 8, 6))
     rhs[:, :6, :] = np.eye(6)
     return np.linalg.solve(J, rhs)[:, :6, :]
+
+
+# ------------------------------------------------------------------ strain-driven update
+def local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives=True, kmax=None):
+    """Stress update of Algorithm global_stress_update (App. C), steps 2-6, for this model,
+    from the total log strain: T_tr = E : (eps - eps_p,n), the elastic test (reading R10),
+    the projection `cpp`, and the recovery eps_p,n+1 = eps_p,n + dgamma N(T), T = E : (eps -
+    eps_p,n+1), alpha_n+1 (components, order 11,22,33,12,23,13).
+
+    Returns dict(z (B, 13) = (T, eps_p,n+1, alpha_n+1), dgamma, plastic, iters, converged, ftr)
+    and, if derivatives, dz (B, 13, 13) = dz/dp for p = (eps, eps_p,n, alpha_n) by implicit
+    differentiation of the converged local system (App. D)."""
+    from .material import LOCAL_KMAX
+    kmax = LOCAL_KMAX if kmax is None else kmax
+    eps = np.asarray(eps, dtype=np.float64)
+    epn = np.asarray(epn, dtype=np.float64)
+    alpn = np.asarray(alpn, dtype=np.float64)
+    B = eps.shape[0]
+    p_all = np.concatenate([eps, epn, alpn[:, None]], axis=1)        # (B, 13)
+
+    def ttr(pc):
+        return elastic(E, nu, pc[:, 0:6] - pc[:, 6:12])
+
+    def z_el(pc):
+        return np.concatenate([ttr(pc), pc[:, 6:12], pc[:, 12:13]], axis=1)
+
+    def z_of(yy, pc):
+        N, _ = model.flow(yy[:, :6])
+        epnew = pc[:, 6:12] + yy[:, 7:8] * N
+        return np.concatenate([elastic(E, nu, pc[:, 0:6] - epnew), epnew, yy[:, 6:7]], axis=1)
+
+    Ttr = ttr(p_all)
+    ftr = model.phi_poly(Ttr) - sigma_y(hardening, h, alpn)
+    plastic = ftr > 0.0
+    z = z_el(p_all)
+    dgam = np.zeros(B)
+    iters = np.zeros(B, dtype=np.int64)
+    conv = np.ones(B, dtype=bool)
+    P = np.nonzero(plastic)[0]
+    y = None
+    if P.size:
+        y, it, cv = cpp(model, E, nu, hardening, h, Ttr[P], alpn[P], kmax=kmax)
+        z[P] = z_of(y, p_all[P])
+        dgam[P] = y[:, 7]
+        iters[P] = it
+        conv[P] = cv
+    out = dict(z=z, dgamma=dgam, plastic=plastic, iters=iters, converged=conv, ftr=ftr)
+    if not derivatives:
+        return out
+    dz = np.empty((B, 13, 13))
+    Eidx = np.nonzero(~plastic)[0]
+    if Eidx.size:
+        dz[Eidx] = complex_step_jacobian(z_el, p_all[Eidx], 13)
+    if P.size:
+        pP = p_all[P]
+        Jy = complex_step_jacobian(
+            lambda yy: residual(model, E, nu, hardening, h, yy, ttr(pP), pP[:, 12]), y, 8)
+        Gp = complex_step_jacobian(
+            lambda pc: residual(model, E, nu, hardening, h, y.astype(pc.dtype), ttr(pc), pc[:, 12]), pP, 8)
+        ydot = -np.linalg.solve(Jy, Gp)                                 # (B, 8, 13)
+        zy = complex_step_jacobian(lambda yy: z_of(yy, pP), y, 13)
+        zp = complex_step_jacobian(lambda pc: z_of(y.astype(pc.dtype), pc), pP, 13)
+        dz[P] = zy @ ydot + zp
+    out["dz"] = dz
+    return out
+
+
+def local(model, E, nu, hardening, h, kmax=None):
+    """The update above as the callable (eps, epn, alpn, derivatives) that
+    material.gauss_point takes in place of the Hill-48 update."""
+    def f(eps, epn, alpn, derivatives=True):
+        return local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives, kmax)
+    return f

@@ -50,13 +50,16 @@ def gradients(Xe):
     return g, det * GP_W[None, :]
 
 
-def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tangent", fbar=False):
+def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tangent", fbar=False, local=None):
     """All elements at once.
 
     X (n_nodes,3), conn (n_el,8), u (n_dof,), hist (n_el,8,7) history at t_n,
     theta (11,) or (n_el,11), Theta None/(3,3)/(n_el,3,3).
     Returns Re (n_el,24), Ke (n_el,24,24) if jacobians, h_new (n_el,8,7), the Gauss-point
     dict of material.gauss_point (arrays flattened over (el, gp)), g and wdet.
+
+    local: another model's strain-driven update for material.gauss_point (e.g. barlat.local);
+    theta, hardening and Theta are then unused.
 
     fbar: the F-bar element of Sec. 2.2.4 (Eq. Fbar): the constitutive model receives
     Fbar = (Jbar / J)^(1/3) F with Jbar = (1/V_e) int_e J dV, the residual is
@@ -70,7 +73,7 @@ def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tan
     g, wdet = gradients(Xe)
     F = np.eye(3) + np.einsum("eai,egaj->egij", ue, g)  # F = I + sum_a u_a (x) g_a
     if fbar:
-        return _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_el)
+        return _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_el, local)
     theta = np.asarray(theta, dtype=np.float64)
     th = np.broadcast_to(theta if theta.ndim == 1 else theta[:, None, :], (n_el, 8, 11))
     if Theta is None:
@@ -80,7 +83,7 @@ def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tan
         Th = np.broadcast_to(Theta if Theta.ndim == 2 else Theta[:, None], (n_el, 8, 3, 3))
     gp = material.gauss_point(F.reshape(-1, 3, 3), hist[..., :6].reshape(-1, 6),
                               hist[..., 6].reshape(-1), th.reshape(-1, 11), hardening,
-                              Th.reshape(-1, 3, 3), jacobians=jacobians)
+                              Th.reshape(-1, 3, 3), jacobians=jacobians, local=local)
     P = gp["P"].reshape(n_el, 8, 3, 3)
     Re = np.einsum("eg,egiJ,egaJ->eai", wdet, P, g).reshape(n_el, 24)
     out = dict(Re=Re, h_new=gp["h_new"].reshape(n_el, 8, 7), gp=gp, g=g, wdet=wdet, F=F)
@@ -91,7 +94,7 @@ def element_sweep(X, conn, u, hist, theta, hardening, Theta=None, jacobians="tan
     return out
 
 
-def _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_el):
+def _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_el, local=None):
     J = np.linalg.det(F)                                          # (n_el, 8)
     Jbar = np.einsum("eg,eg->e", wdet, J) / wdet.sum(axis=1)      # volume average of J
     s = np.cbrt(Jbar[:, None] / J)                                # (Jbar / J)^(1/3)
@@ -105,7 +108,7 @@ def _element_sweep_fbar(F, g, wdet, hist, theta, hardening, Theta, jacobians, n_
         Th = np.broadcast_to(Theta if Theta.ndim == 2 else Theta[:, None], (n_el, 8, 3, 3))
     gp = material.gauss_point(Fb.reshape(-1, 3, 3), hist[..., :6].reshape(-1, 6),
                               hist[..., 6].reshape(-1), th.reshape(-1, 11), hardening,
-                              Th.reshape(-1, 3, 3), jacobians=jacobians)
+                              Th.reshape(-1, 3, 3), jacobians=jacobians, local=local)
     P = gp["P"].reshape(n_el, 8, 3, 3)                            # P(Fbar)
     Re = np.einsum("eg,egiJ,egaJ->eai", wdet, P, g).reshape(n_el, 24)
     out = dict(Re=Re, h_new=gp["h_new"].reshape(n_el, 8, 7), gp=gp, g=g, wdet=wdet, F=F, Fbar=Fb, Jbar=Jbar)

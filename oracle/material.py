@@ -384,13 +384,16 @@ def dk2(w, Q, X, Y):
 
 
 # ------------------------------------------------------------------ full Gauss point
-def gauss_point(F, epn, alpn, theta, hardening, Theta=None, jacobians="tangent"):
+def gauss_point(F, epn, alpn, theta, hardening, Theta=None, jacobians="tangent", local=None):
     """Algorithm global_stress_update (App. C) plus the first Piola-Kirchhoff tangent.
 
     F (B,3,3); epn (B,6); alpn (B,); theta (11,) or (B,11); Theta None, (3,3) or (B,3,3).
     jacobians: None (P and history only), "tangent" (also A = dP/dF), or "all" (also
     dP/dh_old, dP/dtheta, dh/dF, dh/dh_old, dh/dtheta for the adjoint).
-    History h = (eps_p (6), alpha).
+    History h = (eps_p (6), alpha).  local: None for the Hill-48 update, or another model's
+    strain-driven update (eps, epn, alpn, derivatives) -> dict(z, dz, ...) with dz over
+    (eps, eps_p,n, alpha_n) (e.g. barlat.local); theta, hardening and Theta are then unused
+    and jacobians "all" is not available.
     """
     F = np.asarray(F, dtype=np.float64)
     B = F.shape[0]
@@ -401,8 +404,13 @@ def gauss_point(F, epn, alpn, theta, hardening, Theta=None, jacobians="tangent")
     C = np.einsum("bki,bkj->bij", F, F)
     w, Q = eig_C(C)
     eps = vec6(log_strain(w, Q))
-    lu = local_update(eps, np.asarray(epn, float), np.asarray(alpn, float), theta, hardening,
-                      Theta, derivatives=jacobians is not None)
+    if local is None:
+        lu = local_update(eps, np.asarray(epn, float), np.asarray(alpn, float), theta, hardening,
+                          Theta, derivatives=jacobians is not None)
+    else:
+        if jacobians == "all":
+            raise NotImplementedError("parameter derivatives are available for the Hill-48 update only")
+        lu = local(eps, np.asarray(epn, float), np.asarray(alpn, float), derivatives=jacobians is not None)
     z = lu["z"]
     T = sym(z[:, :6])
     S = 2.0 * dk1(w, Q, T)                       # S = P_L : T   (Eq. proj_lagrange)

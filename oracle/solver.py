@@ -44,6 +44,7 @@ class Problem:
     Theta: np.ndarray | None = None
     f_ext: np.ndarray | None = None   # nodal dead load at t = 1 (n_dof,), optional
     fbar: bool = False                # F-bar element (Eq. Fbar); K is then non-symmetric
+    local: object = None              # another model's stress update (barlat.local); theta unused
 
     @property
     def n_dof(self):
@@ -87,7 +88,7 @@ def free_mask(prob):
 def residual(prob, u, hist, t=1.0, jacobians="tangent"):
     """R(u) = f_int(u; h_n) - t f_ext and, with jacobians, K = dR/du."""
     es = element.element_sweep(prob.X, prob.conn, u, hist, prob.theta, prob.hardening,
-                               prob.Theta, jacobians=jacobians, fbar=prob.fbar)
+                               prob.Theta, jacobians=jacobians, fbar=prob.fbar, local=prob.local)
     R = assemble_R(prob, es["Re"])
     if prob.f_ext is not None:
         R = R - t * prob.f_ext
@@ -189,6 +190,8 @@ def adjoint(prob, t_steps, us, hs, u_gt, w=1.0, per_element=False):
     """dJ/dtheta by the discrete adjoint; (11,) for uniform theta, (n_el, 11) if per_element."""
     if prob.fbar:
         raise NotImplementedError("the adjoint of the F-bar element is not part of the oracle")
+    if prob.local is not None:
+        raise NotImplementedError("the adjoint is written for the Hill-48 parameters")
     free = free_mask(prob)
     n_el = prob.n_el
     N = len(t_steps)
@@ -217,6 +220,8 @@ def direct_sensitivity(prob, t_steps, us, hs, u_gt, dtheta, w=1.0):
     """dJ/dtheta . dtheta by forward (tangent) propagation; dtheta (11,) or (n_el, 11)."""
     if prob.fbar:
         raise NotImplementedError("the sensitivity of the F-bar element is not part of the oracle")
+    if prob.local is not None:
+        raise NotImplementedError("the sensitivity is written for the Hill-48 parameters")
     free = free_mask(prob)
     n_el = prob.n_el
     dth = np.broadcast_to(np.asarray(dtheta, dtype=np.float64), (n_el, 11))

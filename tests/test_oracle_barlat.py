@@ -312,3 +312,79 @@ def test_orthotropic_projection_is_the_energy_minimiser():
                        options=dict(ftol=1e-16, maxiter=1000))
         assert np.abs(res.x - y[p, :6]).max() <= 2e-5 * np.abs(Ttr[p]).max()
         assert energy(y[p, :6], p) <= res.fun * (1 + 1e-9)
+
+
+# ------------------------------------------------------------ finite strain, element, forward
+def _hill_isotropic_swift():
+    """Hill-48 with F = G = H = 1/2, L = M = N = 3/2 (all r-ratios 1: von Mises), Swift."""
+    th = inputs.config0_material().theta_vector().copy()
+    th[2:8] = [0.5, 0.5, 0.5, 1.5, 1.5, 1.5]
+    return th
+
+
+def test_isotropic_barlat_gauss_point_equals_isotropic_hill():
+    """All 18 coefficients 1 with m = 2 and isotropic Hill-48 are both J2 plasticity with alpha
+    the equivalent plastic strain (W = 1 against sqrt(2/3) in both f and the alpha-rate), so
+    the finite-strain Gauss points (P, dP/dF, history) agree although the two local solvers,
+    their unknowns and their tangents are different code."""
+    from oracle import material as M
+    th = _hill_isotropic_swift()
+    E, nu, K, e0, n = th[0], th[1], th[8], th[9], th[10]
+    model = BA.Barlat(ONES, ONES, 2)
+    loc = BA.local(model, E, nu, "swift", (K, e0, n))
+    F = inputs.random_deformation_gradients(48, seed=201, scale=0.003)
+    ep, al = inputs.random_history(48, seed=202, eps_scale=0.0015, alpha_max=0.02)
+    gh = M.gauss_point(F, ep, al, th, "swift")
+    gb = M.gauss_point(F, ep, al, th, "swift", local=loc)
+    assert gh["plastic"].any() and (~gh["plastic"]).any()
+    assert np.array_equal(gh["plastic"], gb["plastic"])
+    sP = np.abs(gh["P"]).max()
+    assert np.abs(gb["P"] - gh["P"]).max() <= 1e-10 * sP
+    assert np.abs(gb["h_new"] - gh["h_new"]).max() <= 1e-11
+    assert np.abs(gb["A"] - gh["A"]).max() <= 1e-8 * np.abs(gh["A"]).max()
+
+
+def test_barlat_element_tangent_against_differences():
+    """The element stiffness with the Barlat update (paper parameters, rotated frame, plastic
+    state) against central differences of the element residual."""
+    from oracle import element
+    mat = inputs.barlat_verification_material()
+    mat.E, mat.h = 70000.0, (1.0, 0.0, 0.0)
+    model = BA.Barlat(mat.c1, mat.c2, mat.m, inputs.random_rotation(203))
+    loc = BA.local(model, mat.E, mat.nu, "voce", (1.0, 0.0, 0.0))
+    mesh = inputs.distorted_box_mesh(1, seed=204, amp=0.15)
+    rng = np.random.default_rng(205)
+    u = (mesh.X @ (4e-5 * rng.uniform(-1, 1, (3, 3))).T + 1e-5 * rng.uniform(-1, 1, mesh.X.shape)).ravel()
+    hist = np.zeros((1, 8, 7))
+    es = element.element_sweep(mesh.X, mesh.conn.astype(np.int64), u, hist, np.zeros(11), "voce", local=loc)
+    assert es["gp"]["plastic"].any()
+    Ke = es["Ke"][0]                               # element-local order (node a of conn, component)
+    gdof = (3 * mesh.conn[0][:, None] + np.arange(3)).ravel()
+    h = 1e-9
+    fd = np.empty((24, 24))
+    for j in range(24):
+        e = np.zeros(mesh.n_dof)
+        e[gdof[j]] = h
+        rp = element.element_sweep(mesh.X, mesh.conn.astype(np.int64), u + e, hist, np.zeros(11), "voce",
+                                   jacobians=None, local=loc)["Re"][0]
+        rm = element.element_sweep(mesh.X, mesh.conn.astype(np.int64), u - e, hist, np.zeros(11), "voce",
+                                   jacobians=None, local=loc)["Re"][0]
+        fd[:, j] = (rp - rm) / (2 * h)
+    assert np.abs(fd - Ke).max() <= 1e-6 * np.abs(Ke).max()
+
+
+def test_isotropic_barlat_forward_equals_isotropic_hill():
+    """The whole forward solve (config 0's cube, 4^3... here 2^3, 4 load steps) with the
+    isotropic Barlat update equals the isotropic Hill-48 solve."""
+    from oracle import solver
+    mesh, bc, mat, ts = inputs.config0_problem(n=2, n_steps=4)
+    th = _hill_isotropic_swift()
+    E, nu, K, e0, n = th[0], th[1], th[8], th[9], th[10]
+    ph = solver.from_inputs(mesh, bc, mat, th)
+    pb = solver.from_inputs(mesh, bc, mat, th)
+    pb.local = BA.local(BA.Barlat(ONES, ONES, 2), E, nu, "swift", (K, e0, n))
+    uh, hh, ih = solver.forward(ph, ts, rtol=1e-12)
+    ub, hb, ib = solver.forward(pb, ts, rtol=1e-12)
+    assert sum(i["plastic"] for i in ih) > 0
+    assert np.abs(ub - uh).max() <= 1e-10 * np.abs(uh).max()
+    assert np.abs(np.asarray(hb) - np.asarray(hh)).max() <= 1e-10
