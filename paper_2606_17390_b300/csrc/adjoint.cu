@@ -1021,6 +1021,7 @@ hfe_status ensure_transpose(hfe_handle* h, AdjointWork* w) {
 hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const double* u_target, double wgt,
                        double* J_out, double* grad_out, hfe_stats* stats) {
   auto w0 = std::chrono::steady_clock::now();
+  if (h->barlat != nullptr) return fail(h, HFE_EINVAL, "adjoint: the Hill-48 parameters only (Barlat material set)");
   std::vector<double> t(t_in, t_in + n_steps);
   HFE_TRY(ensure_work(h, n_steps));
   AdjointWork* w = h->adj;

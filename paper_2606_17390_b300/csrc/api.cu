@@ -167,7 +167,18 @@ hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, d
   a.local_maxit = h->opt.local_maxit;
   a.local_tol = h->opt.local_tol;
   a.fbar = h->opt.fbar;
+  a.ext_eps = h->ext_eps;
+  a.ext_T = h->ext_T;
+  a.ext_D = h->ext_D;
+  a.ext_plastic = h->ext_pl;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->s), "memset"));
+  if (h->barlat != nullptr) {   // Barlat: strain pass, the Gauss-point update, assembly pass
+    launch_gp_sweep_ext(a, 1, mode, h->P.color_off, h->s);
+    launch_barlat_gp(h->barlat, h->ext_eps, (const double*)hist, (double*)hist_trial, h->n_gp, h->ext_T, h->ext_D,
+                     h->ext_pl, mode == HFE_SWEEP_TANGENT ? 1 : 0, h->status, h->s);
+    launch_gp_sweep_ext(a, 2, mode, h->P.color_off, h->s);
+    return HFE_OK;
+  }
   launch_gp_sweep(a, fp64, mode, h->P.color_off, h->s);
   return HFE_OK;
 }
@@ -584,6 +595,7 @@ void hfe_destroy(hfe_handle* h) {
   if (h == nullptr) return;
   if (h->s) cudaStreamSynchronize(h->s);
   adjoint_free(h->adj);
+  hfe::barlat_model_free(h->barlat);
   if (h->ls.graph) cudaGraphExecDestroy(h->ls.graph);
   for (void* p : h->allocs) cudaFree(p);
   if (h->sigma) cudaFree(h->sigma);
@@ -599,6 +611,37 @@ void hfe_destroy(hfe_handle* h) {
 }
 
 const char* hfe_last_error(const hfe_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const hfe_cpp_options* opt) {
+  if (h == nullptr) return HFE_EINVAL;
+  if (mat == nullptr) {   // back to the Hill-48 material of the handle
+    hfe::barlat_model_free(h->barlat);
+    h->barlat = nullptr;
+    h->pred_valid = false;
+    return HFE_OK;
+  }
+  if (!h->fp64) return fail(h, HFE_EINVAL, "Barlat material: FP64 handles only");
+  if (h->n_mat != 1) return fail(h, HFE_EINVAL, "Barlat material: the handle's material must be uniform");
+  if (h->opt.fbar) return fail(h, HFE_EINVAL, "Barlat material: the standard element only");
+  hfe_status st = HFE_OK;
+  hfe::BarlatModel* m = hfe::barlat_model_new(mat, opt, &st);
+  if (m == nullptr) return fail(h, st, "Barlat material: invalid parameters or options");
+  if (h->ext_eps == nullptr) {
+    const size_t ng = (size_t)h->n_gp;
+    hfe_status a = dalloc(h, &h->ext_eps, 6 * ng);
+    if (a == HFE_OK) a = dalloc(h, &h->ext_T, 6 * ng);
+    if (a == HFE_OK) a = dalloc(h, &h->ext_D, 36 * ng);
+    if (a == HFE_OK) a = dalloc(h, &h->ext_pl, ng);
+    if (a != HFE_OK) {
+      hfe::barlat_model_free(m);
+      return a;
+    }
+  }
+  hfe::barlat_model_free(h->barlat);
+  h->barlat = m;
+  h->pred_valid = false;
+  return HFE_OK;
+}
 
 hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info) {
   if (h == nullptr || info == nullptr) return HFE_EINVAL;

@@ -37,6 +37,7 @@
 
 #include "gp_math.cuh"
 #include "hfe.h"
+#include "hfe_internal.h"
 
 namespace {
 
@@ -738,8 +739,47 @@ __global__ void __launch_bounds__(kThreads, MINB) barlat_fp64_kernel(BarlatDev p
   }
 }
 
-// dT/dT_tr (App. D) at the returned state, in FP64: J z = [e_c; 0; 0] for each component c;
-// the identity for elastic and failed points.
+// dT/dT_tr (App. D) at the state y, in FP64: J z = [e_c; 0; 0] for each component c (a shear
+// component moving both symmetric entries).  Also returns N = dphi/dT (tensor components) at
+// y.  False if phi = 0 or the system is singular.
+__device__ __forceinline__ bool cpp_tangent(const BarlatDev& P, const double y[8], const double Ttr[6], double alpn,
+                                            double Tg[6][6], double N[6]) {
+  double G[8], dphi[6];
+  Spec<double> s;
+  if (!residual<double>(P, y, Ttr, alpn, G, s, dphi)) return false;
+  double H[6][6], A6[6][6], X[6][7], EN[6];
+  phi_hessian<double>(P, s, dphi, H);
+  build_A6<double>(P, H, y[7], A6);
+#pragma unroll
+  for (int p = 0; p < 6; ++p) N[p] = dphi[p] / kWf<double>(p);
+  elastic<double>(P, N, EN);
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) X[p][c] = (p == c) ? 1.0 : 0.0;
+    X[p][6] = EN[p];
+  }
+  double hs;
+  sigma_y<double>(P, y[6], &hs);
+  if (!lu_solve6<double, 7>(A6, X)) return false;
+  double nx2 = 0.0;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) nx2 += dphi[p] * X[p][6];
+  const double den = nx2 + hs;
+  if (!(den != 0.0 && isfinite(den))) return false;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    double nz = 0.0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) nz += dphi[p] * X[p][c];
+    const double zg = nz / den;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Tg[a][c] = X[a][c] - X[a][6] * zg;
+  }
+  return true;
+}
+
+// dT/dT_tr at the returned state; the identity for elastic and failed points.
 __global__ void __launch_bounds__(kThreads) barlat_tangent_kernel(BarlatDev prm, const double* __restrict__ Ttr_g,
                                                                   const double* __restrict__ alpn_g, int64_t n,
                                                                   const double* __restrict__ T_out,
@@ -758,46 +798,12 @@ __global__ void __launch_bounds__(kThreads) barlat_tangent_kernel(BarlatDev prm,
   if (okt) {
     PointIn q;
     load_point(P, Ttr_g, alpn_g, pt, q);
-    double y[8], G[8], dphi[6];
+    double y[8], N[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p) y[p] = T_out[pt * 6 + p];
     y[6] = alpha_out[pt];
     y[7] = dg_out[pt];
-    Spec<double> s;
-    okt = residual<double>(P, y, q.Ttr, q.alpn, G, s, dphi);
-    if (okt) {
-      double H[6][6], A6[6][6], X[6][7], EN[6], N[6];
-      phi_hessian<double>(P, s, dphi, H);
-      build_A6<double>(P, H, y[7], A6);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) N[p] = dphi[p] / kWf<double>(p);
-      elastic<double>(P, N, EN);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) X[p][c] = (p == c) ? 1.0 : 0.0;
-        X[p][6] = EN[p];
-      }
-      double hs;
-      sigma_y<double>(P, y[6], &hs);
-      okt = lu_solve6<double, 7>(A6, X);
-      double nx2 = 0.0;
-#pragma unroll
-      for (int p = 0; p < 6; ++p) nx2 += dphi[p] * X[p][6];
-      const double den = nx2 + hs;
-      okt = okt && den != 0.0 && isfinite(den);
-      if (okt) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          double nz = 0.0;
-#pragma unroll
-          for (int p = 0; p < 6; ++p) nz += dphi[p] * X[p][c];
-          const double zg = nz / den;
-#pragma unroll
-          for (int a = 0; a < 6; ++a) Tg[a][c] = X[a][c] - X[a][6] * zg;
-        }
-      }
-    }
+    okt = cpp_tangent(P, y, q.Ttr, q.alpn, Tg, N);
   }
   if (!okt) {
 #pragma unroll
@@ -809,6 +815,122 @@ __global__ void __launch_bounds__(kThreads) barlat_tangent_kernel(BarlatDev prm,
   for (int a = 0; a < 6; ++a)
 #pragma unroll
     for (int c = 0; c < 6; ++c) tan_out[pt * 36 + a * 6 + c] = Tg[a][c];
+}
+
+// The strain-driven update of a hex8 sweep's Gauss points (App. C, Algorithm
+// global_stress_update steps 2-6, FP64): from the Mandel log strain and the FP64 history
+// [8][n_gp] (eps_p tensor components, alpha, sigma_y cache), T_tr = E : (eps - eps_p,n), the
+// elastic test, the projection, the recovery eps_p,n+1 = eps_p,n + dgamma N(T),
+// T = E : (eps - eps_p,n+1); out: the trial history, the Mandel stress, the plastic flag and
+// (tangent != 0) D = dT/deps = (dT/dT_tr) E in Mandel form.  Non-converged projections are
+// counted in status->local_fail.
+__global__ void __launch_bounds__(kThreads) barlat_gp_kernel(BarlatDev prm, const double* __restrict__ eps_M,
+                                                             const double* __restrict__ hist,
+                                                             double* __restrict__ hist_trial, int64_t ng,
+                                                             double* __restrict__ T_M, double* __restrict__ D_M,
+                                                             uint8_t* __restrict__ pl, int tangent,
+                                                             hfe::DevStatus* __restrict__ status) {
+  __shared__ BarlatDev P;
+  if (threadIdx.x == 0) P = prm;
+  __syncthreads();
+  const int64_t pt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (pt >= ng) return;
+  constexpr double kISq2d = 0.70710678118654752440, kSq2d = 1.41421356237309504880;
+  double eps[6], epn[6], Ttr[6], ee[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    eps[p] = eps_M[pt * 6 + p] * (p < 3 ? 1.0 : kISq2d);
+    epn[p] = hist[p * ng + pt];
+    ee[p] = eps[p] - epn[p];
+  }
+  const double alpn = hist[6 * ng + pt];
+  elastic<double>(P, ee, Ttr);
+  double ds0;
+  double sref = sigma_y<double>(P, alpn, &ds0);
+  {
+    double nt = 0.0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) nt = fma(Ttr[p], Ttr[p], nt);
+    sref = fmax(sref, sqrt(nt));
+  }
+  double y[8];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) y[p] = Ttr[p];
+  y[6] = alpn;
+  y[7] = 0.0;
+  int k = 0;
+  const int st = cpp_phase<double>(P, y, Ttr, alpn, 1.0 / sref, P.tol, P.kmax, k, 1);
+  double T[6], epnew[6], alpha = alpn, Dc[6][6];
+  bool plastic = false;
+  if (st == kElastic) {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      T[p] = Ttr[p];
+      epnew[p] = epn[p];
+    }
+  } else {
+    plastic = true;
+    if (st != kConverged) atomicAdd(&status->local_fail, 1);
+    double Tg[6][6], N[6];
+    bool ok = cpp_tangent(P, y, Ttr, alpn, Tg, N);
+    if (!ok) {
+      atomicAdd(&status->nonfinite, 1);
+#pragma unroll
+      for (int p = 0; p < 6; ++p) N[p] = 0.0;
+    }
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      epnew[p] = epn[p] + y[7] * N[p];
+      ee[p] = eps[p] - epnew[p];
+    }
+    elastic<double>(P, ee, T);
+    alpha = y[6];
+    if (tangent) {
+      // D = Tg E: column q of E is E applied to the unit component q
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double eq[6], Eq[6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) eq[p] = (p == q) ? 1.0 : 0.0;
+        elastic<double>(P, eq, Eq);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          double v = 0.0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) v += (ok ? Tg[a][c] : (a == c ? 1.0 : 0.0)) * Eq[c];
+          Dc[a][q] = v;
+        }
+      }
+    }
+  }
+  if (tangent && !plastic) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      double eq[6], Eq[6];
+#pragma unroll
+      for (int p = 0; p < 6; ++p) eq[p] = (p == q) ? 1.0 : 0.0;
+      elastic<double>(P, eq, Eq);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) Dc[a][q] = Eq[a];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    T_M[pt * 6 + p] = T[p] * (p < 3 ? 1.0 : kSq2d);
+    hist_trial[p * ng + pt] = epnew[p];
+  }
+  hist_trial[6 * ng + pt] = alpha;
+  double dsy;
+  hist_trial[7 * ng + pt] = sigma_y<double>(P, alpha, &dsy);
+  pl[pt] = plastic ? 1 : 0;
+  if (tangent) {
+    // Mandel: D_M[p][q] = s_p Dc[p][q] / s_q, s = (1, 1, 1, sqrt2, sqrt2, sqrt2)
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        D_M[pt * 36 + a * 6 + q] = Dc[a][q] * (a < 3 ? 1.0 : kSq2d) * (q < 3 ? 1.0 : kISq2d);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) barlat_phi_kernel(BarlatDev prm, const double* __restrict__ T_g,
@@ -986,7 +1108,56 @@ cudaError_t resident_blocks(int dev, int* g32, int* g64, int* g64f) {
   return cudaSuccess;
 }
 
+hfe_status apply_options(const hfe_cpp_options* opt, BarlatDev* P) {
+  hfe_cpp_options o;
+  if (opt != nullptr) o = *opt;
+  else hfe_default_cpp_options(&o);
+  if (o.kmax < 0 || o.kmax > 100000 || o.jmax < 0 || o.jmax > 1000) return HFE_EINVAL;
+  if (!(o.beta > 0.0 && o.beta < 0.5) || !(o.eta > 0.0 && o.eta < 1.0) || !(o.tol > 0.0)) return HFE_EINVAL;
+  if (o.precision != HFE_PRECISION_FP64 && o.precision != HFE_PRECISION_MIXED) return HFE_EINVAL;
+  P->kmax = o.kmax;
+  P->jmax = o.jmax;
+  P->line_search = o.line_search != 0;
+  P->precision = o.precision;
+  P->sd.beta = o.beta;
+  P->sd.eta = o.eta;
+  P->tol = o.tol;
+  P->sf = Scal<float>{(float)P->sd.lam, (float)P->sd.mu, (float)P->sd.h0, (float)P->sd.h1,
+                      (float)P->sd.h2, (float)P->sd.beta, (float)P->sd.eta};
+  return HFE_OK;
+}
+
 }  // namespace
+
+// ---- the Barlat material of a hex8 handle (internal interface, hfe_internal.h)
+namespace hfe {
+struct BarlatModel {
+  BarlatDev P;
+};
+
+BarlatModel* barlat_model_new(const hfe_barlat_material* mat, const hfe_cpp_options* opt, hfe_status* st) {
+  BarlatModel* m = new BarlatModel();
+  *st = make_params(mat, &m->P);
+  if (*st == HFE_OK) *st = apply_options(opt, &m->P);
+  if (*st != HFE_OK) {
+    delete m;
+    return nullptr;
+  }
+  m->P.precision = HFE_PRECISION_FP64;
+  return m;
+}
+
+void barlat_model_free(BarlatModel* m) { delete m; }
+
+void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* hist, double* hist_trial,
+                      int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent, DevStatus* status,
+                      cudaStream_t s) {
+  const unsigned blocks = (unsigned)((n_gp + kThreads - 1) / kThreads);
+  if (blocks > 0)
+    barlat_gp_kernel<<<blocks, kThreads, 0, s>>>(m->P, eps_M, hist, hist_trial, n_gp, T_M, D_M, plastic, tangent,
+                                                 status);
+}
+}  // namespace hfe
 
 extern "C" void hfe_default_cpp_options(hfe_cpp_options* o) {
   if (o == nullptr) return;
@@ -1026,21 +1197,8 @@ extern "C" hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, cons
   BarlatDev P{};
   hfe_status st = make_params(mat, &P);
   if (st != HFE_OK) return st;
-  hfe_cpp_options o;
-  if (opt != nullptr) o = *opt;
-  else hfe_default_cpp_options(&o);
-  if (o.kmax < 0 || o.kmax > 100000 || o.jmax < 0 || o.jmax > 1000) return HFE_EINVAL;
-  if (!(o.beta > 0.0 && o.beta < 0.5) || !(o.eta > 0.0 && o.eta < 1.0) || !(o.tol > 0.0)) return HFE_EINVAL;
-  if (o.precision != HFE_PRECISION_FP64 && o.precision != HFE_PRECISION_MIXED) return HFE_EINVAL;
-  P.kmax = o.kmax;
-  P.jmax = o.jmax;
-  P.line_search = o.line_search != 0;
-  P.precision = o.precision;
-  P.sd.beta = o.beta;
-  P.sd.eta = o.eta;
-  P.tol = o.tol;
-  P.sf = Scal<float>{(float)P.sd.lam, (float)P.sd.mu, (float)P.sd.h0, (float)P.sd.h1,
-                     (float)P.sd.h2, (float)P.sd.beta, (float)P.sd.eta};
+  st = apply_options(opt, &P);
+  if (st != HFE_OK) return st;
   if (n < 0) return HFE_EINVAL;
   if (n == 0) return HFE_OK;
   if (!T_trial || !alpha_n || !T_out || !alpha_out || !dgamma_out || !iters_out || !status_out) return HFE_EINVAL;

@@ -45,6 +45,11 @@ struct hfe_handle {
   int64_t n_nodes = 0, n_el = 0, n_dof = 0, n_gp = 0, n_fixed = 0, n_mat = 1;
   int hardening = 0;
   Pattern P;
+  // Barlat Yld2004-18p material (hfe_set_barlat; FP64 handles): the model and the per-Gauss-
+  // point exchange buffers of its sweep (Mandel strain, stress, tangent, plastic flag)
+  hfe::BarlatModel* barlat = nullptr;
+  double *ext_eps = nullptr, *ext_T = nullptr, *ext_D = nullptr;
+  uint8_t* ext_pl = nullptr;
   // device buffers
   double* X = nullptr;
   int32_t* conn = nullptr;

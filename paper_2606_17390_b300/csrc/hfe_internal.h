@@ -78,6 +78,12 @@ struct SweepArgs {
   int local_maxit;
   double local_tol;
   int fbar;                // F-bar element (Eq. Fbar)
+  // external material model (FP64, uniform material, standard element): the strain pass
+  // writes ext_eps; the assembly pass reads ext_T, ext_D and ext_plastic
+  double* ext_eps;         // [n_gp*6] Mandel log strain
+  const double* ext_T;     // [n_gp*6] Mandel stress
+  const double* ext_D;     // [n_gp*36] Mandel dT/deps, row-major
+  const uint8_t* ext_plastic;   // [n_gp]
 };
 
 void launch_material_setup(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,
@@ -85,6 +91,18 @@ void launch_material_setup(const double* theta, const double* Theta, int64_t n_m
 // mode: HFE_SWEEP_RESIDUAL / HFE_SWEEP_TANGENT; fp64 selects the plain FP64 kernel.
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
                      cudaStream_t s);
+// The Barlat Yld2004-18p material of a handle (barlat.cu): parameters and local controls,
+// and the strain-driven update of every Gauss point between the two external sweep passes.
+struct BarlatModel;
+BarlatModel* barlat_model_new(const hfe_barlat_material* mat, const hfe_cpp_options* opt, hfe_status* st);
+void barlat_model_free(BarlatModel* m);
+void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* hist, double* hist_trial,
+                      int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent, DevStatus* status,
+                      cudaStream_t s);
+// External material model, FP64: pass 1 = strain pass (ext_eps out), pass 2 = assembly with
+// ext_T / ext_D / ext_plastic (mode HFE_SWEEP_RESIDUAL or HFE_SWEEP_TANGENT).
+void launch_gp_sweep_ext(const SweepArgs& a, int pass, int mode, const std::vector<int64_t>& color_off,
+                         cudaStream_t s);
 void launch_sigma_cache(void* hist, bool fp64, const MatRec* mat, int mat_per_element, int hardening,
                         int64_t n_gp, cudaStream_t s);
 // user layout double [7][n_gp] <-> internal layout (the cache is not touched)

@@ -186,7 +186,10 @@ template <> struct MatOf<double> { using T = MatRec; };
 // ----------------------------------------------------------------------------------------
 // UNIF: one material for all elements, passed by value so that its entries are kernel-
 // parameter (constant-bank) operands rather than loads.
-template <typename R, bool TANGENT, bool UNIF, bool FBAR>
+// MAT: 0 the Hill-48 update in the kernel; 1 the strain pass of an external material model
+// (the Mandel log strain of every Gauss point out, nothing assembled); 2 the external model's
+// stress, plastic flag and tangent dT/deps in (S4 and S5 replaced, S6-S8 as for Hill).
+template <typename R, bool TANGENT, bool UNIF, bool FBAR, int MAT = 0>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     gp_sweep_kernel(SweepArgs a, const typename MatOf<R>::T mrec, int64_t cbeg, int64_t ccount) {
   constexpr int kGpStride = Lay<FBAR>::kGpStride;
@@ -419,10 +422,32 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       epsM[p] = (i == j) ? s : R(kSq2) * s;
     }
 
+    if constexpr (MAT == 1) {
+      // strain pass of an external material: the Mandel log strain out, nothing else
+#pragma unroll
+      for (int p = 0; p < 6; ++p) a.ext_eps[gpi * 6 + p] = (double)epsM[p];
+    } else {
     // ---- S4 elastic predictor (Eq. Tr_stress) and return mapping in the Hill eigenbasis
     const double alpn = (double)alpn_r;
     const MR& m = UNIF ? mrec : matR[mi];
     const R lam = m.lam, mu = m.mu;
+    bool plastic = false;
+    RM rm;
+    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0;
+    R Teig[6];
+    R s_pl = R(0), phy = R(1);
+    R TM[6];
+    if constexpr (MAT == 2) {
+      // external material (its own kernel ran S4 and wrote the trial history): the Mandel
+      // stress and the plastic flag of this Gauss point
+#pragma unroll
+      for (int p = 0; p < 6; ++p) TM[p] = (R)a.ext_T[gpi * 6 + p];
+      plastic = a.ext_plastic[gpi] != 0;
+      flag_plastic = plastic ? 1 : 0;
+#pragma unroll
+      for (int p = 0; p < 6; ++p) Teig[p] = R(0);
+      (void)alpn;
+    } else {
     R ee[6];
 #pragma unroll
     for (int p = 0; p < 6; ++p) ee[p] = epsM[p] - (p < 3 ? epn[p] : R(kSq2) * epn[p]);
@@ -438,9 +463,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       for (int i = 0; i < 6; ++i) s += m.QH[i * 6 + j] * Ttr[i];
       t[j] = s;
     }
-    bool plastic = false;
-    RM rm;
-    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0;
     double syn64;
     if constexpr (sizeof(R) == 8) {
       const MR& m64 = m;
@@ -511,8 +533,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     local_iters = rm.iters;
 
     // stress T and plastic update in the Hill eigenbasis, then back to Mandel components
-    R Teig[6];
-    R s_pl = R(0), phy = R(1);
     if (plastic) {
       phy = (R)(kSq23 * rm.syn1);
       s_pl = Num<R>::div(R(2) * mu * (R)rm.dgamma, phy);
@@ -520,7 +540,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     Teig[0] = t[0];
 #pragma unroll
     for (int i = 1; i < 6; ++i) Teig[i] = plastic ? Num<R>::div(t[i], R(1) + s_pl * (R)m.h[i]) : t[i];
-    R TM[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       R s = R(0);
@@ -551,6 +570,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       }
       Hist<R>::cache(hb, ng)[gpi] = rm.syn1;
     }
+    }   // MAT == 0
 
     // ---- S6 post-processor in the eigenbasis of C: That = Q^T T Q, Shat_ab = 2 f1_ab That_ab
     R Tt[3][3];
@@ -636,7 +656,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       R Dh[6][6];
       R Rq[6][6];
       mandel_rotation<R>(Q, Rq);
-      if (!plastic) {
+      if constexpr (MAT == 2) {
+        // external material: D = dT/deps (Mandel) from its kernel, rotated, Dh = Rq D Rq^T
+        R RD[6][6];
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            R v = R(0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v += Rq[p][k] * (R)a.ext_D[gpi * 36 + k * 6 + q];
+            RD[p][q] = v;
+          }
+#pragma unroll
+        for (int p = 0; p < 6; ++p)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            R v = R(0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v += RD[p][k] * Rq[q][k];
+            Dh[p][q] = v;
+          }
+      } else if (!plastic) {
 #pragma unroll
         for (int p = 0; p < 6; ++p)
 #pragma unroll
@@ -772,6 +813,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
 #pragma unroll
       for (int k = 0; k < 12; ++k) V4<R>::st(gp + 4 * k, av[4 * k], av[4 * k + 1], av[4 * k + 2], av[4 * k + 3]);
     }
+    }   // MAT != 1
   }
 
   // ---- status counters (one atomic per warp and counter)
@@ -793,6 +835,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   // 8 threads, all in one warp: a warp barrier suffices, and warps move on independently
   cp_async_wait_all();
   __syncwarp();
+  if constexpr (MAT == 1) return;   // the strain pass assembles nothing
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
   if (!valid) return;
@@ -1126,14 +1169,14 @@ void launch_hist_export(const void* hist, double* user, bool fp64, int64_t n_gp,
   else hist_export_kernel<float><<<blocks, threads, 0, s>>>(hist, user, n_gp);
 }
 
-template <typename R, bool TANGENT, bool UNIF, bool FBAR>
+template <typename R, bool TANGENT, bool UNIF, bool FBAR, int MAT = 0>
 static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cudaStream_t s) {
   using MR = typename MatOf<R>::T;
   const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * Lay<FBAR>::kElStride) +
                      sizeof(int32_t) * kElemsPerCta * 64;
   // the dynamic shared-memory limit is a per-device function attribute: set it on every call
   // (a host-side call, no synchronisation) so that each device the handle runs on has it
-  cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF, FBAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   MR rec;
   if (UNIF) memcpy(&rec, a.mat_host, sizeof(MR));   // host copy of the single record
@@ -1142,7 +1185,7 @@ static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cu
     int64_t cnt = off[c + 1] - off[c];
     if (cnt <= 0) continue;
     unsigned blocks = (unsigned)((cnt + kElemsPerCta - 1) / kElemsPerCta);
-    gp_sweep_kernel<R, TANGENT, UNIF, FBAR><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
+    gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
   }
 }
 
@@ -1151,6 +1194,13 @@ static void launch_mode(const SweepArgs& a, int mode, const std::vector<int64_t>
   const bool u = a.mat_host != nullptr;
   if (mode == HFE_SWEEP_TANGENT) u ? launch_typed<R, true, true, FBAR>(a, off, s) : launch_typed<R, true, false, FBAR>(a, off, s);
   else u ? launch_typed<R, false, true, FBAR>(a, off, s) : launch_typed<R, false, false, FBAR>(a, off, s);
+}
+
+void launch_gp_sweep_ext(const SweepArgs& a, int pass, int mode, const std::vector<int64_t>& color_off,
+                         cudaStream_t s) {
+  if (pass == 1) launch_typed<double, false, true, false, 1>(a, color_off, s);
+  else if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true, true, false, 2>(a, color_off, s);
+  else launch_typed<double, false, true, false, 2>(a, color_off, s);
 }
 
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,

@@ -258,6 +258,19 @@ class Solver:
         self._check(lib().hfe_spmv(self._h, _ptr(x), _ptr(y)))
         return y
 
+    def set_barlat(self, mat, **options):
+        """Give this FP64 handle the Barlat material `mat` (inputs.BarlatMaterial-like) through
+        hfe_set_barlat, with the local controls of cpp_options; mat None returns it to Hill-48."""
+        f = lib().hfe_set_barlat
+        f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
+        if mat is None:
+            self._check(f(self._h, None, None))
+            return
+        m = barlat_material(mat)
+        o = cpp_options(**options)
+        self._check(f(self._h, C.byref(m), C.byref(o)))
+
     def solve(self, b):
         b = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b
         x = np.empty(self.n_dof) if isinstance(b, np.ndarray) else b.new_empty(self.n_dof)
