@@ -213,6 +213,47 @@ def barlat_map_section(reps, stream, dev, with_cpu):
     return sec
 
 
+def barlat_fe_section(n, stream, dev, reps=5):
+    """Device time per FP64 tangent sweep of an n^3 cube at the compression state, with the
+    paper's Yld2004-18p coefficients (rotated 30 degrees about z, config 0's elasticity and
+    Swift hardening; the local projection with the FP32 iteration and FP64 finish, or all
+    FP64), and with the Hill-48 material of the same configuration."""
+    import torch
+    from paper_2606_17390_b300 import hfe
+    mesh, bc, mat, _ = inputs.config2_problem(n=n)
+    u, hist = inputs.compression_state(mesh, LOAD)
+    bm = inputs.barlat_verification_material()
+    th = mat.theta_vector()
+    bm.E, bm.nu, bm.hardening, bm.h = th[0], th[1], "swift", (th[8], th[9], th[10])
+    a = np.deg2rad(30.0)
+    bm.Theta = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1.0]])
+    out = {"workload": f"hex8 cube {n}^3 ({mesh.n_el} elements, {8 * mesh.n_el} Gauss points), clamped-platen "
+                       "compression mid-step state, FP64 tangent sweep; Yld2004-18p (m = 8) vs Hill-48"}
+    for name in ("barlat_mixed_projection", "barlat_fp64_projection", "hill"):
+        with torch.cuda.stream(stream):
+            s = hfe.from_inputs(mesh, bc, mat, precision="fp64", stream=stream.cuda_stream)
+            if name.startswith("barlat"):
+                s.set_barlat(bm, precision="mixed" if "mixed" in name else "fp64")
+            s.set_state(u, hist)
+            u_d = torch.from_numpy(u).to(dev)
+            R_d = torch.empty(mesh.n_dof, dtype=torch.float64, device=dev)
+            _, _, st = s.sweep(u_d, LOAD, tangent=True, R_out=R_d, stats=True)
+            for _ in range(2):
+                s.sweep(u_d, LOAD, tangent=True, R_out=R_d, stats=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                s.sweep(u_d, LOAD, tangent=True, R_out=R_d, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s.close()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_sweep": ms, "gp_per_s": 8 * mesh.n_el / (ms * 1e-3), "plastic_gps": st["plastic_gps"]}
+    out["barlat_over_hill"] = out["barlat_mixed_projection"]["ms_per_sweep"] / out["hill"]["ms_per_sweep"]
+    return out
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -258,6 +299,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
     ap.add_argument("--barlat-reps", type=int, default=20,
                     help="timed launches of the Barlat line-search map (0 = skip)")
+    ap.add_argument("--barlat-fe-n", type=int, default=40,
+                    help="cube edge of the FP64 Barlat tangent sweep timed against Hill-48 (0 = skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -487,6 +530,13 @@ def main():
     if args.barlat_reps > 0:
         barlat = barlat_map_section(args.barlat_reps, stream, dev, rank == 0 and not args.no_cpu_baseline)
 
+    # the Barlat model in the hex8 path (FP64): tangent sweeps of an n^3 cube at the
+    # compression state (strain pass, Gauss-point update, assembly pass) against the FP64
+    # Hill-48 sweep of the same state
+    barlat_fe = None
+    if args.barlat_fe_n > 0:
+        barlat_fe = barlat_fe_section(args.barlat_fe_n, stream, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist)
@@ -505,7 +555,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
                 "pcg": pcg, "adjoint": adjoint, "forward": forward, "fbar_sweep": fbar,
-                "barlat_map": barlat,
+                "barlat_map": barlat, "barlat_fe_sweep": barlat_fe,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}

@@ -364,12 +364,14 @@ hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, const hfe_cpp_o
  * T = E : (eps - eps_p,n+1)) and assembles with its tangent dT/deps = (dT/dT_tr) E, the
  * geometric pre- and post-processor and the element being those of the Hill-48 path.  The
  * history layout is unchanged (eps_p tensor components, alpha).  opt NULL = the defaults
- * (kmax 40; precision is ignored: FP64).  mat NULL returns the handle to Hill-48.  A local
+ * (kmax 40); opt->precision selects the projection's arithmetic (FP64, or the FP32 iteration
+ * with the FP64 finish to the same tolerance); the element path itself is FP64.  mat NULL
+ * returns the handle to Hill-48.  A local
  * projection that stops at kmax counts in stats.local_fail and the call returns
  * HFE_ELOCAL like the Hill-48 path.  hfe_adjoint returns HFE_EINVAL while the model is set.
  * Errors: HFE_EINVAL for a mixed-precision handle, per-element Hill parameters, the F-bar
- * element, or invalid material / options; HFE_ENOMEM if the exchange buffers (49 doubles and
- * a byte per Gauss point) cannot be allocated. */
+ * element, or invalid material / options; HFE_ENOMEM if the exchange buffers (64 doubles and
+ * 6 bytes per Gauss point) cannot be allocated. */
 hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const hfe_cpp_options* opt);
 
 #ifdef __cplusplus

@@ -175,7 +175,7 @@ hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, d
   if (h->barlat != nullptr) {   // Barlat: strain pass, the Gauss-point update, assembly pass
     launch_gp_sweep_ext(a, 1, mode, h->P.color_off, h->s);
     launch_barlat_gp(h->barlat, h->ext_eps, (const double*)hist, (double*)hist_trial, h->n_gp, h->ext_T, h->ext_D,
-                     h->ext_pl, mode == HFE_SWEEP_TANGENT ? 1 : 0, h->status, h->s);
+                     h->ext_pl, mode == HFE_SWEEP_TANGENT ? 1 : 0, h->status, h->ext_work, h->ext_it, h->ext_st, h->s);
     launch_gp_sweep_ext(a, 2, mode, h->P.color_off, h->s);
     return HFE_OK;
   }
@@ -632,6 +632,9 @@ hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const h
     if (a == HFE_OK) a = dalloc(h, &h->ext_T, 6 * ng);
     if (a == HFE_OK) a = dalloc(h, &h->ext_D, 36 * ng);
     if (a == HFE_OK) a = dalloc(h, &h->ext_pl, ng);
+    if (a == HFE_OK) a = dalloc(h, &h->ext_work, 15 * ng);
+    if (a == HFE_OK) a = dalloc(h, &h->ext_it, ng);
+    if (a == HFE_OK) a = dalloc(h, &h->ext_st, ng);
     if (a != HFE_OK) {
       hfe::barlat_model_free(m);
       return a;

@@ -818,50 +818,56 @@ __global__ void __launch_bounds__(kThreads) barlat_tangent_kernel(BarlatDev prm,
 }
 
 // The strain-driven update of a hex8 sweep's Gauss points (App. C, Algorithm
-// global_stress_update steps 2-6, FP64): from the Mandel log strain and the FP64 history
-// [8][n_gp] (eps_p tensor components, alpha, sigma_y cache), T_tr = E : (eps - eps_p,n), the
-// elastic test, the projection, the recovery eps_p,n+1 = eps_p,n + dgamma N(T),
-// T = E : (eps - eps_p,n+1); out: the trial history, the Mandel stress, the plastic flag and
-// (tangent != 0) D = dT/deps = (dT/dT_tr) E in Mandel form.  Non-converged projections are
-// counted in status->local_fail.
-__global__ void __launch_bounds__(kThreads) barlat_gp_kernel(BarlatDev prm, const double* __restrict__ eps_M,
-                                                             const double* __restrict__ hist,
-                                                             double* __restrict__ hist_trial, int64_t ng,
-                                                             double* __restrict__ T_M, double* __restrict__ D_M,
-                                                             uint8_t* __restrict__ pl, int tangent,
-                                                             hfe::DevStatus* __restrict__ status) {
+// global_stress_update steps 2-6): a prep kernel forms T_tr = E : (eps - eps_p,n) and alpha_n
+// from the Mandel log strain and the FP64 history [8][n_gp] (eps_p tensor components, alpha,
+// sigma_y cache); the projection kernels of the batch run on them (FP32 phase and FP64 finish,
+// or FP64, with lane refill); a post kernel recovers eps_p,n+1 = eps_p,n + dgamma N(T) and
+// T = E : (eps - eps_p,n+1), and writes the trial history, the Mandel stress, the plastic
+// flag and (tangent != 0) D = dT/deps = (dT/dT_tr) E in Mandel form.  Projections that end
+// without convergence are counted in status->local_fail.
+constexpr double kISq2d = 0.70710678118654752440, kSq2d = 1.41421356237309504880;
+
+__global__ void __launch_bounds__(kThreads) barlat_gp_prep_kernel(BarlatDev prm, const double* __restrict__ eps_M,
+                                                                  const double* __restrict__ hist, int64_t ng,
+                                                                  double* __restrict__ Ttr_out,
+                                                                  double* __restrict__ alpn_out) {
   __shared__ BarlatDev P;
   if (threadIdx.x == 0) P = prm;
   __syncthreads();
   const int64_t pt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (pt >= ng) return;
-  constexpr double kISq2d = 0.70710678118654752440, kSq2d = 1.41421356237309504880;
+  double ee[6], Ttr[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) ee[p] = eps_M[pt * 6 + p] * (p < 3 ? 1.0 : kISq2d) - hist[p * ng + pt];
+  elastic<double>(P, ee, Ttr);
+#pragma unroll
+  for (int p = 0; p < 6; ++p) Ttr_out[pt * 6 + p] = Ttr[p];
+  alpn_out[pt] = hist[6 * ng + pt];
+}
+
+__global__ void __launch_bounds__(kThreads) barlat_gp_post_kernel(
+    BarlatDev prm, const double* __restrict__ eps_M, const double* __restrict__ hist,
+    const double* __restrict__ Ttr_g, const double* __restrict__ alpn_g, const double* __restrict__ Ty,
+    const double* __restrict__ aly, const double* __restrict__ dgy, const int8_t* __restrict__ st_g, int64_t ng,
+    double* __restrict__ hist_trial, double* __restrict__ T_M, double* __restrict__ D_M, uint8_t* __restrict__ pl,
+    int tangent, hfe::DevStatus* __restrict__ status) {
+  __shared__ BarlatDev P;
+  if (threadIdx.x == 0) P = prm;
+  __syncthreads();
+  const int64_t pt = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (pt >= ng) return;
   double eps[6], epn[6], Ttr[6], ee[6];
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     eps[p] = eps_M[pt * 6 + p] * (p < 3 ? 1.0 : kISq2d);
     epn[p] = hist[p * ng + pt];
-    ee[p] = eps[p] - epn[p];
+    Ttr[p] = Ttr_g[pt * 6 + p];
   }
-  const double alpn = hist[6 * ng + pt];
-  elastic<double>(P, ee, Ttr);
-  double ds0;
-  double sref = sigma_y<double>(P, alpn, &ds0);
-  {
-    double nt = 0.0;
-#pragma unroll
-    for (int p = 0; p < 6; ++p) nt = fma(Ttr[p], Ttr[p], nt);
-    sref = fmax(sref, sqrt(nt));
-  }
-  double y[8];
-#pragma unroll
-  for (int p = 0; p < 6; ++p) y[p] = Ttr[p];
-  y[6] = alpn;
-  y[7] = 0.0;
-  int k = 0;
-  const int st = cpp_phase<double>(P, y, Ttr, alpn, 1.0 / sref, P.tol, P.kmax, k, 1);
+  const double alpn = alpn_g[pt];
+  const int st = st_g[pt];
   double T[6], epnew[6], alpha = alpn, Dc[6][6];
-  bool plastic = false;
+  bool plastic = false, ok = false;
+  double Tg[6][6];
   if (st == kElastic) {
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
@@ -871,8 +877,12 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_kernel(BarlatDev prm, cons
   } else {
     plastic = true;
     if (st != kConverged) atomicAdd(&status->local_fail, 1);
-    double Tg[6][6], N[6];
-    bool ok = cpp_tangent(P, y, Ttr, alpn, Tg, N);
+    double y[8], N[6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) y[p] = Ty[pt * 6 + p];
+    y[6] = aly[pt];
+    y[7] = dgy[pt];
+    ok = st != kNonfinite && cpp_tangent(P, y, Ttr, alpn, Tg, N);
     if (!ok) {
       atomicAdd(&status->nonfinite, 1);
 #pragma unroll
@@ -885,25 +895,9 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_kernel(BarlatDev prm, cons
     }
     elastic<double>(P, ee, T);
     alpha = y[6];
-    if (tangent) {
-      // D = Tg E: column q of E is E applied to the unit component q
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        double eq[6], Eq[6];
-#pragma unroll
-        for (int p = 0; p < 6; ++p) eq[p] = (p == q) ? 1.0 : 0.0;
-        elastic<double>(P, eq, Eq);
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          double v = 0.0;
-#pragma unroll
-          for (int c = 0; c < 6; ++c) v += (ok ? Tg[a][c] : (a == c ? 1.0 : 0.0)) * Eq[c];
-          Dc[a][q] = v;
-        }
-      }
-    }
   }
-  if (tangent && !plastic) {
+  if (tangent) {
+    // D = Tg E (E alone when elastic): column q of E is E applied to the unit component q
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       double eq[6], Eq[6];
@@ -911,8 +905,22 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_kernel(BarlatDev prm, cons
       for (int p = 0; p < 6; ++p) eq[p] = (p == q) ? 1.0 : 0.0;
       elastic<double>(P, eq, Eq);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) Dc[a][q] = Eq[a];
+      for (int a = 0; a < 6; ++a) {
+        double v = Eq[a];
+        if (ok) {
+          v = 0.0;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) v += Tg[a][c] * Eq[c];
+        }
+        Dc[a][q] = v;
+      }
     }
+    // Mandel: D_M[p][q] = s_p Dc[p][q] / s_q, s = (1, 1, 1, sqrt2, sqrt2, sqrt2)
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        D_M[pt * 36 + a * 6 + q] = Dc[a][q] * (a < 3 ? 1.0 : kSq2d) * (q < 3 ? 1.0 : kISq2d);
   }
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
@@ -923,14 +931,6 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_kernel(BarlatDev prm, cons
   double dsy;
   hist_trial[7 * ng + pt] = sigma_y<double>(P, alpha, &dsy);
   pl[pt] = plastic ? 1 : 0;
-  if (tangent) {
-    // Mandel: D_M[p][q] = s_p Dc[p][q] / s_q, s = (1, 1, 1, sqrt2, sqrt2, sqrt2)
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-      for (int q = 0; q < 6; ++q)
-        D_M[pt * 36 + a * 6 + q] = Dc[a][q] * (a < 3 ? 1.0 : kSq2d) * (q < 3 ? 1.0 : kISq2d);
-  }
 }
 
 __global__ void __launch_bounds__(kThreads) barlat_phi_kernel(BarlatDev prm, const double* __restrict__ T_g,
@@ -1127,6 +1127,29 @@ hfe_status apply_options(const hfe_cpp_options* opt, BarlatDev* P) {
   return HFE_OK;
 }
 
+// The projection of n trial states (FP32 phase and FP64 finish, or FP64) with lane refill
+// once the batch exceeds the resident threads.
+cudaError_t launch_projection(const BarlatDev& P, const double* Ttr, const double* alpn, int64_t n, double* T_out,
+                              double* alpha_out, double* dg_out, int32_t* it_out, int8_t* st_out, cudaStream_t s) {
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  int dev = 0, g32 = 0, g64 = 0, g64f = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = resident_blocks(dev, &g32, &g64, &g64f);
+  if (e != cudaSuccess) return e;
+  auto grid = [&](int resident) { return (unsigned)std::min<int64_t>(blocks, resident); };
+  auto chunk = [&](int resident) { return blocks > resident ? kChunk : (1 << 30); };
+  if (P.precision == HFE_PRECISION_MIXED) {
+    barlat_fp32_kernel<<<grid(g32), kThreads, 0, s>>>(P, Ttr, alpn, n, chunk(g32), T_out, alpha_out, dg_out, it_out,
+                                                      st_out);
+    barlat_fp64_kernel<1><<<grid(g64f), kThreads, 0, s>>>(P, Ttr, alpn, n, 0, chunk(g64f), T_out, alpha_out, dg_out,
+                                                          it_out, st_out);
+  } else {
+    barlat_fp64_kernel<3><<<grid(g64), kThreads, 0, s>>>(P, Ttr, alpn, n, 1, chunk(g64), T_out, alpha_out, dg_out,
+                                                         it_out, st_out);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // ---- the Barlat material of a hex8 handle (internal interface, hfe_internal.h)
@@ -1143,7 +1166,6 @@ BarlatModel* barlat_model_new(const hfe_barlat_material* mat, const hfe_cpp_opti
     delete m;
     return nullptr;
   }
-  m->P.precision = HFE_PRECISION_FP64;
   return m;
 }
 
@@ -1151,11 +1173,18 @@ void barlat_model_free(BarlatModel* m) { delete m; }
 
 void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* hist, double* hist_trial,
                       int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent, DevStatus* status,
-                      cudaStream_t s) {
+                      double* work, int32_t* iters, int8_t* st, cudaStream_t s) {
   const unsigned blocks = (unsigned)((n_gp + kThreads - 1) / kThreads);
-  if (blocks > 0)
-    barlat_gp_kernel<<<blocks, kThreads, 0, s>>>(m->P, eps_M, hist, hist_trial, n_gp, T_M, D_M, plastic, tangent,
-                                                 status);
+  if (blocks == 0) return;
+  double* Ttr = work;                 // [n_gp*6]
+  double* alpn = work + 6 * n_gp;     // [n_gp]
+  double* Ty = work + 7 * n_gp;       // [n_gp*6]
+  double* aly = work + 13 * n_gp;     // [n_gp]
+  double* dgy = work + 14 * n_gp;     // [n_gp]
+  barlat_gp_prep_kernel<<<blocks, kThreads, 0, s>>>(m->P, eps_M, hist, n_gp, Ttr, alpn);
+  launch_projection(m->P, Ttr, alpn, n_gp, Ty, aly, dgy, iters, st, s);
+  barlat_gp_post_kernel<<<blocks, kThreads, 0, s>>>(m->P, eps_M, hist, Ttr, alpn, Ty, aly, dgy, st, n_gp, hist_trial,
+                                                    T_M, D_M, plastic, tangent, status);
 }
 }  // namespace hfe
 
@@ -1211,22 +1240,9 @@ extern "C" hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, cons
   const int64_t blocks = (n + kThreads - 1) / kThreads;
   if (blocks > 0x7fffffffLL) return HFE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  const bool mixed = P.precision == HFE_PRECISION_MIXED;
-  int g32 = 0, g64 = 0, g64f = 0;
-  if (resident_blocks(dev, &g32, &g64, &g64f) != cudaSuccess) return HFE_ECUDA;
-  // one point per lane while the batch fits in the resident threads; otherwise turns of
-  // kChunk iterations with lane refill
-  auto grid = [&](int resident) { return (unsigned)std::min<int64_t>(blocks, resident); };
-  auto chunk = [&](int resident) { return blocks > resident ? kChunk : (1 << 30); };
-  if (mixed) {
-    barlat_fp32_kernel<<<grid(g32), kThreads, 0, s>>>(P, T_trial, alpha_n, n, chunk(g32), T_out, alpha_out,
-                                                      dgamma_out, iters_out, status_out);
-    barlat_fp64_kernel<1><<<grid(g64f), kThreads, 0, s>>>(P, T_trial, alpha_n, n, 0, chunk(g64f), T_out, alpha_out,
-                                                          dgamma_out, iters_out, status_out);
-  } else {
-    barlat_fp64_kernel<3><<<grid(g64), kThreads, 0, s>>>(P, T_trial, alpha_n, n, 1, chunk(g64), T_out, alpha_out,
-                                                         dgamma_out, iters_out, status_out);
-  }
+  if (launch_projection(P, T_trial, alpha_n, n, T_out, alpha_out, dgamma_out, iters_out, status_out, s) !=
+      cudaSuccess)
+    return HFE_ECUDA;
   if (tangent_out != nullptr)
     barlat_tangent_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(P, T_trial, alpha_n, n, T_out, alpha_out,
                                                                dgamma_out, status_out, tangent_out);

@@ -48,8 +48,10 @@ struct hfe_handle {
   // Barlat Yld2004-18p material (hfe_set_barlat; FP64 handles): the model and the per-Gauss-
   // point exchange buffers of its sweep (Mandel strain, stress, tangent, plastic flag)
   hfe::BarlatModel* barlat = nullptr;
-  double *ext_eps = nullptr, *ext_T = nullptr, *ext_D = nullptr;
+  double *ext_eps = nullptr, *ext_T = nullptr, *ext_D = nullptr, *ext_work = nullptr;
   uint8_t* ext_pl = nullptr;
+  int32_t* ext_it = nullptr;
+  int8_t* ext_st = nullptr;
   // device buffers
   double* X = nullptr;
   int32_t* conn = nullptr;

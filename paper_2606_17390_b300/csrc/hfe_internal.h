@@ -96,9 +96,10 @@ void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<
 struct BarlatModel;
 BarlatModel* barlat_model_new(const hfe_barlat_material* mat, const hfe_cpp_options* opt, hfe_status* st);
 void barlat_model_free(BarlatModel* m);
+// work: [n_gp*15] doubles, iters: [n_gp] int32, st: [n_gp] int8 (scratch of the projection)
 void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* hist, double* hist_trial,
                       int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent, DevStatus* status,
-                      cudaStream_t s);
+                      double* work, int32_t* iters, int8_t* st, cudaStream_t s);
 // External material model, FP64: pass 1 = strain pass (ext_eps out), pass 2 = assembly with
 // ext_T / ext_D / ext_plastic (mode HFE_SWEEP_RESIDUAL or HFE_SWEEP_TANGENT).
 void launch_gp_sweep_ext(const SweepArgs& a, int pass, int mode, const std::vector<int64_t>& color_off,

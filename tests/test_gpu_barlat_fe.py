@@ -35,7 +35,8 @@ def _local(m):
     return BA.local(BA.Barlat(m.c1, m.c2, m.m, m.Theta), m.E, m.nu, m.hardening, m.h)
 
 
-def test_barlat_sweep_vs_oracle():
+@pytest.mark.parametrize("projection", ["fp64", "mixed"])
+def test_barlat_sweep_vs_oracle(projection):
     mesh = inputs.distorted_box_mesh(3, seed=7, amp=0.2)
     u, hist = mixed_state(mesh, 41)
     m = _material()
@@ -47,7 +48,7 @@ def test_barlat_sweep_vs_oracle():
     Ro, Ko = solver.assemble_R(prob, es["Re"]), solver.assemble_K(prob, es["Ke"])
     th = inputs.config0_material().theta_vector()
     with hfe.Solver(mesh.X, mesh.conn, np.zeros(0, np.int64), np.zeros(0), th, "swift", precision="fp64") as s:
-        s.set_barlat(m)
+        s.set_barlat(m, precision=projection)
         s.set_state(np.zeros(mesh.n_dof), hist_oracle_to_soa(hist))
         Ht = np.empty((7, 8 * mesh.n_el))
         R, _, st = s.sweep(u, 1.0, tangent=True, hist_out=Ht)
@@ -59,9 +60,11 @@ def test_barlat_sweep_vs_oracle():
     assert np.abs(Hn - es["h_new"]).max() < 1e-12
 
 
-def test_barlat_forward_vs_oracle():
+@pytest.mark.parametrize("projection", ["fp64", "mixed"])
+def test_barlat_forward_vs_oracle(projection):
     """Config 0's cube (3^3, roller symmetry, stretch along x) in 4 steps, anisotropic and
-    rotated: every step's displacement against the oracle's forward."""
+    rotated: every step's displacement against the oracle's forward (the local projection in
+    FP64, or its FP32 iteration with the FP64 finish)."""
     mesh, bc, mat, ts = inputs.config0_problem(n=3, n_steps=4)
     m = _material()
     prob = solver.from_inputs(mesh, bc, mat)
@@ -69,7 +72,7 @@ def test_barlat_forward_vs_oracle():
     us, hs, infos = solver.forward(prob, ts, rtol=1e-13)
     assert infos[-1]["plastic"] > 0
     with hfe.from_inputs(mesh, bc, mat, precision="fp64", **OPTS) as s:
-        s.set_barlat(m)
+        s.set_barlat(m, precision=projection)
         u, st = s.forward(ts)
     for n in range(len(ts)):
         assert np.abs(u[n] - us[n]).max() < 1e-10 * np.abs(us[n]).max(), (n, np.abs(u[n] - us[n]).max())
