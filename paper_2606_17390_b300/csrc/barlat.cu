@@ -25,7 +25,8 @@
 // Precision.  FP64 runs every iteration in double.  B300 issues FP64 at a small fraction of
 // the FP32 rate, so the mixed path runs the same iteration (line search included) in FP32 down
 // to a scaled residual of 1e-5, about ten times the FP32 rounding floor, and finishes with at
-// most six FP64 Newton iterations from there; the elastic test is taken in FP32 outside a
+// most six iterations from there whose residual, test and line search are FP64 and whose
+// Newton matrix is formed in FP32; the elastic test is taken in FP32 outside a
 // band of 1e-5 s around f_tr = 0 and in FP64 inside it.  The tangent is always formed in FP64
 // at the returned state.
 #include <cuda_runtime.h>
@@ -421,7 +422,10 @@ __device__ __forceinline__ R psi_of(const R G[8]) {
 // sit at different stages of their own iterations, share that evaluation; a lane whose trial
 // is accepted (or that starts) goes on, in the same pass, to its convergence test and its
 // next Newton direction.  With the full step accepted, one Newton iteration is one pass.
-template <typename R>
+// RJ: arithmetic of the Newton matrix (R, or float for the FP64 finish of the mixed path,
+// where a Jacobian good to ~1e-7 still takes the residual from 1e-5 to the tolerance in the
+// same two iterations; the residual, its test and the line search stay in R).
+template <typename R, typename RJ = R>
 __device__ __forceinline__ int cpp_phase(const BarlatDev& P, R y[8], const R Ttr[6], R alpn, R isref, R tol,
                                          int kend, int& k, int elastic_test) {
   const Scal<R>& cs = scal<R>(P);
@@ -485,28 +489,39 @@ __device__ __forceinline__ int cpp_phase(const BarlatDev& P, R y[8], const R Ttr
     if (sqrt(r2) <= tol) return kConverged;
     if (k >= kend) return kMaxit;
     // Newton direction: J dy = -G by block elimination (G_alpha is linear in y)
-    R H[6][6], A6[6][6], X[6][2], EN[6], N[6];
-    phi_hessian<R>(P, s, dphi, H);
-    build_A6<R>(P, H, y[7], A6);
+    RJ H[6][6], A6[6][6], X[6][2], EN[6], N[6], dj[6];
+    Spec<RJ> sj;
+    if constexpr (sizeof(RJ) == sizeof(R)) {
+      phi_hessian<RJ>(P, s, dphi, H);
 #pragma unroll
-    for (int p = 0; p < 6; ++p) N[p] = dphi[p] / kWf<R>(p);
-    elastic<R>(P, N, EN);
+      for (int p = 0; p < 6; ++p) dj[p] = dphi[p];
+    } else {
+      RJ yj[8];
 #pragma unroll
-    for (int p = 0; p < 6; ++p) { X[p][0] = G[p]; X[p][1] = EN[p]; }
-    R hs;
-    sigma_y<R>(P, y[6], &hs);
-    bool okj = lu_solve6<R, 2>(A6, X);
-    R nx1 = R(0), nx2 = R(0);
+      for (int p = 0; p < 8; ++p) yj[p] = (RJ)y[p];
+      if (!phi_grad<RJ>(P, yj, sj, dj)) return kSingular;
+      phi_hessian<RJ>(P, sj, dj, H);
+    }
+    build_A6<RJ>(P, H, (RJ)y[7], A6);
 #pragma unroll
-    for (int p = 0; p < 6; ++p) { nx1 += dphi[p] * X[p][0]; nx2 += dphi[p] * X[p][1]; }
-    const R den = nx2 + hs;
-    okj = okj && den != R(0) && isfinite(den);
+    for (int p = 0; p < 6; ++p) N[p] = dj[p] / kWf<RJ>(p);
+    elastic<RJ>(P, N, EN);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) { X[p][0] = (RJ)G[p]; X[p][1] = EN[p]; }
+    RJ hs;
+    sigma_y<RJ>(P, (RJ)y[6], &hs);
+    bool okj = lu_solve6<RJ, 2>(A6, X);
+    RJ nx1 = RJ(0), nx2 = RJ(0);
+#pragma unroll
+    for (int p = 0; p < 6; ++p) { nx1 += dj[p] * X[p][0]; nx2 += dj[p] * X[p][1]; }
+    const RJ den = nx2 + hs;
+    okj = okj && den != RJ(0) && isfinite(den);
     if (!okj) return kSingular;
-    const R ddg = (G[7] + hs * G[6] - nx1) / den;
+    const RJ ddg = ((RJ)G[7] + hs * (RJ)G[6] - nx1) / den;
 #pragma unroll
-    for (int p = 0; p < 6; ++p) dy[p] = -X[p][0] - X[p][1] * ddg;
-    dy[6] = ddg - G[6];
-    dy[7] = ddg;
+    for (int p = 0; p < 6; ++p) dy[p] = (R)(-X[p][0] - X[p][1] * ddg);
+    dy[6] = (R)ddg - G[6];
+    dy[7] = (R)ddg;
     ++k;
     if (!P.line_search) {
 #pragma unroll
@@ -672,8 +687,9 @@ __global__ void __launch_bounds__(kThreads, 5) barlat_fp32_kernel(BarlatDev prm,
 // path from the FP32 results in the output arrays (full == 0).  Elastic points get T = T_tr.
 // Same lane scheduling as the FP32 kernel.  MINB: resident blocks per SM the register
 // allocation is bounded for (3 for the whole FP64 projection, 1 for the short finish; both
-// measured on the 16,000-point map and on a 64 times larger batch).
-template <int MINB>
+// measured on the 16,000-point map and on a 64 times larger batch).  RJ: arithmetic of the
+// Newton matrix (double for the FP64 projection, float for the finish of the mixed path).
+template <int MINB, typename RJ>
 __global__ void __launch_bounds__(kThreads, MINB) barlat_fp64_kernel(BarlatDev prm, const double* __restrict__ Ttr_g,
                                                                const double* __restrict__ alpn_g, int64_t n,
                                                                int full, int chunk, double* __restrict__ T_out,
@@ -724,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, MINB) barlat_fp64_kernel(BarlatDev p
       fresh = false;
     }
     const int k0 = k;
-    int status = cpp_phase<double>(P, y, q.Ttr, q.alpn, q.isref, P.tol, min(k + chunk, kend_pt), k, test);
+    int status = cpp_phase<double, RJ>(P, y, q.Ttr, q.alpn, q.isref, P.tol, min(k + chunk, kend_pt), k, test);
     test = 0;
     if (status == kMaxit && k < kend_pt && k > k0) continue;   // end of a turn: the point goes on
     if (status == kElastic) {
@@ -1095,8 +1111,8 @@ cudaError_t resident_blocks(int dev, int* g32, int* g64, int* g64f) {
     int sms = 0, b32 = 0, b64 = 0, b64f = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, barlat_fp32_kernel, kThreads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, barlat_fp64_kernel<3>, kThreads, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64f, barlat_fp64_kernel<1>, kThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, barlat_fp64_kernel<3, double>, kThreads, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64f, barlat_fp64_kernel<1, float>, kThreads, 0);
     if (e != cudaSuccess) return e;
     g_occ32[dev] = std::max(1, sms * b32);
     g_occ64[dev] = std::max(1, sms * b64);
@@ -1141,10 +1157,10 @@ cudaError_t launch_projection(const BarlatDev& P, const double* Ttr, const doubl
   if (P.precision == HFE_PRECISION_MIXED) {
     barlat_fp32_kernel<<<grid(g32), kThreads, 0, s>>>(P, Ttr, alpn, n, chunk(g32), T_out, alpha_out, dg_out, it_out,
                                                       st_out);
-    barlat_fp64_kernel<1><<<grid(g64f), kThreads, 0, s>>>(P, Ttr, alpn, n, 0, chunk(g64f), T_out, alpha_out, dg_out,
+    barlat_fp64_kernel<1, float><<<grid(g64f), kThreads, 0, s>>>(P, Ttr, alpn, n, 0, chunk(g64f), T_out, alpha_out, dg_out,
                                                           it_out, st_out);
   } else {
-    barlat_fp64_kernel<3><<<grid(g64), kThreads, 0, s>>>(P, Ttr, alpn, n, 1, chunk(g64), T_out, alpha_out, dg_out,
+    barlat_fp64_kernel<3, double><<<grid(g64), kThreads, 0, s>>>(P, Ttr, alpn, n, 1, chunk(g64), T_out, alpha_out, dg_out,
                                                          it_out, st_out);
   }
   return cudaGetLastError();
