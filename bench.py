@@ -228,12 +228,15 @@ def barlat_fe_section(n, stream, dev, reps=5):
     a = np.deg2rad(30.0)
     bm.Theta = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1.0]])
     out = {"workload": f"hex8 cube {n}^3 ({mesh.n_el} elements, {8 * mesh.n_el} Gauss points), clamped-platen "
-                       "compression mid-step state, FP64 tangent sweep; Yld2004-18p (m = 8) vs Hill-48"}
-    for name in ("barlat_mixed_projection", "barlat_fp64_projection", "hill"):
+                       "compression mid-step state, tangent sweep (FP64 and mixed handles); Yld2004-18p (m = 8) "
+                       "vs Hill-48"}
+    cases = {"barlat_mixed_projection": ("fp64", "mixed"), "barlat_fp64_projection": ("fp64", "fp64"),
+             "hill": ("fp64", None), "barlat_mixed_handle": ("mixed", "mixed"), "hill_mixed_handle": ("mixed", None)}
+    for name, (handle, projection) in cases.items():
         with torch.cuda.stream(stream):
-            s = hfe.from_inputs(mesh, bc, mat, precision="fp64", stream=stream.cuda_stream)
-            if name.startswith("barlat"):
-                s.set_barlat(bm, precision="mixed" if "mixed" in name else "fp64")
+            s = hfe.from_inputs(mesh, bc, mat, precision=handle, stream=stream.cuda_stream)
+            if projection is not None:
+                s.set_barlat(bm, precision=projection)
             s.set_state(u, hist)
             u_d = torch.from_numpy(u).to(dev)
             R_d = torch.empty(mesh.n_dof, dtype=torch.float64, device=dev)
@@ -251,6 +254,8 @@ def barlat_fe_section(n, stream, dev, reps=5):
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms_per_sweep": ms, "gp_per_s": 8 * mesh.n_el / (ms * 1e-3), "plastic_gps": st["plastic_gps"]}
     out["barlat_over_hill"] = out["barlat_mixed_projection"]["ms_per_sweep"] / out["hill"]["ms_per_sweep"]
+    out["barlat_over_hill_mixed_handle"] = (out["barlat_mixed_handle"]["ms_per_sweep"] /
+                                            out["hill_mixed_handle"]["ms_per_sweep"])
     return out
 
 

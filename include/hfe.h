@@ -357,7 +357,7 @@ hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, const hfe_cpp_o
                                  double* dgamma_out, int32_t* iters_out, int8_t* status_out, double* tangent_out,
                                  void* cuda_stream);
 
-/* Give an FP64 handle the Barlat Yld2004-18p material (uniform, standard element) in place of
+/* Give a handle the Barlat Yld2004-18p material (uniform, standard element) in place of
  * its Hill-48 parameters: every later sweep, solve and forward step updates the Gauss points
  * with App. C's stress update of this model from the total log strain (elastic test, the
  * projection with opt's controls in FP64, recovery eps_p,n+1 = eps_p,n + dgamma N,
@@ -365,12 +365,13 @@ hfe_status hfe_barlat_return_map(const hfe_barlat_material* mat, const hfe_cpp_o
  * geometric pre- and post-processor and the element being those of the Hill-48 path.  The
  * history layout is unchanged (eps_p tensor components, alpha).  opt NULL = the defaults
  * (kmax 40); opt->precision selects the projection's arithmetic (FP64, or the FP32 iteration
- * with the FP64 finish to the same tolerance); the element path itself is FP64.  mat NULL
+ * with the FP64 finish to the same tolerance); the element path keeps the handle's precision
+ * (FP64, or the mixed path's FP32 kinematics, post-processor and assembly).  mat NULL
  * returns the handle to Hill-48.  A local
  * projection that stops at kmax counts in stats.local_fail and the call returns
  * HFE_ELOCAL like the Hill-48 path.  hfe_adjoint returns HFE_EINVAL while the model is set.
- * Errors: HFE_EINVAL for a mixed-precision handle, per-element Hill parameters, the F-bar
- * element, or invalid material / options; HFE_ENOMEM if the exchange buffers (64 doubles and
+ * Errors: HFE_EINVAL for per-element Hill parameters, the F-bar element, or invalid
+ * material / options; HFE_ENOMEM if the exchange buffers (64 doubles and
  * 6 bytes per Gauss point) cannot be allocated. */
 hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const hfe_cpp_options* opt);
 

@@ -173,10 +173,10 @@ hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, d
   a.ext_plastic = h->ext_pl;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->s), "memset"));
   if (h->barlat != nullptr) {   // Barlat: strain pass, the Gauss-point update, assembly pass
-    launch_gp_sweep_ext(a, 1, mode, h->P.color_off, h->s);
-    launch_barlat_gp(h->barlat, h->ext_eps, (const double*)hist, (double*)hist_trial, h->n_gp, h->ext_T, h->ext_D,
-                     h->ext_pl, mode == HFE_SWEEP_TANGENT ? 1 : 0, h->status, h->ext_work, h->ext_it, h->ext_st, h->s);
-    launch_gp_sweep_ext(a, 2, mode, h->P.color_off, h->s);
+    launch_gp_sweep_ext(a, fp64, 1, mode, h->P.color_off, h->s);
+    launch_barlat_gp(h->barlat, fp64, h->ext_eps, hist, hist_trial, h->n_gp, h->ext_T, h->ext_D, h->ext_pl,
+                     mode == HFE_SWEEP_TANGENT ? 1 : 0, h->status, h->ext_work, h->ext_it, h->ext_st, h->s);
+    launch_gp_sweep_ext(a, fp64, 2, mode, h->P.color_off, h->s);
     return HFE_OK;
   }
   launch_gp_sweep(a, fp64, mode, h->P.color_off, h->s);
@@ -620,7 +620,6 @@ hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const h
     h->pred_valid = false;
     return HFE_OK;
   }
-  if (!h->fp64) return fail(h, HFE_EINVAL, "Barlat material: FP64 handles only");
   if (h->n_mat != 1) return fail(h, HFE_EINVAL, "Barlat material: the handle's material must be uniform");
   if (h->opt.fbar) return fail(h, HFE_EINVAL, "Barlat material: the standard element only");
   hfe_status st = HFE_OK;

@@ -843,8 +843,17 @@ __global__ void __launch_bounds__(kThreads) barlat_tangent_kernel(BarlatDev prm,
 // without convergence are counted in status->local_fail.
 constexpr double kISq2d = 0.70710678118654752440, kSq2d = 1.41421356237309504880;
 
+// history component c of Gauss point i in the handle's layout (H = double: [8][n_gp] with the
+// sigma_y cache at row 7; H = float: [7][n_gp] and the FP64 cache after it, at byte 28 n_gp)
+template <typename H>
+__device__ __forceinline__ double* hist_cache(void* h, int64_t ng) {
+  if constexpr (sizeof(H) == 8) return reinterpret_cast<double*>(h) + 7 * ng;
+  else return reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(h) + 28 * ng);
+}
+
+template <typename H>
 __global__ void __launch_bounds__(kThreads) barlat_gp_prep_kernel(BarlatDev prm, const double* __restrict__ eps_M,
-                                                                  const double* __restrict__ hist, int64_t ng,
+                                                                  const H* __restrict__ hist, int64_t ng,
                                                                   double* __restrict__ Ttr_out,
                                                                   double* __restrict__ alpn_out) {
   __shared__ BarlatDev P;
@@ -854,18 +863,19 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_prep_kernel(BarlatDev prm,
   if (pt >= ng) return;
   double ee[6], Ttr[6];
 #pragma unroll
-  for (int p = 0; p < 6; ++p) ee[p] = eps_M[pt * 6 + p] * (p < 3 ? 1.0 : kISq2d) - hist[p * ng + pt];
+  for (int p = 0; p < 6; ++p) ee[p] = eps_M[pt * 6 + p] * (p < 3 ? 1.0 : kISq2d) - (double)hist[p * ng + pt];
   elastic<double>(P, ee, Ttr);
 #pragma unroll
   for (int p = 0; p < 6; ++p) Ttr_out[pt * 6 + p] = Ttr[p];
-  alpn_out[pt] = hist[6 * ng + pt];
+  alpn_out[pt] = (double)hist[6 * ng + pt];
 }
 
+template <typename H>
 __global__ void __launch_bounds__(kThreads) barlat_gp_post_kernel(
-    BarlatDev prm, const double* __restrict__ eps_M, const double* __restrict__ hist,
+    BarlatDev prm, const double* __restrict__ eps_M, const H* __restrict__ hist,
     const double* __restrict__ Ttr_g, const double* __restrict__ alpn_g, const double* __restrict__ Ty,
     const double* __restrict__ aly, const double* __restrict__ dgy, const int8_t* __restrict__ st_g, int64_t ng,
-    double* __restrict__ hist_trial, double* __restrict__ T_M, double* __restrict__ D_M, uint8_t* __restrict__ pl,
+    H* __restrict__ hist_trial, double* __restrict__ T_M, double* __restrict__ D_M, uint8_t* __restrict__ pl,
     int tangent, hfe::DevStatus* __restrict__ status) {
   __shared__ BarlatDev P;
   if (threadIdx.x == 0) P = prm;
@@ -876,7 +886,7 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_post_kernel(
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     eps[p] = eps_M[pt * 6 + p] * (p < 3 ? 1.0 : kISq2d);
-    epn[p] = hist[p * ng + pt];
+    epn[p] = (double)hist[p * ng + pt];
     Ttr[p] = Ttr_g[pt * 6 + p];
   }
   const double alpn = alpn_g[pt];
@@ -941,11 +951,11 @@ __global__ void __launch_bounds__(kThreads) barlat_gp_post_kernel(
 #pragma unroll
   for (int p = 0; p < 6; ++p) {
     T_M[pt * 6 + p] = T[p] * (p < 3 ? 1.0 : kSq2d);
-    hist_trial[p * ng + pt] = epnew[p];
+    hist_trial[p * ng + pt] = (H)epnew[p];
   }
-  hist_trial[6 * ng + pt] = alpha;
+  hist_trial[6 * ng + pt] = (H)alpha;
   double dsy;
-  hist_trial[7 * ng + pt] = sigma_y<double>(P, alpha, &dsy);
+  hist_cache<H>(hist_trial, ng)[pt] = sigma_y<double>(P, alpha, &dsy);
   pl[pt] = plastic ? 1 : 0;
 }
 
@@ -1187,9 +1197,9 @@ BarlatModel* barlat_model_new(const hfe_barlat_material* mat, const hfe_cpp_opti
 
 void barlat_model_free(BarlatModel* m) { delete m; }
 
-void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* hist, double* hist_trial,
-                      int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent, DevStatus* status,
-                      double* work, int32_t* iters, int8_t* st, cudaStream_t s) {
+void launch_barlat_gp(const BarlatModel* m, bool fp64_hist, const double* eps_M, const void* hist,
+                      void* hist_trial, int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent,
+                      DevStatus* status, double* work, int32_t* iters, int8_t* st, cudaStream_t s) {
   const unsigned blocks = (unsigned)((n_gp + kThreads - 1) / kThreads);
   if (blocks == 0) return;
   double* Ttr = work;                 // [n_gp*6]
@@ -1197,10 +1207,19 @@ void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* h
   double* Ty = work + 7 * n_gp;       // [n_gp*6]
   double* aly = work + 13 * n_gp;     // [n_gp]
   double* dgy = work + 14 * n_gp;     // [n_gp]
-  barlat_gp_prep_kernel<<<blocks, kThreads, 0, s>>>(m->P, eps_M, hist, n_gp, Ttr, alpn);
+  if (fp64_hist)
+    barlat_gp_prep_kernel<double><<<blocks, kThreads, 0, s>>>(m->P, eps_M, (const double*)hist, n_gp, Ttr, alpn);
+  else
+    barlat_gp_prep_kernel<float><<<blocks, kThreads, 0, s>>>(m->P, eps_M, (const float*)hist, n_gp, Ttr, alpn);
   launch_projection(m->P, Ttr, alpn, n_gp, Ty, aly, dgy, iters, st, s);
-  barlat_gp_post_kernel<<<blocks, kThreads, 0, s>>>(m->P, eps_M, hist, Ttr, alpn, Ty, aly, dgy, st, n_gp, hist_trial,
-                                                    T_M, D_M, plastic, tangent, status);
+  if (fp64_hist)
+    barlat_gp_post_kernel<double><<<blocks, kThreads, 0, s>>>(m->P, eps_M, (const double*)hist, Ttr, alpn, Ty, aly,
+                                                              dgy, st, n_gp, (double*)hist_trial, T_M, D_M, plastic,
+                                                              tangent, status);
+  else
+    barlat_gp_post_kernel<float><<<blocks, kThreads, 0, s>>>(m->P, eps_M, (const float*)hist, Ttr, alpn, Ty, aly, dgy,
+                                                             st, n_gp, (float*)hist_trial, T_M, D_M, plastic, tangent,
+                                                             status);
 }
 }  // namespace hfe
 

@@ -96,13 +96,14 @@ void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<
 struct BarlatModel;
 BarlatModel* barlat_model_new(const hfe_barlat_material* mat, const hfe_cpp_options* opt, hfe_status* st);
 void barlat_model_free(BarlatModel* m);
-// work: [n_gp*15] doubles, iters: [n_gp] int32, st: [n_gp] int8 (scratch of the projection)
-void launch_barlat_gp(const BarlatModel* m, const double* eps_M, const double* hist, double* hist_trial,
-                      int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent, DevStatus* status,
-                      double* work, int32_t* iters, int8_t* st, cudaStream_t s);
-// External material model, FP64: pass 1 = strain pass (ext_eps out), pass 2 = assembly with
-// ext_T / ext_D / ext_plastic (mode HFE_SWEEP_RESIDUAL or HFE_SWEEP_TANGENT).
-void launch_gp_sweep_ext(const SweepArgs& a, int pass, int mode, const std::vector<int64_t>& color_off,
+// hist / hist_trial in the handle's layout (fp64: double [8][n_gp]; mixed: float [7][n_gp] and
+// the FP64 sigma_y cache); work: [n_gp*15] doubles, iters: [n_gp] int32, st: [n_gp] int8
+void launch_barlat_gp(const BarlatModel* m, bool fp64_hist, const double* eps_M, const void* hist,
+                      void* hist_trial, int64_t n_gp, double* T_M, double* D_M, uint8_t* plastic, int tangent,
+                      DevStatus* status, double* work, int32_t* iters, int8_t* st, cudaStream_t s);
+// External material model (FP64 or mixed sweep): pass 1 = strain pass (ext_eps out), pass 2 =
+// assembly with ext_T / ext_D / ext_plastic (mode HFE_SWEEP_RESIDUAL or HFE_SWEEP_TANGENT).
+void launch_gp_sweep_ext(const SweepArgs& a, bool fp64, int pass, int mode, const std::vector<int64_t>& color_off,
                          cudaStream_t s);
 void launch_sigma_cache(void* hist, bool fp64, const MatRec* mat, int mat_per_element, int hardening,
                         int64_t n_gp, cudaStream_t s);

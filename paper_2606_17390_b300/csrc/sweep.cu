@@ -1196,11 +1196,17 @@ static void launch_mode(const SweepArgs& a, int mode, const std::vector<int64_t>
   else u ? launch_typed<R, false, true, FBAR>(a, off, s) : launch_typed<R, false, false, FBAR>(a, off, s);
 }
 
-void launch_gp_sweep_ext(const SweepArgs& a, int pass, int mode, const std::vector<int64_t>& color_off,
+void launch_gp_sweep_ext(const SweepArgs& a, bool fp64, int pass, int mode, const std::vector<int64_t>& color_off,
                          cudaStream_t s) {
-  if (pass == 1) launch_typed<double, false, true, false, 1>(a, color_off, s);
-  else if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true, true, false, 2>(a, color_off, s);
-  else launch_typed<double, false, true, false, 2>(a, color_off, s);
+  if (fp64) {
+    if (pass == 1) launch_typed<double, false, true, false, 1>(a, color_off, s);
+    else if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true, true, false, 2>(a, color_off, s);
+    else launch_typed<double, false, true, false, 2>(a, color_off, s);
+  } else {
+    if (pass == 1) launch_typed<float, false, true, false, 1>(a, color_off, s);
+    else if (mode == HFE_SWEEP_TANGENT) launch_typed<float, true, true, false, 2>(a, color_off, s);
+    else launch_typed<float, false, true, false, 2>(a, color_off, s);
+  }
 }
 
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,

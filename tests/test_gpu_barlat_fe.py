@@ -1,8 +1,8 @@
-"""The Barlat Yld2004-18p material in the hex8 path (hfe_set_barlat, FP64): the tangent sweep
+"""The Barlat Yld2004-18p material in the hex8 path (hfe_set_barlat, FP64 and mixed handles): the tangent sweep
 on a distorted mesh with a mixed elastic/plastic state against the oracle's element with the
 Barlat stress update (residual, tangent through the exported block-CSR, trial history);
 forward runs against the oracle's forward; the isotropic model against the GPU's isotropic
-Hill-48 forward; switching back to Hill-48; and the refusals (mixed handle, adjoint)."""
+Hill-48 forward; switching back to Hill-48; and the refusals (adjoint, invalid material)."""
 import numpy as np
 import pytest
 
@@ -15,6 +15,8 @@ pytestmark = pytest.mark.gpu
 
 ONES = (1.0,) * 9
 OPTS = dict(newton_rtol=1e-12, pcg_rtol=1e-13)
+TOL = {"fp64": dict(R=1e-11, K=1e-9, h=1e-12, u=1e-10), "mixed": dict(R=2e-5, K=1e-4, h=1e-5, u=1e-5)}
+CASES = [("fp64", "fp64"), ("fp64", "mixed"), ("mixed", "mixed")]   # (handle, projection)
 
 
 def _material(iso=False, rotated=True):
@@ -35,8 +37,8 @@ def _local(m):
     return BA.local(BA.Barlat(m.c1, m.c2, m.m, m.Theta), m.E, m.nu, m.hardening, m.h)
 
 
-@pytest.mark.parametrize("projection", ["fp64", "mixed"])
-def test_barlat_sweep_vs_oracle(projection):
+@pytest.mark.parametrize("handle,projection", CASES)
+def test_barlat_sweep_vs_oracle(handle, projection):
     mesh = inputs.distorted_box_mesh(3, seed=7, amp=0.2)
     u, hist = mixed_state(mesh, 41)
     m = _material()
@@ -47,21 +49,22 @@ def test_barlat_sweep_vs_oracle(projection):
                           theta=np.zeros(11), hardening="swift")
     Ro, Ko = solver.assemble_R(prob, es["Re"]), solver.assemble_K(prob, es["Ke"])
     th = inputs.config0_material().theta_vector()
-    with hfe.Solver(mesh.X, mesh.conn, np.zeros(0, np.int64), np.zeros(0), th, "swift", precision="fp64") as s:
+    with hfe.Solver(mesh.X, mesh.conn, np.zeros(0, np.int64), np.zeros(0), th, "swift", precision=handle) as s:
         s.set_barlat(m, precision=projection)
         s.set_state(np.zeros(mesh.n_dof), hist_oracle_to_soa(hist))
         Ht = np.empty((7, 8 * mesh.n_el))
         R, _, st = s.sweep(u, 1.0, tangent=True, hist_out=Ht)
         K = bsr_to_csr(*s.get_bsr(), mesh.n_nodes)
-    assert st["plastic_gps"] == int(es["gp"]["plastic"].sum())
-    assert rel_inf(R, Ro) < 1e-11, rel_inf(R, Ro)
-    assert abs(K - Ko).max() < 1e-9 * abs(Ko).max()
+    tol = TOL[handle]
+    assert abs(st["plastic_gps"] - int(es["gp"]["plastic"].sum())) <= (0 if handle == "fp64" else 2)
+    assert rel_inf(R, Ro) < tol["R"], rel_inf(R, Ro)
+    assert abs(K - Ko).max() < tol["K"] * abs(Ko).max()
     Hn = hist_soa_to_oracle(Ht, mesh.n_el)
-    assert np.abs(Hn - es["h_new"]).max() < 1e-12
+    assert np.abs(Hn - es["h_new"]).max() < tol["h"]
 
 
-@pytest.mark.parametrize("projection", ["fp64", "mixed"])
-def test_barlat_forward_vs_oracle(projection):
+@pytest.mark.parametrize("handle,projection", CASES)
+def test_barlat_forward_vs_oracle(handle, projection):
     """Config 0's cube (3^3, roller symmetry, stretch along x) in 4 steps, anisotropic and
     rotated: every step's displacement against the oracle's forward (the local projection in
     FP64, or its FP32 iteration with the FP64 finish)."""
@@ -71,11 +74,12 @@ def test_barlat_forward_vs_oracle(projection):
     prob.local = _local(m)
     us, hs, infos = solver.forward(prob, ts, rtol=1e-13)
     assert infos[-1]["plastic"] > 0
-    with hfe.from_inputs(mesh, bc, mat, precision="fp64", **OPTS) as s:
+    opts = OPTS if handle == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=handle, **opts) as s:
         s.set_barlat(m, precision=projection)
         u, st = s.forward(ts)
     for n in range(len(ts)):
-        assert np.abs(u[n] - us[n]).max() < 1e-10 * np.abs(us[n]).max(), (n, np.abs(u[n] - us[n]).max())
+        assert np.abs(u[n] - us[n]).max() < TOL[handle]["u"] * np.abs(us[n]).max(), (n, np.abs(u[n] - us[n]).max())
 
 
 def test_isotropic_barlat_equals_isotropic_hill_on_gpu_and_switch_back():
@@ -101,10 +105,6 @@ def test_isotropic_barlat_equals_isotropic_hill_on_gpu_and_switch_back():
 def test_barlat_refusals():
     mesh, bc, mat, ts = inputs.config0_problem(n=2, n_steps=2)
     m = _material()
-    with hfe.from_inputs(mesh, bc, mat, precision="mixed") as s:
-        with pytest.raises(hfe.HfeError) as e:
-            s.set_barlat(m)
-        assert e.value.status == -1
     with hfe.from_inputs(mesh, bc, mat, precision="fp64") as s:
         s.set_barlat(m)
         u, _ = s.forward(ts)
