@@ -296,6 +296,8 @@ def main():
     ap.add_argument("--pcg-iters", type=int, default=200, help="PCG iterations timed for context (0 = skip)")
     ap.add_argument("--adjoint-nx", type=int, default=200, help="plate resolution of the adjoint ratio run (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--warm-delta", type=float, default=0.01,
+                    help="relative parameter change of the warm-start forward comparison (0 = skip)")
     ap.add_argument("--fbar-steps", type=int, default=20, help="timed F-bar tangent sweeps (0 = skip)")
     ap.add_argument("--adjoint-config", type=int, default=3, choices=(3, 4),
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
@@ -496,20 +498,46 @@ def main():
         with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th_true, stream=stream.cuda_stream) as s3:
             u_true, _ = s3.forward(t3)
         u_gt = u_true + inputs.noise(u_true.shape, 1e-3 * np.abs(u_true).max())
+        warm = None
         with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th_eval, stream=stream.cuda_stream) as s3:
             s3.set_state(None, None)
+            if args.warm_delta > 0:
+                s3.set_warm_start("record")   # this pass is the record of the warm-start run below
             t0 = time.perf_counter()
             _, fst = s3.forward(t3, want_u=False)
             t_fwd = time.perf_counter() - t0
             t0 = time.perf_counter()
             J3, g3, ast = s3.adjoint(t3, u_gt)
             t_adj = time.perf_counter() - t0
+            if args.warm_delta > 0:
+                # warm start (Sec. 3.6): the next evaluation of an inverse loop, parameters moved
+                # by up to warm_delta (relative, seeded), forward from the record vs cold
+                rng = np.random.default_rng(31)
+                th_next = th_eval * (1 + args.warm_delta * rng.uniform(-1, 1, th_eval.shape))
+                s3.set_material(th_next, s3.Theta_axes)
+                s3.set_warm_start("use")
+                s3.set_state(None, None)
+                t0 = time.perf_counter()
+                _, wst = s3.forward(t3, want_u=False)
+                t_warm = time.perf_counter() - t0
+                s3.set_warm_start("off")
+                s3.set_state(None, None)
+                t0 = time.perf_counter()
+                _, cst = s3.forward(t3, want_u=False)
+                t_cold = time.perf_counter() - t0
+                warm = {"parameter_change": f"every parameter x (1 + {args.warm_delta} U(-1, 1)), seed 31",
+                        "cold_forward_s": t_cold, "warm_forward_s": t_warm, "speedup": t_cold / t_warm,
+                        "cold_newton_iters": cst["newton_iters"], "warm_newton_iters": wst["newton_iters"],
+                        "cold_pcg_iters": cst["pcg_iters"], "warm_pcg_iters": wst["pcg_iters"],
+                        "warm_steps": wst["warm_steps"], "warm_retries": wst["warm_retries"],
+                        "cold_substeps": cst["substeps"], "warm_substeps": wst["substeps"]}
         adjoint = {"workload": f"config {args.adjoint_config}: perforated plate {nx}x{nx // 2} ({m3.n_el} elements, "
                                f"{m3.n_dof} dofs), {args.adjoint_steps} steps, {what}",
                    "forward_s": t_fwd, "gradient_call_s": t_adj, "reverse_s": ast["solve_ms"] * 1e-3,
                    "gradient_over_forward": t_adj / t_fwd, "reverse_over_forward": ast["solve_ms"] * 1e-3 / t_fwd,
                    "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"],
-                   "forward_substeps": fst["substeps"], "gradient_substeps": ast["substeps"]}
+                   "forward_substeps": fst["substeps"], "gradient_substeps": ast["substeps"],
+                   "warm_start": warm}
 
     # end-to-end forward solve of the 100^3 clamped-platen compression (10 load steps, mixed):
     # Newton, PCG and substep counts, and the in-solve Gauss-point update rate

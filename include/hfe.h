@@ -158,6 +158,9 @@ typedef struct {
                              solved again by BiCGSTAB */
   int64_t substeps;       /* accepted load (sub)steps */
   int64_t cutbacks;       /* rejected attempts (adaptive stepping) */
+  int64_t warm_steps;     /* requested load steps whose Newton iteration started from the
+                             warm-start record (hfe_set_warm_start) */
+  int64_t warm_retries;   /* of those, attempts that failed and were retried cold */
 } hfe_stats;
 
 /* Sizes of the internal data (for tests and benchmarks). */
@@ -231,6 +234,33 @@ hfe_status hfe_solve(hfe_handle* h, const double* b, double* x, hfe_stats* stats
  * device or NULL.  On success the stored state is the final one. */
 hfe_status hfe_forward(hfe_handle* h, int n_steps, const double* t, double* u_out,
                        double* sigma_out, double* hist_out, hfe_stats* stats);
+
+/* Warm start of the load steps for repeated forward passes (Sec. 3.6: inside the inverse
+ * loop the displacement of every step of the previous pass is the initial guess of the same
+ * step of the next, enabled while every parameter moved by less than 10 %).  The library
+ * records, on the device, the displacement each pass (hfe_forward, and the forward pass of
+ * hfe_adjoint) converges to at each requested load factor t[n].  In HFE_WARM_USE a later
+ * pass starts the Newton iteration of requested step n from record slot n when that slot was
+ * recorded at the same load factor (|t_rec - t[n]| <= 1e-12 max(1, |t[n]|)), with the
+ * Dirichlet values of t[n]; the step then spans the whole interval at once (an increment
+ * reduced by cutbacks in an earlier interval is not carried into it), and no predictor solve
+ * is made.  Its convergence reference is the cold step's (the predictor right-hand side norm,
+ * or the residual at u_{n-1} with the new Dirichlet values when options.predictor = 0), so a
+ * warm step meets the same tolerance as a cold one.  A warm attempt that fails is retried
+ * cold over the same increment before any cutback (hfe_stats.warm_retries).
+ *   mode: HFE_WARM_OFF (default): nothing recorded, every step cold, the record is freed;
+ *         HFE_WARM_RECORD: record each pass, start cold;
+ *         HFE_WARM_USE: record each pass and start from the record.
+ * Memory: n_steps x n_dof doubles on the device, owned by the handle, grown to the longest
+ * pass (older slots kept) and freed by HFE_WARM_OFF or hfe_destroy.  hfe_set_material,
+ * hfe_set_state and hfe_set_barlat keep the record: deciding whether it is close enough to
+ * the current parameters (the paper's 10 % rule) is the caller's.
+ * Errors: HFE_EINVAL for a NULL handle or an unknown mode; HFE_ENOMEM if the record cannot
+ * be allocated at the start of a pass (the pass then fails before its first step). */
+#define HFE_WARM_OFF 0
+#define HFE_WARM_RECORD 1
+#define HFE_WARM_USE 2
+hfe_status hfe_set_warm_start(hfe_handle* h, int mode);
 
 /* Misfit J = w sum_n ||u^n - u_target^n||^2 of a forward run from zero state over t, and its
  * gradient by the discrete adjoint (Eq. dR_u, Eq. main_grad) with the per-Gauss-point

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <string>
 #include <vector>
@@ -599,6 +600,7 @@ void hfe_destroy(hfe_handle* h) {
   if (h->ls.graph) cudaGraphExecDestroy(h->ls.graph);
   for (void* p : h->allocs) cudaFree(p);
   if (h->sigma) cudaFree(h->sigma);
+  if (h->warm_u) cudaFree(h->warm_u);
   if (h->h_sc) cudaFreeHost(h->h_sc);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
@@ -802,6 +804,49 @@ hfe_status hfe_solve(hfe_handle* h, const double* b, double* x, hfe_stats* stats
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
+// Warm-start record: room for n_steps displacements, the slots already recorded kept.
+namespace {
+hfe_status warm_reserve(hfe_handle* h, int n_steps) {
+  if (n_steps > h->warm_cap) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * (size_t)n_steps * h->n_dof) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, HFE_ENOMEM, "warm-start record");
+    }
+    double* nu = static_cast<double*>(p);
+    if (h->warm_u != nullptr) {
+      cudaError_t e = cudaMemcpyAsync(nu, h->warm_u, sizeof(double) * (size_t)h->warm_cap * h->n_dof,
+                                      cudaMemcpyDeviceToDevice, h->s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+      if (e != cudaSuccess) {
+        cudaFree(nu);
+        return cuda_check(h, e, "warm-start record");
+      }
+      cudaFree(h->warm_u);
+    }
+    h->warm_u = nu;
+    h->warm_cap = n_steps;
+  }
+  if ((int)h->warm_t.size() < n_steps) h->warm_t.resize(n_steps, std::numeric_limits<double>::quiet_NaN());
+  return HFE_OK;
+}
+}  // namespace
+
+extern "C" hfe_status hfe_set_warm_start(hfe_handle* h, int mode) {
+  if (h == nullptr || mode < HFE_WARM_OFF || mode > HFE_WARM_USE) return HFE_EINVAL;
+  if (mode == HFE_WARM_OFF && h->warm_u != nullptr) {
+    StreamScope scope(h);
+    cudaStreamSynchronize(h->s);
+    cudaFree(h->warm_u);
+    h->warm_u = nullptr;
+    h->warm_cap = 0;
+    h->warm_t.clear();
+  }
+  h->warm_mode = mode;
+  return HFE_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // Newton driver (shared with the adjoint's forward pass).
 hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double* u_out_dev_or_host,
                             double* sigma_out, double* hist_out, hfe_stats* st, StepHook* hook) {
@@ -812,10 +857,12 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   const int64_t bicg0 = h->n_bicgstab;
   // one load (sub)step from the stored state to t_new: predictor, Newton, commit; marker =
   // index of the requested load factor it reaches, or -1 for an intermediate substep
-  auto one_step = [&](const double t_new, const int marker) -> hfe_status {
+  // guess: the warm-start record slot of this requested step, or nullptr for a cold start
+  auto one_step = [&](const double t_new, const int marker, const double* guess) -> hfe_status {
       double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
       double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
-      bool last_tight = !h->opt.predictor || !h->opt.ew_forcing;   // the predictor solve is loose
+      // the predictor solve is loose; a warm start makes none
+      bool last_tight = !h->opt.predictor || !h->opt.ew_forcing || guess != nullptr;
       bool force_tight = false;
       int backtracks = 0;
       const double t_prev = h->t_state;
@@ -852,7 +899,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         HFE_TRY(read_status(h));
         ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
         set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
-        if (h->h_sc->norm2 > 0.0) {
+        if (h->h_sc->norm2 > 0.0 && guess == nullptr) {
           cudaEventRecord(h->t0, h->s);
           if (h->opt.ew_forcing) h->pcg_rtol_now = std::max(h->opt.pcg_rtol, 1e-3);   // predictor: rough solve
           h->allow_truncated = true;
@@ -872,6 +919,26 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         }
       } else {
         set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
+        if (guess != nullptr) {
+          // the cold step's reference: the residual at u_{n-1} with the new Dirichlet values
+          cudaEventRecord(h->t0, h->s);
+          HFE_TRY(sweep(h, h->u, t_new, HFE_SWEEP_RESIDUAL, h->R, nullptr));
+          cudaEventRecord(h->t1, h->s);
+          free_norm(h->R, h->freem, h->n_dof, h->sc, h->part, h->s, nullptr);
+          HFE_TRY(read_status(h));
+          loc.sweeps++;
+          loc.sweep_ms += elapsed(h->t0, h->t1);
+          HFE_TRY(check_sweep_status(h));
+          if (h->h_sc->nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite residual");
+          ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
+        }
+      }
+      if (guess != nullptr) {
+        // warm start: the previous pass's converged displacement at this load factor
+        HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u, guess, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
+                           "copy"));
+        set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
+        step_scale = 0.0;
       }
       int stall = 0;
       bool conv = false;
@@ -969,6 +1036,11 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       }
       std::swap(h->hist, h->hist_trial);   // commit h_n = H(u_n, h_{n-1})
       if (!h->fp64) launch_sigma_cache(h->hist, false, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
+      if (h->warm_mode != HFE_WARM_OFF && marker >= 0) {
+        HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->warm_u + (size_t)marker * h->n_dof, h->u, sizeof(double) * h->n_dof,
+                                              cudaMemcpyDeviceToDevice, h->s), "copy"));
+        h->warm_t[marker] = t_new;
+      }
       if (u_out_dev_or_host != nullptr && marker >= 0) {
         double* dst = u_out_dev_or_host + (size_t)marker * h->n_dof;
         if (u_out_dev) HFE_TRY(cuda_check(h, cudaMemcpyAsync(dst, h->u, 8 * h->n_dof, cudaMemcpyDeviceToDevice, h->s), "copy"));
@@ -980,8 +1052,8 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       return HFE_OK;
   };
   // a failed attempt leaves the stored state at the last converged step
-  auto attempt = [&](const double t_new, const int marker) -> hfe_status {
-    const hfe_status s = one_step(t_new, marker);
+  auto attempt = [&](const double t_new, const int marker, const double* guess) -> hfe_status {
+    const hfe_status s = one_step(t_new, marker, guess);
     if (s != HFE_OK) {
       h->pred_valid = false;
       h->allow_truncated = h->allow_indefinite = false;
@@ -1000,6 +1072,10 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   // increment carries over to the next interval.
   // Increments are handled as magnitudes along the direction of each interval, so loading
   // and unloading intervals are stepped alike.
+  //
+  // Warm start: the record is sized for this pass first; a requested step whose record slot
+  // holds the same load factor starts from it and spans its whole interval.
+  if (h->warm_mode != HFE_WARM_OFF) HFE_TRY(warm_reserve(h, n_steps));
   double inc_carry = 0.0;
   for (int n = 0; n < n_steps; ++n) {
     int cuts = 0, ok_run = 0;
@@ -1007,13 +1083,27 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
     const double dirn = span < 0.0 ? -1.0 : 1.0;
     double inc_try = std::fabs(span);
     const double inc_min = inc_try * std::pow(h->opt.cutback, (double)h->opt.max_cutbacks);
-    if (inc_carry > 0.0 && inc_carry < inc_try) inc_try = inc_carry;
+    const double* guess = nullptr;
+    if (h->warm_mode == HFE_WARM_USE && n < (int)h->warm_t.size() &&
+        std::fabs(h->warm_t[n] - t[n]) <= 1e-12 * std::max(1.0, std::fabs(t[n])))
+      guess = h->warm_u + (size_t)n * h->n_dof;
+    if (guess == nullptr && inc_carry > 0.0 && inc_carry < inc_try) inc_try = inc_carry;
+    if (guess != nullptr) loc.warm_steps++;
     for (;;) {
       const double remaining = std::fabs(t[n] - h->t_state);
       const double inc = std::min(inc_try, remaining);
       const bool hits = inc >= remaining * (1.0 - 1e-12);
       const double t_new = hits ? t[n] : h->t_state + dirn * inc;
-      const hfe_status s = attempt(t_new, hits ? n : -1);
+      const double* g = hits ? guess : nullptr;
+      const hfe_status s = attempt(t_new, hits ? n : -1, g);
+      const bool recoverable = s == HFE_ENEWTON || s == HFE_EDETJ || s == HFE_ENONFINITE || s == HFE_EPCG ||
+                               s == HFE_ELOCAL;
+      if (s != HFE_OK && g != nullptr && recoverable) {
+        // a failed warm attempt is retried cold over the same increment
+        guess = nullptr;
+        loc.warm_retries++;
+        continue;
+      }
       if (s == HFE_OK) {
         loc.substeps++;
         if (hits) break;
@@ -1025,8 +1115,6 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         }
         continue;
       }
-      const bool recoverable = s == HFE_ENEWTON || s == HFE_EDETJ || s == HFE_ENONFINITE || s == HFE_EPCG ||
-                               s == HFE_ELOCAL;
       if (!h->opt.adaptive || !recoverable || inc * h->opt.cutback < inc_min * (1.0 - 1e-9)) {
         loc.bicgstab_solves = h->n_bicgstab - bicg0;
         if (st) *st = loc;

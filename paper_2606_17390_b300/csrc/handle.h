@@ -97,6 +97,12 @@ struct hfe_handle {
   bool pred_valid = false;
   double* u_start = nullptr;     // start-of-step displacement, restored when a step fails
   double* sigma = nullptr;     // n_gp * 6, allocated on demand
+  // warm start: the displacement each pass converged to at its requested load factors
+  // (warm_t[k], slot k of warm_u, warm_cap slots of n_dof doubles), kept across passes
+  int warm_mode = 0;
+  double* warm_u = nullptr;
+  int warm_cap = 0;
+  std::vector<double> warm_t;
   // pinned host mirrors of the device scalars
   PcgScalars* h_sc = nullptr;
   DevStatus* h_status = nullptr;

@@ -56,7 +56,8 @@ class Stats(C.Structure):
                 ("plastic_gps", C.c_int64), ("local_fail", C.c_int64), ("max_local_iters", C.c_int32),
                 ("steps_done", C.c_int32), ("last_residual", C.c_double), ("sweep_ms", C.c_double),
                 ("solve_ms", C.c_double), ("total_ms", C.c_double), ("bicgstab_solves", C.c_int64),
-                ("substeps", C.c_int64), ("cutbacks", C.c_int64)]
+                ("substeps", C.c_int64), ("cutbacks", C.c_int64), ("warm_steps", C.c_int64),
+                ("warm_retries", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -259,8 +260,9 @@ class Solver:
         return y
 
     def set_barlat(self, mat, **options):
-        """Give this FP64 handle the Barlat material `mat` (inputs.BarlatMaterial-like) through
-        hfe_set_barlat, with the local controls of cpp_options; mat None returns it to Hill-48."""
+        """Give this handle (FP64 or mixed) the Barlat material `mat` (inputs.BarlatMaterial-like)
+        through hfe_set_barlat, with the local controls of cpp_options; mat None returns it to
+        Hill-48."""
         f = lib().hfe_set_barlat
         f.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         f.restype = C.c_int
@@ -270,6 +272,17 @@ class Solver:
         m = barlat_material(mat)
         o = cpp_options(**options)
         self._check(f(self._h, C.byref(m), C.byref(o)))
+
+    WARM_MODES = {"off": 0, "record": 1, "use": 2}
+
+    def set_warm_start(self, mode):
+        """hfe_set_warm_start: "off" (cold steps, record freed), "record" (record each pass's
+        displacement at its requested load factors) or "use" (record, and start each requested
+        step's Newton iteration from the recorded displacement at the same load factor)."""
+        f = lib().hfe_set_warm_start
+        f.argtypes = [C.c_void_p, C.c_int]
+        f.restype = C.c_int
+        self._check(f(self._h, self.WARM_MODES[mode] if isinstance(mode, str) else int(mode)))
 
     def solve(self, b):
         b = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b

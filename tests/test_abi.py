@@ -47,3 +47,39 @@ def test_null_arguments_rejected_without_device_work():
     assert L.hfe_create(None, None, None, None, None, None) == -1
     assert L.hfe_get_info(None, None) == -1
     assert L.hfe_last_error(None) == b"null handle"
+    L.hfe_set_warm_start.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert L.hfe_set_warm_start(None, 0) == -1
+
+
+def test_ctypes_mirrors_match_the_header_layout(tmp_path):
+    """Every struct of include/hfe.h that the binding mirrors has the same size and field
+    offsets in ctypes as in C (the header compiled by the host compiler)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    mirrors = {"hfe_mesh": hfe._Mesh, "hfe_bc": hfe._BC, "hfe_material": hfe._Material,
+               "hfe_options": hfe.Options, "hfe_stats": hfe.Stats, "hfe_info": hfe.Info,
+               "hfe_barlat_material": hfe.BarlatMaterialC, "hfe_cpp_options": hfe.CppOptions}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hfe.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -19,6 +19,18 @@ def test_normalisation_round_trip_and_paper_initial_guess():
     assert np.allclose(inverse.denormalize(1.0, tmin, tref), tmin + tref)
 
 
+def test_warm_start_rule():
+    # Sec. 3.6: the previous pass is reused when every parameter moved by less than 10 %
+    prev = np.array([150.0, 120.0, 12.0, 0.0])
+    assert not inverse.warm_start_applies(prev, None)
+    assert inverse.warm_start_applies(prev, prev)
+    assert inverse.warm_start_applies(prev * [1.09, 0.92, 1.0, 1.0], prev)
+    assert not inverse.warm_start_applies(prev * [1.1, 1.0, 1.0, 1.0], prev)      # exactly 10 %
+    assert not inverse.warm_start_applies(prev * [1.0, 1.0, 0.85, 1.0], prev)
+    assert not inverse.warm_start_applies(prev + [0.0, 0.0, 0.0, 1e-9], prev)     # from 0
+    assert inverse.warm_start_applies(np.full((3, 2), 1.05), np.ones((3, 2)))    # per element
+
+
 @pytest.mark.gpu
 def test_identify_voce_parameters_noiseless():
     from oracle import solver
