@@ -303,6 +303,8 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
+    ap.add_argument("--forward-predictors", default="1",
+                    help="comma-separated options.predictor values of the forward run (first one reported)")
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
     ap.add_argument("--barlat-reps", type=int, default=20,
                     help="timed launches of the Barlat line-search map (0 = skip)")
@@ -544,16 +546,23 @@ def main():
     forward = None
     if args.forward_n > 0:
         m2, bc2, mat2, t2 = inputs.config2_problem(args.forward_n, args.forward_steps)
-        with hfe.from_inputs(m2, bc2, mat2, precision=args.precision, stream=stream.cuda_stream) as s2:
-            t0 = time.perf_counter()
-            _, st2 = s2.forward(t2, want_u=False)
-            wall = time.perf_counter() - t0
+        names = {0: "previous", 1: "tangent", 2: "linear_extrapolation", 3: "quadratic_extrapolation"}
+        runs = {}
+        for pm in [int(x) for x in args.forward_predictors.split(",")]:
+            with hfe.from_inputs(m2, bc2, mat2, precision=args.precision, stream=stream.cuda_stream,
+                                 predictor=pm) as s2:
+                t0 = time.perf_counter()
+                _, st2 = s2.forward(t2, want_u=False)
+                wall = time.perf_counter() - t0
+            runs[names[pm]] = {"wall_s": wall, "newton_iters": st2["newton_iters"], "pcg_iters": st2["pcg_iters"],
+                               "substeps": st2["substeps"], "cutbacks": st2["cutbacks"], "sweeps": st2["sweeps"],
+                               "sweep_s": st2["sweep_ms"] * 1e-3, "solve_s": st2["solve_ms"] * 1e-3,
+                               "in_solve_gp_per_s": st2["sweeps"] * 8 * m2.n_el / (st2["sweep_ms"] * 1e-3)}
+        first = next(iter(runs.values()))
         forward = {"workload": f"hex8 cube {args.forward_n}^3 ({m2.n_dof} dofs), 10 % compression between clamped "
-                               f"platens, {args.forward_steps} load steps, {args.precision}",
-                   "wall_s": wall, "newton_iters": st2["newton_iters"], "pcg_iters": st2["pcg_iters"],
-                   "substeps": st2["substeps"], "cutbacks": st2["cutbacks"], "sweeps": st2["sweeps"],
-                   "sweep_s": st2["sweep_ms"] * 1e-3, "solve_s": st2["solve_ms"] * 1e-3,
-                   "in_solve_gp_per_s": st2["sweeps"] * 8 * m2.n_el / (st2["sweep_ms"] * 1e-3)}
+                               f"platens, {args.forward_steps} load steps, {args.precision}", **first}
+        if len(runs) > 1:
+            forward["predictors"] = runs
 
     # Barlat Yld2004-18p material points: the line-search robustness map (16,000 pi-plane trial
     # states between the yield surface and 30 times it, the verification parameters, perfect

@@ -113,10 +113,18 @@ typedef struct {
   int local_maxit;        /* bound of the local return-mapping Newton */
   double local_tol;       /* relative tolerance of the local yield residual */
   int ckpt_every;         /* adjoint: store the history every k steps, recompute between */
-  int predictor;          /* 1 (default): each step starts from the tangent predictor
-                             u = u_{n-1} + du_D + dK^-1 (-(R + K du_D)) built on the converged
-                             start-of-step state, where K is positive definite; 0: from u_{n-1}
-                             with the new Dirichlet values only */
+  int predictor;          /* initial guess of each (sub)step's Newton iteration:
+                             1 (default): the tangent predictor u = u_{n-1} + du_D +
+                             K^-1 (-(R + K du_D)) built on the converged start-of-step state;
+                             0: u_{n-1} with the new Dirichlet values;
+                             2 / 3: linear / quadratic extrapolation in the load factor through
+                             the last 2 / 3 converged (sub)step solutions (Sec. 2.2, automatic
+                             time stepping), lower order while fewer are stored (after
+                             hfe_create, hfe_set_state, hfe_set_load, hfe_set_material or
+                             hfe_set_barlat the stored state is the only one); the Dirichlet
+                             values are those of the new load factor.  Modes 0, 2 and 3 take the
+                             residual at u_{n-1} with the new Dirichlet values as the Newton
+                             reference norm (2 and 3 spend one residual sweep on it) */
   int ew_forcing;         /* 1: inexact Newton, the CG tolerance of each Newton solve follows the
                              Eisenstat-Walker forcing term (never below pcg_rtol) and a step is
                              accepted only after a correction solved to pcg_rtol; about 2x fewer

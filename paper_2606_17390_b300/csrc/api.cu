@@ -453,6 +453,7 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   if (h->opt.adaptive && !(h->opt.cutback > 0.0 && h->opt.cutback < 1.0))
     return fail(h, HFE_EINVAL, "options: cutback must lie in (0, 1)");
   if (h->opt.max_cutbacks < 0) return fail(h, HFE_EINVAL, "options: max_cutbacks must be >= 0");
+  if (h->opt.predictor < 0 || h->opt.predictor > 3) return fail(h, HFE_EINVAL, "options: predictor must be 0 to 3");
   h->fp64 = h->opt.precision == HFE_PRECISION_FP64;
   h->user = reinterpret_cast<cudaStream_t>(stream);
   HFE_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"));
@@ -601,6 +602,8 @@ void hfe_destroy(hfe_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->sigma) cudaFree(h->sigma);
   if (h->warm_u) cudaFree(h->warm_u);
+  for (double* p : h->extrap_u)
+    if (p) cudaFree(p);
   if (h->h_sc) cudaFreeHost(h->h_sc);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
@@ -620,6 +623,7 @@ hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const h
     hfe::barlat_model_free(h->barlat);
     h->barlat = nullptr;
     h->pred_valid = false;
+    h->extrap_n = 0;
     return HFE_OK;
   }
   if (h->n_mat != 1) return fail(h, HFE_EINVAL, "Barlat material: the handle's material must be uniform");
@@ -644,6 +648,7 @@ hfe_status hfe_set_barlat(hfe_handle* h, const hfe_barlat_material* mat, const h
   hfe::barlat_model_free(h->barlat);
   h->barlat = m;
   h->pred_valid = false;
+  h->extrap_n = 0;
   return HFE_OK;
 }
 
@@ -662,8 +667,9 @@ hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info) {
 }
 
 hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat) {
-  if (h) h->pred_valid = false;
   if (h == nullptr) return HFE_EINVAL;
+  h->pred_valid = false;
+  h->extrap_n = 0;
   StreamScope scope(h);
   HFE_TRY(upload_material(h, mat));
   launch_sigma_cache(h->hist, h->fp64 != 0, h->mat64, h->n_mat > 1, h->hardening, h->n_gp, h->s);
@@ -672,7 +678,8 @@ hfe_status hfe_set_material(hfe_handle* h, const hfe_material* mat) {
 
 hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist) {
   if (h == nullptr) return HFE_EINVAL;
-  if (h) h->pred_valid = false;
+  h->pred_valid = false;
+  h->extrap_n = 0;
   StreamScope scope(h);
   if (u) HFE_TRY(copy_in(h, h->u, u, sizeof(double) * h->n_dof));
   else HFE_TRY(cuda_check(h, cudaMemsetAsync(h->u, 0, sizeof(double) * h->n_dof, h->s), "memset"));
@@ -685,7 +692,8 @@ hfe_status hfe_set_state(hfe_handle* h, const double* u, const double* hist) {
 
 hfe_status hfe_set_load(hfe_handle* h, double t) {
   if (h == nullptr || !std::isfinite(t)) return HFE_EINVAL;
-  if (h) h->pred_valid = false;
+  h->pred_valid = false;
+  h->extrap_n = 0;
   h->t_state = t;
   return HFE_OK;
 }
@@ -804,6 +812,58 @@ hfe_status hfe_solve(hfe_handle* h, const double* b, double* x, hfe_stats* stats
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
+// Extrapolated predictor (Sec. 2.2, automatic time stepping): u = sum_k w_k u_k on the free
+// dofs, w_k the Lagrange weights in the load factor of the stored (sub)step solutions.
+namespace {
+constexpr int kExtrapBlock = 256;
+
+__global__ void __launch_bounds__(kExtrapBlock) extrapolate_kernel(double* __restrict__ u, const double* __restrict__ u0,
+                                                                   const double* __restrict__ u1,
+                                                                   const double* __restrict__ u2, double w0, double w1,
+                                                                   double w2, const uint8_t* __restrict__ freem,
+                                                                   int64_t n_dof) {
+  const int64_t d = (int64_t)blockIdx.x * kExtrapBlock + threadIdx.x;
+  if (d >= n_dof || !freem[d]) return;
+  double v = w0 * u0[d] + w1 * u1[d];
+  if (u2 != nullptr) v += w2 * u2[d];
+  u[d] = v;
+}
+
+// stores (t, u) as the newest solution of the extrapolation history
+hfe_status extrap_push(hfe_handle* h, double t) {
+  double* oldest = h->extrap_u[2];
+  h->extrap_u[2] = h->extrap_u[1];
+  h->extrap_u[1] = h->extrap_u[0];
+  h->extrap_u[0] = oldest;
+  h->extrap_t[2] = h->extrap_t[1];
+  h->extrap_t[1] = h->extrap_t[0];
+  h->extrap_t[0] = t;
+  h->extrap_n = std::min(h->extrap_n + 1, 3);
+  return cuda_check(h, cudaMemcpyAsync(h->extrap_u[0], h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
+                    "copy");
+}
+
+// the number of stored solutions the extrapolation to t_new uses (1 = none: u_{n-1} stays),
+// and their Lagrange weights; points closer than 1e-12 in the load factor lower the order
+int extrap_weights(const hfe_handle* h, double t_new, double w[3]) {
+  int k = std::min(h->extrap_n, h->opt.predictor == 2 ? 2 : 3);
+  const double* tk = h->extrap_t;
+  auto close = [](double a, double b) { return std::fabs(a - b) <= 1e-12 * std::max(1.0, std::fabs(a)); };
+  if (k == 3 && (close(tk[0], tk[2]) || close(tk[1], tk[2]))) k = 2;
+  if (k >= 2 && close(tk[0], tk[1])) k = 1;
+  w[0] = 1.0;
+  w[1] = w[2] = 0.0;
+  for (int i = 0; i < k; ++i) {
+    double l = 1.0;
+    for (int j = 0; j < k; ++j)
+      if (j != i) l *= (t_new - tk[j]) / (tk[i] - tk[j]);
+    w[i] = l;
+  }
+  return k;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
 // Warm-start record: room for n_steps displacements, the slots already recorded kept.
 namespace {
 hfe_status warm_reserve(hfe_handle* h, int n_steps) {
@@ -861,14 +921,17 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   auto one_step = [&](const double t_new, const int marker, const double* guess) -> hfe_status {
       double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
       double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
-      // the predictor solve is loose; a warm start makes none
-      bool last_tight = !h->opt.predictor || !h->opt.ew_forcing || guess != nullptr;
+      // the tangent predictor's solve is loose; a warm start or an extrapolation makes none
+      bool last_tight = h->opt.predictor != 1 || !h->opt.ew_forcing || guess != nullptr;
       bool force_tight = false;
       int backtracks = 0;
       const double t_prev = h->t_state;
       HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u_start, h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
                          "copy"));
-      if (h->opt.predictor) {
+      if (h->opt.predictor >= 2 && h->extrap_n == 0) HFE_TRY(extrap_push(h, t_prev));
+      double wex[3];
+      const int kex = (h->opt.predictor >= 2 && guess == nullptr) ? extrap_weights(h, t_new, wex) : 1;
+      if (h->opt.predictor == 1) {
         // tangent predictor on the converged start-of-step state u_{n-1}:
         // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment,
         // with K and R of the previous step's last Newton iteration (its consistent tangent at
@@ -919,8 +982,8 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         }
       } else {
         set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
-        if (guess != nullptr) {
-          // the cold step's reference: the residual at u_{n-1} with the new Dirichlet values
+        if (guess != nullptr || kex > 1) {
+          // the reference of a step from u_{n-1}: the residual there with the new Dirichlet values
           cudaEventRecord(h->t0, h->s);
           HFE_TRY(sweep(h, h->u, t_new, HFE_SWEEP_RESIDUAL, h->R, nullptr));
           cudaEventRecord(h->t1, h->s);
@@ -931,6 +994,14 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
           HFE_TRY(check_sweep_status(h));
           if (h->h_sc->nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite residual");
           ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
+        }
+        if (kex > 1) {
+          const unsigned blocks = (unsigned)((h->n_dof + kExtrapBlock - 1) / kExtrapBlock);
+          extrapolate_kernel<<<blocks, kExtrapBlock, 0, h->s>>>(h->u, h->extrap_u[0], h->extrap_u[1],
+                                                              kex == 3 ? h->extrap_u[2] : nullptr, wex[0], wex[1],
+                                                              wex[2], h->freem, h->n_dof);
+          HFE_TRY(cuda_check(h, cudaGetLastError(), "extrapolate"));
+          step_scale = 0.0;
         }
       }
       if (guess != nullptr) {
@@ -1048,6 +1119,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       }
       h->t_state = t_new;
       h->pred_valid = true;
+      if (h->opt.predictor >= 2) HFE_TRY(extrap_push(h, t_new));
       if (hook) HFE_TRY(hook->after_commit(h, t_new, marker));
       return HFE_OK;
   };
@@ -1076,6 +1148,21 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   // Warm start: the record is sized for this pass first; a requested step whose record slot
   // holds the same load factor starts from it and spans its whole interval.
   if (h->warm_mode != HFE_WARM_OFF) HFE_TRY(warm_reserve(h, n_steps));
+  if (h->opt.predictor >= 2 && h->extrap_u[0] == nullptr) {
+    for (double*& p : h->extrap_u) {
+      void* q = nullptr;
+      if (cudaMalloc(&q, sizeof(double) * h->n_dof) != cudaSuccess) {
+        cudaGetLastError();
+        for (double*& r : h->extrap_u) {
+          if (r) cudaFree(r);
+          r = nullptr;
+        }
+        return fail(h, HFE_ENOMEM, "extrapolation history");
+      }
+      p = static_cast<double*>(q);
+    }
+    h->extrap_n = 0;
+  }
   double inc_carry = 0.0;
   for (int n = 0; n < n_steps; ++n) {
     int cuts = 0, ok_run = 0;

@@ -99,6 +99,11 @@ struct hfe_handle {
   double* sigma = nullptr;     // n_gp * 6, allocated on demand
   // warm start: the displacement each pass converged to at its requested load factors
   // (warm_t[k], slot k of warm_u, warm_cap slots of n_dof doubles), kept across passes
+  // extrapolated predictor: the last converged (sub)step solutions, newest first (extrap_n
+  // valid of 3 slots of n_dof doubles, allocated when options.predictor >= 2)
+  double* extrap_u[3] = {nullptr, nullptr, nullptr};
+  double extrap_t[3] = {0.0, 0.0, 0.0};
+  int extrap_n = 0;
   int warm_mode = 0;
   double* warm_u = nullptr;
   int warm_cap = 0;

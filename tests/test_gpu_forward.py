@@ -41,11 +41,17 @@ def _sym(s6):
     return material.sym(s6)
 
 
+# initial guess of each step: 1 tangent predictor (default), 0 previous displacement, 2 / 3
+# linear / quadratic extrapolation through the last converged steps
+PREDICTORS = [1, 0, 2, 3]
+
+
+@pytest.mark.parametrize("predictor", PREDICTORS)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_config0_forward(config0_oracle, precision):
+def test_config0_forward(config0_oracle, precision, predictor):
     mesh, bc, mat, ts, uo, ho, infos = config0_oracle
     opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
-    with hfe.from_inputs(mesh, bc, mat, precision=precision, **opts) as s:
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, predictor=predictor, **opts) as s:
         sig = np.empty((mesh.n_el * 8, 6))
         hist = np.empty((7, mesh.n_el * 8))
         u, st = s.forward(ts, sigma_out=sig, hist_out=hist)
@@ -55,12 +61,13 @@ def test_config0_forward(config0_oracle, precision):
     assert np.abs(hist[6] - ho[-1][..., 6].ravel()).max() < (1e-12 if precision == "fp64" else 1e-6)
 
 
+@pytest.mark.parametrize("predictor", [1, 2, 3])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_plate_forward(plate_oracle, precision):
+def test_plate_forward(plate_oracle, precision, predictor):
     mesh, bc, mat, ts, uo, ho, infos = plate_oracle
     assert 0 < infos[-1]["plastic"] < 8 * mesh.n_el      # heterogeneous elastic/plastic mix
     opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
-    with hfe.from_inputs(mesh, bc, mat, precision=precision, **opts) as s:
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, predictor=predictor, **opts) as s:
         sig = np.empty((mesh.n_el * 8, 6))
         u, st = s.forward(ts, sigma_out=sig)
     tol = 1e-10 if precision == "fp64" else 1e-5
@@ -171,14 +178,30 @@ def test_adaptive_stepping_plate_in_few_steps():
     assert rn[0] < 1.0, rn
 
 
-def test_unloading_step_matches_oracle():
+@pytest.mark.parametrize("predictor", PREDICTORS)
+def test_unloading_step_matches_oracle(predictor):
     """Load factors need not increase: tension to 5 %, then back to 3 % (beyond the elastic
     range 2 sigma_y / E, so the unloading yields in reverse), against the oracle's forward on
-    the same factors (FP64 1e-10)."""
+    the same factors (FP64 1e-10); the extrapolations then point the wrong way at the reversal."""
     mesh, bc, mat, _ = inputs.config0_problem(n=2)
     ts = np.array([0.5, 1.0, 0.6])
     us, hs, _ = solver.forward(solver.from_inputs(mesh, bc, mat), ts, rtol=1e-13)
     assert np.abs(hs[3][..., 6] - hs[2][..., 6]).max() > 0.0           # reverse plastic flow
-    with hfe.from_inputs(mesh, bc, mat, precision="fp64", newton_rtol=1e-12, pcg_rtol=1e-13) as s:
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", newton_rtol=1e-12, pcg_rtol=1e-13,
+                         predictor=predictor) as s:
         u, st = s.forward(ts)
     assert _per_step_rel(u, us) < 1e-10
+
+
+def test_extrapolation_history_restarts_after_set_state():
+    """Quadratic extrapolation over two passes of the same loading on one handle: the second
+    pass (after hfe_set_state) starts from the stored state alone, so it repeats the first
+    bit for bit; options.predictor outside 0-3 is refused at hfe_create."""
+    mesh, bc, mat, ts = inputs.config0_problem(n=3, n_steps=5)
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", predictor=3) as s:
+        u1, st1 = s.forward(ts)
+        s.set_state(None, None)
+        u2, st2 = s.forward(ts)
+    assert np.array_equal(u1, u2) and st1["newton_iters"] == st2["newton_iters"]
+    with pytest.raises(hfe.HfeError):
+        hfe.from_inputs(mesh, bc, mat, precision="fp64", predictor=4)
