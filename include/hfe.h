@@ -119,12 +119,14 @@ typedef struct {
                              0: u_{n-1} with the new Dirichlet values;
                              2 / 3: linear / quadratic extrapolation in the load factor through
                              the last 2 / 3 converged (sub)step solutions (Sec. 2.2, automatic
-                             time stepping), lower order while fewer are stored (after
-                             hfe_create, hfe_set_state, hfe_set_load, hfe_set_material or
-                             hfe_set_barlat the stored state is the only one); the Dirichlet
-                             values are those of the new load factor.  Modes 0, 2 and 3 take the
-                             residual at u_{n-1} with the new Dirichlet values as the Newton
-                             reference norm (2 and 3 spend one residual sweep on it) */
+                             time stepping), quadratic with linear while only two are stored,
+                             and the tangent predictor while only one is (after hfe_create,
+                             hfe_set_state, hfe_set_load, hfe_set_material or hfe_set_barlat
+                             the stored state is the only one); the Dirichlet values are those
+                             of the new load factor.  Modes 1-3 take the norm of the tangent
+                             predictor's right-hand side as the Newton reference (2 and 3 form
+                             it without the solve); mode 0 the residual at u_{n-1} with the new
+                             Dirichlet values */
   int ew_forcing;         /* 1: inexact Newton, the CG tolerance of each Newton solve follows the
                              Eisenstat-Walker forcing term (never below pcg_rtol) and a step is
                              accepted only after a correction solved to pcg_rtol; about 2x fewer

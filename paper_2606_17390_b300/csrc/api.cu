@@ -921,22 +921,27 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
   auto one_step = [&](const double t_new, const int marker, const double* guess) -> hfe_status {
       double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
       double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
-      // the tangent predictor's solve is loose; a warm start or an extrapolation makes none
-      bool last_tight = h->opt.predictor != 1 || !h->opt.ew_forcing || guess != nullptr;
-      bool force_tight = false;
-      int backtracks = 0;
       const double t_prev = h->t_state;
-      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u_start, h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
-                         "copy"));
       if (h->opt.predictor >= 2 && h->extrap_n == 0) HFE_TRY(extrap_push(h, t_prev));
       double wex[3];
       const int kex = (h->opt.predictor >= 2 && guess == nullptr) ? extrap_weights(h, t_new, wex) : 1;
-      if (h->opt.predictor == 1) {
+      // the tangent predictor's solve; it also starts an extrapolating run until two solutions
+      // are stored (a step from u_{n-1} with the new Dirichlet values alone can land on another
+      // equilibrium branch of the perforated plate)
+      const bool solve_pred = guess == nullptr && (h->opt.predictor == 1 || (h->opt.predictor >= 2 && kex == 1));
+      // the predictor solve is loose; a warm start or an extrapolation makes none
+      bool last_tight = !solve_pred || !h->opt.ew_forcing;
+      bool force_tight = false;
+      int backtracks = 0;
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->u_start, h->u, sizeof(double) * h->n_dof, cudaMemcpyDeviceToDevice, h->s),
+                         "copy"));
+      if (h->opt.predictor >= 1) {
         // tangent predictor on the converged start-of-step state u_{n-1}:
         // K du = -(R(u_{n-1}) + K du_D - dt f_ext) on the free dofs, du_D = Dirichlet increment,
         // with K and R of the previous step's last Newton iteration (its consistent tangent at
         // u_{n-1}); without them (first step, or after the state was set) the sweep at
-        // (u_{n-1}, h_{n-1})
+        // (u_{n-1}, h_{n-1}).  The norm of its right-hand side is the Newton reference of the
+        // step whatever starts it (this solve, an extrapolation or a warm start).
         if (!h->pred_valid) {
           cudaEventRecord(h->t0, h->s);
           HFE_TRY(sweep(h, h->u, t_prev, HFE_SWEEP_TANGENT, h->R, nullptr));
@@ -962,7 +967,13 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         HFE_TRY(read_status(h));
         ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
         set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
-        if (h->h_sc->norm2 > 0.0 && guess == nullptr) {
+        if (kex > 1) {
+          const unsigned blocks = (unsigned)((h->n_dof + kExtrapBlock - 1) / kExtrapBlock);
+          extrapolate_kernel<<<blocks, kExtrapBlock, 0, h->s>>>(h->u, h->extrap_u[0], h->extrap_u[1],
+                                                              kex == 3 ? h->extrap_u[2] : nullptr, wex[0], wex[1],
+                                                              wex[2], h->freem, h->n_dof);
+          HFE_TRY(cuda_check(h, cudaGetLastError(), "extrapolate"));
+        } else if (h->h_sc->norm2 > 0.0 && solve_pred) {
           cudaEventRecord(h->t0, h->s);
           if (h->opt.ew_forcing) h->pcg_rtol_now = std::max(h->opt.pcg_rtol, 1e-3);   // predictor: rough solve
           h->allow_truncated = true;
@@ -982,7 +993,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         }
       } else {
         set_dirichlet(h->u, h->fixed_dof, h->fixed_val, t_new, h->n_fixed, h->s);
-        if (guess != nullptr || kex > 1) {
+        if (guess != nullptr) {
           // the reference of a step from u_{n-1}: the residual there with the new Dirichlet values
           cudaEventRecord(h->t0, h->s);
           HFE_TRY(sweep(h, h->u, t_new, HFE_SWEEP_RESIDUAL, h->R, nullptr));
@@ -994,14 +1005,6 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
           HFE_TRY(check_sweep_status(h));
           if (h->h_sc->nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite residual");
           ref = std::max(std::sqrt(h->h_sc->norm2), h->opt.newton_atol);
-        }
-        if (kex > 1) {
-          const unsigned blocks = (unsigned)((h->n_dof + kExtrapBlock - 1) / kExtrapBlock);
-          extrapolate_kernel<<<blocks, kExtrapBlock, 0, h->s>>>(h->u, h->extrap_u[0], h->extrap_u[1],
-                                                              kex == 3 ? h->extrap_u[2] : nullptr, wex[0], wex[1],
-                                                              wex[2], h->freem, h->n_dof);
-          HFE_TRY(cuda_check(h, cudaGetLastError(), "extrapolate"));
-          step_scale = 0.0;
         }
       }
       if (guess != nullptr) {
