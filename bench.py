@@ -304,7 +304,9 @@ def main():
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
     ap.add_argument("--forward-predictors", default="1",
-                    help="comma-separated options.predictor values of the forward run (first one reported)")
+                    help="comma-separated options.predictor values of the forward run (first one reported); "
+                         "0 restarts each step from the previous displacement, which inverts the elements "
+                         "next to a platen at this size and is left to cutbacks (very slow)")
     ap.add_argument("--ref-step-s", type=float, default=6.0, help="CPU seconds per reference-arm step")
     ap.add_argument("--barlat-reps", type=int, default=20,
                     help="timed launches of the Barlat line-search map (0 = skip)")
@@ -554,6 +556,8 @@ def main():
                 t0 = time.perf_counter()
                 _, st2 = s2.forward(t2, want_u=False)
                 wall = time.perf_counter() - t0
+            print(f"forward {args.forward_n}^3, predictor {pm}: {wall:.1f} s, {st2['newton_iters']} Newton, "
+                  f"{st2['pcg_iters']} PCG, {st2['substeps']} substeps", file=sys.stderr, flush=True)
             runs[names[pm]] = {"wall_s": wall, "newton_iters": st2["newton_iters"], "pcg_iters": st2["pcg_iters"],
                                "substeps": st2["substeps"], "cutbacks": st2["cutbacks"], "sweeps": st2["sweeps"],
                                "sweep_s": st2["sweep_ms"] * 1e-3, "solve_s": st2["solve_ms"] * 1e-3,
