@@ -303,7 +303,7 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
-    ap.add_argument("--forward-predictors", default="1",
+    ap.add_argument("--forward-predictors", default="2",
                     help="comma-separated options.predictor values of the forward run (first one reported); "
                          "0 restarts each step from the previous displacement, which inverts the elements "
                          "next to a platen at this size and is left to cutbacks (very slow)")

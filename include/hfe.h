@@ -114,10 +114,10 @@ typedef struct {
   double local_tol;       /* relative tolerance of the local yield residual */
   int ckpt_every;         /* adjoint: store the history every k steps, recompute between */
   int predictor;          /* initial guess of each (sub)step's Newton iteration:
-                             1 (default): the tangent predictor u = u_{n-1} + du_D +
-                             K^-1 (-(R + K du_D)) built on the converged start-of-step state;
+                             1: the tangent predictor u = u_{n-1} + du_D + K^-1 (-(R + K du_D))
+                             built on the converged start-of-step state;
                              0: u_{n-1} with the new Dirichlet values;
-                             2 / 3: linear / quadratic extrapolation in the load factor through
+                             2 (default) / 3: linear / quadratic extrapolation in the load factor through
                              the last 2 / 3 converged (sub)step solutions (Sec. 2.2, automatic
                              time stepping), quadratic with linear while only two are stored,
                              and the tangent predictor while only one is (after hfe_create,

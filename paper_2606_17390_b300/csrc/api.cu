@@ -428,7 +428,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->local_maxit = 50;
   o->local_tol = 1e-14;
   o->ckpt_every = 1;
-  o->predictor = 1;
+  o->predictor = 2;
   o->ew_forcing = 0;
   o->pcg_persistent = 1;
   o->adaptive = 1;

@@ -40,6 +40,7 @@ def test_default_options(precision):
     assert o.precision == hfe.PRECISION[precision]
     assert o.newton_rtol == (1e-10 if precision == "fp64" else 1e-7)
     assert o.local_maxit > 0 and o.pcg_maxit > 0 and o.pcg_check_every > 0
+    assert o.predictor == 2     # linear extrapolation (Sec. 2.2, automatic time stepping)
 
 
 def test_null_arguments_rejected_without_device_work():

@@ -41,7 +41,7 @@ def _sym(s6):
     return material.sym(s6)
 
 
-# initial guess of each step: 1 tangent predictor (default), 0 previous displacement, 2 / 3
+# initial guess of each step: 1 tangent predictor, 0 previous displacement, 2 (default) / 3
 # linear / quadratic extrapolation through the last converged steps
 PREDICTORS = [1, 0, 2, 3]
 
