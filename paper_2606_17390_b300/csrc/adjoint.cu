@@ -1037,6 +1037,7 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
                      "copy"));
   h->t_state = 0.0;
   h->pred_valid = false;
+  h->extrap_n = 0;
   w->t_sub.clear();
   w->mark.clear();
   HFE_TRY(copy_in(h, w->ugt, u_target, ndof * n_steps * sizeof(double)));

@@ -922,6 +922,9 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       double ref = -1.0, prev = 0.0, prev_solve = -1.0, eta_prev = 1e-3;
       double step_scale = 0.0;   // fraction of the last correction (in ls.vx) currently applied
       const double t_prev = h->t_state;
+      // the newest stored solution must be the stored state; anything else is a history of
+      // another pass (a state reset that did not clear it) and is dropped
+      if (h->extrap_n > 0 && h->extrap_t[0] != t_prev) h->extrap_n = 0;
       if (h->opt.predictor >= 2 && h->extrap_n == 0) HFE_TRY(extrap_push(h, t_prev));
       double wex[3];
       const int kex = (h->opt.predictor >= 2 && guess == nullptr) ? extrap_weights(h, t_new, wex) : 1;

@@ -68,6 +68,23 @@ def test_adjoint_checkpoint_recompute_matches_full_storage(oracle_uniform):
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_after_forward_repeats_a_fresh_handle(oracle_uniform, precision):
+    """hfe_adjoint restarts from the zero state: after a forward (or another adjoint) on the
+    same handle its forward pass starts like a fresh handle's - the extrapolated predictor
+    does not reach back to the previous pass's solutions - so the results are bit-identical."""
+    mesh, bc, mat, ts, u_gt, th, go, Jo = oracle_uniform
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, theta=th, **opts) as s:
+        J0, g0, st0 = s.adjoint(ts, u_gt)
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, theta=th, **opts) as s:
+        s.forward(ts)
+        J1, g1, st1 = s.adjoint(ts, u_gt)
+        J2, g2, st2 = s.adjoint(ts, u_gt)
+    assert J1 == J0 and J2 == J0 and np.array_equal(g1, g0) and np.array_equal(g2, g0)
+    assert st1["newton_iters"] == st0["newton_iters"] == st2["newton_iters"]
+
+
 def test_adjoint_per_element_vs_oracle():
     mesh, bc, mat, ts, u_gt, th = _problem(per_element=True)
     prob = solver.from_inputs(mesh, bc, mat, th)
