@@ -779,7 +779,6 @@ struct AdjointWork {
   std::vector<void*> mem;
   double *u_all = nullptr, *ckpt = nullptr, *h_prev = nullptr, *h_trial = nullptr, *h_tmp = nullptr;
   double *mu = nullptr, *hbar = nullptr, *thbar = nullptr, *ubar = nullptr, *rhs = nullptr, *R64 = nullptr;
-  double* lam = nullptr;     // lambda of the later (sub)step: the start of the next reverse solve
   double *ugt = nullptr, *Jn = nullptr, *part = nullptr;
   unsigned* ticket = nullptr;
   // F-bar element: K is not symmetric; K^T (values in the same block pattern) and the map
@@ -852,7 +851,6 @@ hfe_status ensure_work(hfe_handle* h, int n_steps) {
   HFE_TRY(aalloc(h, w, &w->ubar, ndof));
   HFE_TRY(aalloc(h, w, &w->rhs, ndof));
   HFE_TRY(aalloc(h, w, &w->R64, ndof));
-  HFE_TRY(aalloc(h, w, &w->lam, ndof));
   HFE_TRY(aalloc(h, w, &w->ugt, ndof * n_steps));
   HFE_TRY(aalloc(h, w, &w->Jn, n_steps));
   HFE_TRY(aalloc(h, w, &w->part, 1024));
@@ -1087,44 +1085,11 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
       transpose_blocks_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, h->s>>>((const double*)Kn, w->tslot, w->KT, nb);
       w->ls.K = w->KT;
     }
-    // Started from the later (sub)step's lambda: lambda = lambda_prev + delta with
-    // K^T delta = rhs - K^T lambda_prev, solved to the relative tolerance that keeps the
-    // absolute target ||K^T lambda - rhs|| <= pcg_rtol ||rhs|| of a solve from zero
-    // (successive steps' adjoint states are close, so the correction needs fewer iterations).
-    double* lam_n = reinterpret_cast<double*>(w->ls.vx);
-    bool from_prev = n < M - 1, solved = true;
-    hfe_status ast = HFE_OK;
-    if (from_prev) {
-      free_norm(w->rhs, h->freem, (int64_t)ndof, h->sc, h->part, h->s, nullptr);
-      ast = read_status(h);
-      const double bn = std::sqrt(h->h_sc->norm2);
-      from_prev = ast == HFE_OK && bn > 0.0 && std::isfinite(bn);
-      if (from_prev) {
-        Csr Kc{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
-        spmv_rows<double>(Kc, (const double*)w->ls.K, h->freem, w->lam, w->R64, h->s);
-        sub_free_kernel<<<(unsigned)((ndof + 255) / 256), 256, 0, h->s>>>(w->rhs, w->R64, h->freem, (int64_t)ndof);
-        free_norm(w->rhs, h->freem, (int64_t)ndof, h->sc, h->part, h->s, nullptr);
-        ast = read_status(h);
-        const double dn = std::sqrt(h->h_sc->norm2);
-        if (ast == HFE_OK) {
-          if (dn <= h->opt.pcg_rtol * bn) solved = false;   // lambda_prev already meets the target
-          else h->pcg_rtol_now = h->opt.pcg_rtol * bn / dn;
-        }
-      }
-    }
-    if (ast == HFE_OK && solved) ast = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
-    h->pcg_rtol_now = 0.0;
+    const hfe_status ast = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
     w->ls.K = Kn;
     h->allow_indefinite = false;
     HFE_TRY(ast);
-    if (solved) adj_pcg += h->h_sc->iters;
-    if (!solved)
-      HFE_TRY(cuda_check(h, cudaMemcpyAsync(lam_n, w->lam, ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
-                         "copy"));
-    else if (from_prev)
-      add_update<double>(lam_n, w->lam, h->freem, (int64_t)ndof, h->s);
-    HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->lam, lam_n, ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
-                       "copy"));
+    adj_pcg += h->h_sc->iters;
     launch_vjp(h, w, false, un, w->h_prev, reinterpret_cast<const double*>(w->ls.vx));   // pass B
     HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->mu, w->hbar, 7 * ngp * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
                        "copy"));
