@@ -77,10 +77,12 @@ __device__ __forceinline__ bool last_block_reduce(double pa, double pb, double* 
 }
 
 // y = Kt x with Kt the matrix whose fixed rows/columns are dropped and whose fixed diagonal is 1.
-// One warp per block row, one lane per 3x3 block (rows with more than 32 blocks loop): the
-// lane loads the block's column, the three x entries it multiplies and its 9 values (the
-// warp's value loads cover the row's contiguous 36-byte blocks), then the warp reduces the
-// three partial row sums.  COLMASK = false skips the column mask: inside CG the fixed
+// A warp serves two block rows per pass, one lane per 3x3 block of each (rows with more than
+// 32 blocks loop): the lane loads the block's column, the three x entries it multiplies and
+// its 9 values (the warp's value loads cover the row's contiguous 36-byte blocks), then the
+// warp reduces the six partial row sums.  This standalone form serves the exported SpMV, the
+// tangent predictor and the chunked CG (pcg_persistent = 0); the one-launch CG solve runs its
+// own eight-lanes-per-row SpMV.  COLMASK = false skips the column mask: inside CG the fixed
 // components of p are exactly zero (r, z and p start at zero there and stay zero).
 // Optionally accumulates x.y (FP64) into a last-CTA reduction that sets alpha = rz / (p.Ap).
 template <typename R, bool COLMASK>
