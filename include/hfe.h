@@ -121,8 +121,9 @@ typedef struct {
                              the last 2 / 3 converged (sub)step solutions (Sec. 2.2, automatic
                              time stepping), quadratic with linear while only two are stored,
                              and the tangent predictor while only one is (after hfe_create,
-                             hfe_set_state, hfe_set_load, hfe_set_material or hfe_set_barlat
-                             the stored state is the only one); the Dirichlet values are those
+                             hfe_set_state, hfe_set_load, hfe_set_material, hfe_set_barlat and
+                             at the start of hfe_adjoint's forward pass the stored state is the
+                             only one); the Dirichlet values are those
                              of the new load factor.  Modes 1-3 take the norm of the tangent
                              predictor's right-hand side as the Newton reference (2 and 3 form
                              it without the solve); mode 0 the residual at u_{n-1} with the new
