@@ -53,7 +53,8 @@ typedef enum {
   HFE_EINVAL = -1,      /* invalid argument (sizes, indices, NULL where required) */
   HFE_ENOMEM = -2,      /* device allocation failed */
   HFE_ECUDA = -3,       /* CUDA runtime error (message in hfe_last_error) */
-  HFE_EDETJ = -4,       /* an element has det(dX/dxi) <= 0 or det F <= 0 */
+  HFE_EDETJ = -4,       /* an element has det(dX/dxi) <= 0 or det F <= 0, or one that is not a
+                           number (non-finite coordinates or displacements) */
   HFE_ENEWTON = 1,      /* global Newton did not converge within newton_maxit */
   HFE_ELOCAL = 2,       /* a local return mapping did not converge (count in stats) */
   HFE_EPCG = 3,         /* Krylov solve did not reach pcg_rtol within pcg_maxit, broke down, or (hfe_solve)

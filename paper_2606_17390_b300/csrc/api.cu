@@ -190,7 +190,8 @@ hfe_status sweep(hfe_handle* h, const double* u_dev, double load, int mode, doub
 
 hfe_status check_sweep_status(hfe_handle* h) {
   const DevStatus& st = *h->h_status;
-  if (st.detj > 0) return fail(h, HFE_EDETJ, std::to_string(st.detj) + " Gauss point(s) with det J <= 0");
+  if (st.detj > 0)
+    return fail(h, HFE_EDETJ, std::to_string(st.detj) + " Gauss point(s) with det J <= 0 or not a number");
   if (st.nonfinite > 0) return fail(h, HFE_ENONFINITE, "non-finite internal force");
   if (st.local_fail > 0)
     return fail(h, HFE_ELOCAL, std::to_string(st.local_fail) + " local return mapping(s) hit local_maxit");
