@@ -150,3 +150,24 @@ def test_identify_with_warm_start():
     assert res.warm_passes > 0
     assert res.J < 1e-8 * res.history[0][0], (res.J, res.message)
     assert np.allclose(res.theta[idx], th_true[idx], rtol=1e-4), (res.theta[idx], res.message)
+
+
+def test_record_grows_and_keeps_its_slots():
+    """A longer pass grows the record (reallocated, the recorded slots copied over): after a
+    2-step pass to (0.5, 1.0) a 4-step pass to (0.5, 1.0, 1.25, 1.5) starts its first two steps
+    from the slots recorded before the growth - converged at their first sweep, bit-identical
+    to the 2-step pass - and the last two cold; a repeat of the 4-step pass starts warm at
+    every step and repeats it bit for bit."""
+    mesh, bc, mat, _ = _problem()
+    t2, t4 = np.array([0.5, 1.0]), np.array([0.5, 1.0, 1.25, 1.5])
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", **FP64) as s:
+        s.set_warm_start("use")
+        u2, st_a = s.forward(t2)
+        s.set_state(None, None)
+        u4, st_b = s.forward(t4)
+        s.set_state(None, None)
+        u4w, st_c = s.forward(t4)
+    assert st_a["warm_steps"] == 0 and st_b["warm_steps"] == 2 and st_b["warm_retries"] == 0
+    assert np.array_equal(u4[:2], u2)
+    assert st_c["warm_steps"] == 4 and st_c["newton_iters"] == 0
+    assert np.array_equal(u4w, u4)
