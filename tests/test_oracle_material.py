@@ -161,11 +161,23 @@ def _dlog_via_expm_frechet(C, X):
     return 0.5 * np.linalg.solve(Mx, X.ravel()).reshape(3, 3)
 
 
+def _d2_half_log_block(C, X, Y):
+    """Second Frechet derivative of 1/2 log at C in the directions X, Y, without an
+    eigen-decomposition: the top-right block of log of the block upper-triangular matrix
+    [[C, X, Y, 0], [0, C, 0, Y], [0, 0, C, X], [0, 0, 0, C]] (Higham and Relton, SIAM J.
+    Matrix Anal. Appl. 35 (2014), Thm. 3.5), by scipy's inverse scaling-and-squaring logm."""
+    Z = np.zeros((3, 3))
+    B = np.block([[C, X, Y, Z], [Z, C, Z, Y], [Z, Z, C, X], [Z, Z, Z, C]])
+    return 0.5 * np.real(scipy.linalg.logm(B)[0:3, 9:12])
+
+
 @pytest.mark.parametrize("kind", ["random", "identity", "repeated", "near_repeated"])
 def test_spectral_derivatives_vs_expm_frechet(kind):
     """Daleckii-Krein first derivative (P_L) equals the inverse of the Frechet derivative of
     the matrix exponential at log C (a route with no eigen-decomposition); the second
-    derivative equals a central difference of the first; eps equals 1/2 logm(C)."""
+    derivative equals the block-matrix second Frechet derivative of 1/2 log (no
+    eigen-decomposition either) and a central difference of the first; eps equals
+    1/2 logm(C)."""
     rng = np.random.default_rng(3)
     if kind == "random":
         Fm = np.eye(3) + 0.2 * rng.uniform(-1, 1, (3, 3))
@@ -193,6 +205,7 @@ def test_spectral_derivatives_vs_expm_frechet(kind):
     d2_fd = (M.dk1(wp, Qp, X[None])[0] - M.dk1(wm, Qm, X[None])[0]) / (2 * hd)
     d2 = M.dk2(w, Q, X[None], Y[None])[0]
     assert np.abs(d2 - d2_fd).max() < 1e-7 * max(1.0, np.abs(d2).max())
+    assert np.abs(d2 - _d2_half_log_block(C, X, Y)).max() < 1e-12 * max(1.0, np.abs(d2).max())
 
 
 @pytest.mark.parametrize("hardening", ["swift", "voce"])
