@@ -538,6 +538,10 @@ def main():
         adjoint = {"workload": f"config {args.adjoint_config}: perforated plate {nx}x{nx // 2} ({m3.n_el} elements, "
                                f"{m3.n_dof} dofs), {args.adjoint_steps} steps, {what}",
                    "forward_s": t_fwd, "gradient_call_s": t_adj, "reverse_s": ast["solve_ms"] * 1e-3,
+                   "gradient_forward_pass_s": ast["sweep_ms"] * 1e-3,
+                   "gradient_pcg_iters": {"forward_newton": ast["pcg_iters"] - ast["refine_pcg_iters"]
+                                          - ast["reverse_pcg_iters"], "fp64_refinement": ast["refine_pcg_iters"],
+                                          "reverse": ast["reverse_pcg_iters"]},
                    "gradient_over_forward": t_adj / t_fwd, "reverse_over_forward": ast["solve_ms"] * 1e-3 / t_fwd,
                    "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"],
                    "forward_substeps": fst["substeps"], "gradient_substeps": ast["substeps"],

@@ -173,6 +173,10 @@ typedef struct {
   int64_t warm_steps;     /* requested load steps whose Newton iteration started from the
                              warm-start record (hfe_set_warm_start) */
   int64_t warm_retries;   /* of those, attempts that failed and were retried cold */
+  int64_t refine_pcg_iters;  /* hfe_adjoint on a mixed handle: CG iterations of the FP64
+                                refinement that ends each forward step (part of pcg_iters) */
+  int64_t reverse_pcg_iters; /* hfe_adjoint: Krylov iterations of the reverse pass (part of
+                                pcg_iters) */
 } hfe_stats;
 
 /* Sizes of the internal data (for tests and benchmarks). */

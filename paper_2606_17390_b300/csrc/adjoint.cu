@@ -1123,6 +1123,8 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
   if (stats) {
     *stats = fst;
     stats->pcg_iters = fst.pcg_iters + hook.pcg_iters + adj_pcg;
+    stats->refine_pcg_iters = hook.pcg_iters;
+    stats->reverse_pcg_iters = adj_pcg;
     float fms = 0.f, bms = 0.f;
     cudaEventElapsedTime(&fms, ta, tb);
     cudaEventElapsedTime(&bms, tb, tc);

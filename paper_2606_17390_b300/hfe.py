@@ -57,7 +57,7 @@ class Stats(C.Structure):
                 ("steps_done", C.c_int32), ("last_residual", C.c_double), ("sweep_ms", C.c_double),
                 ("solve_ms", C.c_double), ("total_ms", C.c_double), ("bicgstab_solves", C.c_int64),
                 ("substeps", C.c_int64), ("cutbacks", C.c_int64), ("warm_steps", C.c_int64),
-                ("warm_retries", C.c_int64)]
+                ("warm_retries", C.c_int64), ("refine_pcg_iters", C.c_int64), ("reverse_pcg_iters", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

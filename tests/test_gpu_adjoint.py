@@ -56,6 +56,11 @@ def test_adjoint_uniform_vs_oracle(oracle_uniform, precision):
         J, g, st = s.adjoint(ts, u_gt)
     assert abs(J - Jo) < 1e-8 * Jo
     _check(g[0], go)
+    # iteration counters: the reverse pass solves once per step; only the mixed forward
+    # ends its steps with the FP64 refinement
+    assert st["reverse_pcg_iters"] >= len(ts)
+    assert (st["refine_pcg_iters"] > 0) == (precision == "mixed")
+    assert st["pcg_iters"] >= st["reverse_pcg_iters"] + st["refine_pcg_iters"]
 
 
 def test_adjoint_checkpoint_recompute_matches_full_storage(oracle_uniform):
