@@ -8,6 +8,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -58,3 +59,20 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert len(lines) == 1
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
+
+
+def test_all_cores_cpu_baseline_spawned_pool():
+    """The all-cores CPU baseline: a spawned pool of 2 workers sweeps equal chunks of random
+    elements of the bench state (local node numbering) with the oracle, and one worker's
+    chunk gives the same element results as the oracle on the global mesh."""
+    import bench
+    from oracle import element
+    mesh, _, mat, u, hist = bench.workload(6)
+    r, desc, cores, dt = bench.cpu_oracle_rate_all_cores(mesh, mat, u, hist, per_worker_s=0.2, cores=2)
+    assert cores == 2 and r > 0 and dt > 0 and "2 spawned worker processes" in desc
+    hist_el = np.ascontiguousarray(hist.T.reshape(mesh.n_el, 8, 7))
+    els = np.array([3, 17, 40, 101])
+    X, conn, uu, h, th, hard = bench._local_chunk(mesh, u, hist_el, els, mat.theta_vector(), mat.hardening)
+    loc = element.element_sweep(X, conn, uu, h, th, hard)
+    glo = element.element_sweep(mesh.X, mesh.conn[els].astype(np.int64), u, hist_el[els], th, hard)
+    assert np.array_equal(loc["Re"], glo["Re"]) and np.array_equal(loc["Ke"], glo["Ke"])
