@@ -204,6 +204,28 @@ def cpu_oracle_rate_all_cores(mesh, mat, u, hist, per_worker_s=6.0, seed=0, core
     return 8 * k * cores / wall, desc, cores, wall
 
 
+def config1_forward_section(stream):
+    """Config 1's forward (perforated 200 x 100 x 4 plate, Voce, 20 load steps) in FP32-mixed
+    and in FP64 on the same inputs: wall time and Newton / CG counts of each; a run that fails
+    reports its error instead of ending the benchmark."""
+    from paper_2606_17390_b300 import hfe
+    m1, bc1, mat1, t1 = inputs.config1_problem()
+    out = {"workload": f"config 1: perforated plate 200x100x4 ({m1.n_el} elements, {m1.n_dof} dofs), Voce, "
+                       f"{len(t1)} steps"}
+    for prec in ("mixed", "fp64"):
+        try:
+            with hfe.from_inputs(m1, bc1, mat1, precision=prec, stream=stream.cuda_stream) as s1:
+                t0 = time.perf_counter()
+                _, st = s1.forward(t1, want_u=False)
+                out[prec] = {"wall_s": time.perf_counter() - t0, "newton_iters": st["newton_iters"],
+                             "pcg_iters": st["pcg_iters"], "substeps": st["substeps"], "cutbacks": st["cutbacks"]}
+        except Exception as e:
+            out[prec] = {"error": f"{type(e).__name__}: {e}"[:200]}
+    if "wall_s" in out.get("mixed", {}) and "wall_s" in out.get("fp64", {}):
+        out["fp64_over_mixed"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+    return out
+
+
 def barlat_map_section(reps, stream, dev, with_cpu):
     """Device time of hfe_barlat_return_map on the App. B robustness map and on a 64-times
     larger batch (CUDA events on the launching stream, after 3 warm-up launches), outcome
@@ -357,6 +379,8 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
+    ap.add_argument("--config1-forward", action="store_true",
+                    help="also run config 1's full-size forward in FP32-mixed and in FP64")
     ap.add_argument("--forward-predictors", default="2",
                     help="comma-separated options.predictor values of the forward run (first one reported); "
                          "0 restarts each step from the previous displacement, which inverts the elements "
@@ -641,6 +665,8 @@ def main():
     if args.barlat_fe_n > 0:
         barlat_fe = barlat_fe_section(args.barlat_fe_n, stream, dev)
 
+    config1 = config1_forward_section(stream) if args.config1_forward else None
+
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist)
@@ -663,7 +689,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
-                "pcg": pcg, "adjoint": adjoint, "forward": forward, "fbar_sweep": fbar,
+                "pcg": pcg, "adjoint": adjoint, "forward": forward, "config1_forward": config1, "fbar_sweep": fbar,
                 "barlat_map": barlat, "barlat_fe_sweep": barlat_fe,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
