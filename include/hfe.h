@@ -115,20 +115,20 @@ typedef struct {
   double local_tol;       /* relative tolerance of the local yield residual */
   int ckpt_every;         /* adjoint: store the history every k steps, recompute between */
   int predictor;          /* initial guess of each (sub)step's Newton iteration:
+                             2 (default) / 3: linear / quadratic extrapolation in the load
+                             factor through the last 2 / 3 converged (sub)step solutions
+                             (Sec. 2.2, automatic time stepping); linear while only two are
+                             stored, and the tangent predictor while only the stored state is
+                             known (after hfe_create, hfe_set_state, hfe_set_load,
+                             hfe_set_material, hfe_set_barlat and at the start of
+                             hfe_adjoint's forward pass);
                              1: the tangent predictor u = u_{n-1} + du_D + K^-1 (-(R + K du_D))
-                             built on the converged start-of-step state;
-                             0: u_{n-1} with the new Dirichlet values;
-                             2 (default) / 3: linear / quadratic extrapolation in the load factor through
-                             the last 2 / 3 converged (sub)step solutions (Sec. 2.2, automatic
-                             time stepping), quadratic with linear while only two are stored,
-                             and the tangent predictor while only one is (after hfe_create,
-                             hfe_set_state, hfe_set_load, hfe_set_material, hfe_set_barlat and
-                             at the start of hfe_adjoint's forward pass the stored state is the
-                             only one); the Dirichlet values are those
-                             of the new load factor.  Modes 1-3 take the norm of the tangent
-                             predictor's right-hand side as the Newton reference (2 and 3 form
-                             it without the solve); mode 0 the residual at u_{n-1} with the new
-                             Dirichlet values */
+                             built on the converged start-of-step state, at every step;
+                             0: u_{n-1} with the new Dirichlet values.
+                             The Dirichlet values are those of the new load factor.  Modes 1-3
+                             take the norm of the tangent predictor's right-hand side as the
+                             Newton reference (2 and 3 form it without the solve); mode 0 the
+                             residual at u_{n-1} with the new Dirichlet values */
   int ew_forcing;         /* 1: inexact Newton, the CG tolerance of each Newton solve follows the
                              Eisenstat-Walker forcing term (never below pcg_rtol) and a step is
                              accepted only after a correction solved to pcg_rtol; about 2x fewer
