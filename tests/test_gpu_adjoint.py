@@ -194,3 +194,21 @@ def test_adjoint_through_adaptive_substeps():
     assert st["cutbacks"] > 0
     assert abs(J - solver.objective(us, u_gt)) < 1e-9 * J
     _check(g[0], go)
+
+
+def test_gradcheck_tool_on_the_gpu_path(oracle_uniform):
+    """gradcheck.objective drives the GPU forward: its J equals hfe_adjoint's J, and the
+    finite-difference check of the GPU adjoint gradient along D (relative steps) has its
+    minimum below 1e-5 of g.D and a larger error at both ends of the step range."""
+    from paper_2606_17390_b300 import gradcheck
+    mesh, bc, mat, ts, u_gt, th, go, Jo = oracle_uniform
+    idx = np.array([8, 9])
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", theta=th, newton_rtol=1e-13, pcg_rtol=1e-14) as s:
+        Ja, g, _ = s.adjoint(ts, u_gt)
+        J = gradcheck.objective(s, ts, u_gt)
+        assert abs(J(th) - Ja) <= 1e-12 * Ja
+        res, ref = gradcheck.fd_check(J, g[0][idx], th, steps=gradcheck.PAPER_STEPS[::2], index=idx,
+                                      scale=np.abs(th[idx]))
+    E = np.array([r["E"] for r in res])
+    k = int(E.argmin())
+    assert E[k] < 1e-5 * abs(ref) and E[0] > E[k] and E[-1] > E[k], (E, ref)
