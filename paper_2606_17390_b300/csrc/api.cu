@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "stepping.h"
 
 using namespace hfe;
 
@@ -844,23 +845,10 @@ hfe_status extrap_push(hfe_handle* h, double t) {
                     "copy");
 }
 
-// the number of stored solutions the extrapolation to t_new uses (1 = none: u_{n-1} stays),
-// and their Lagrange weights; points closer than 1e-12 in the load factor lower the order
+// the number of stored solutions the extrapolation to t_new uses (1 = none: u_{n-1} stays)
+// and their Lagrange weights
 int extrap_weights(const hfe_handle* h, double t_new, double w[3]) {
-  int k = std::min(h->extrap_n, h->opt.predictor == 2 ? 2 : 3);
-  const double* tk = h->extrap_t;
-  auto close = [](double a, double b) { return std::fabs(a - b) <= 1e-12 * std::max(1.0, std::fabs(a)); };
-  if (k == 3 && (close(tk[0], tk[2]) || close(tk[1], tk[2]))) k = 2;
-  if (k >= 2 && close(tk[0], tk[1])) k = 1;
-  w[0] = 1.0;
-  w[1] = w[2] = 0.0;
-  for (int i = 0; i < k; ++i) {
-    double l = 1.0;
-    for (int j = 0; j < k; ++j)
-      if (j != i) l *= (t_new - tk[j]) / (tk[i] - tk[j]);
-    w[i] = l;
-  }
-  return k;
+  return extrapolation_weights(h->extrap_t, h->extrap_n, h->opt.predictor == 2 ? 2 : 3, t_new, w);
 }
 }  // namespace
 
