@@ -150,6 +150,18 @@ def cpu_oracle_rate(mesh, mat, u, hist, target_s=12.0, seed=0):
     return 8 * k / dt, f"oracle tangent sweep + assembly of {k} random elements ({8 * k} Gauss points) of the same state", 1, dt
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def _oracle_worker_init():
     from oracle import element, solver  # noqa: F401  (imported once per worker)
 
@@ -181,8 +193,9 @@ def cpu_oracle_rate_all_cores(mesh, mat, u, hist, per_worker_s=6.0, seed=0, core
     Gauss points of all chunks over the wall time of the timed map (workers already started
     and their imports done).  Returns (GP/s, description, cores, seconds)."""
     import multiprocessing
-    if cores is None:
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    if cores is None:   # the permitted cores, at most 64 (the host is shared with other jobs)
+        avail = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        cores = max(1, min(64, avail))
     theta, hardening = mat.theta_vector(), mat.hardening
     hist_el = np.ascontiguousarray(hist.T.reshape(mesh.n_el, 8, 7))
     rng = np.random.default_rng(seed)
@@ -670,10 +683,12 @@ def main():
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist)
-        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt,
+               "cpu_model": cpu_model()}
         try:
             r, desc, cores, dt = cpu_oracle_rate_all_cores(mesh, mat, u, hist)
-            cpu_all = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
+            cpu_all = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt,
+                       "cpu_model": cpu_model()}
         except Exception as e:  # the single-thread baseline above stands on its own
             cpu_all = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
 
