@@ -365,7 +365,8 @@ def reference_arm(args, rank):
             "config": {"workload": f"hex8 cube {args.n}^3, {mesh.n_dof} dofs, {8 * mesh.n_el} Gauss points, "
                                    "Hill-48 + Swift, clamped compression, mid-step state; CPU oracle on a sample",
                        "n_el": mesh.n_el, "n_dof": mesh.n_dof, "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
