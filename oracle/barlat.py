@@ -54,7 +54,7 @@ P_DEV = np.array([[2, -1, -1, 0, 0, 0], [-1, 2, -1, 0, 0, 0], [-1, -1, 2, 0, 0, 
 def transform_matrix(c):
     """The 6x6 matrix of App. A.2 from (c12, c13, c21, c23, c31, c32, c44, c55, c66)."""
     c12, c13, c21, c23, c31, c32, c44, c55, c66 = c
-    C = np.zeros((6, 6))
+    C = np.zeros((6, 6), dtype=np.result_type(*c, np.float64))   # complex coefficients allowed
     C[0, 1], C[0, 2] = -c12, -c13
     C[1, 0], C[1, 2] = -c21, -c23
     C[2, 0], C[2, 1] = -c31, -c32
@@ -81,6 +81,8 @@ class Barlat:
     material frame Theta (3x3, columns = material axes)."""
 
     def __init__(self, c1, c2, m, Theta=None):
+        self.c1 = np.asarray(c1)
+        self.c2 = np.asarray(c2)
         self.C1 = transform_matrix(c1)
         self.C2 = transform_matrix(c2)
         self.m = int(m)
@@ -270,8 +272,34 @@ def cpp_tangent(model, E, nu, hardening, h, y, Ttr, alpn):
     return np.linalg.solve(J, rhs)[:, :6, :]
 
 
+# ------------------------------------------------------------------ parameters
+N_PARAMS = 23   # c' (9), c'' (9), E, nu, the three hardening parameters
+
+
+def params(model, E, nu, h):
+    """The parameter vector p = (c' (9), c'' (9), E, nu, h (3)) of an isotropic-elastic model."""
+    return np.concatenate([model.c1, model.c2, [E, nu], np.asarray(h, dtype=np.float64)]).astype(np.float64)
+
+
+def unpack(p, m, Theta=None):
+    """(model, E, nu, h) from a parameter vector (complex entries allowed)."""
+    return Barlat(p[0:9], p[9:18], m, Theta), p[18], p[19], p[20:23]
+
+
+def _cs_params(fun, p, nout, B):
+    """d fun / d p (B, nout, n_p) by complex step for parameters shared by all B points:
+    fun(p) (B, nout) with the complex parameter vector p."""
+    from .material import CS_H
+    J = np.empty((B, nout, p.size))
+    for j in range(p.size):
+        pc = p.astype(np.complex128)
+        pc[j] += 1j * CS_H
+        J[:, :, j] = np.imag(fun(pc)) / CS_H
+    return J
+
+
 # ------------------------------------------------------------------ strain-driven update
-def local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives=True, kmax=None):
+def local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives=True, kmax=None, param_derivatives=False):
     """Stress update of Algorithm global_stress_update (App. C), steps 2-6, for this model,
     from the total log strain: T_tr = E : (eps - eps_p,n), the elastic test (reading R10),
     the projection `cpp`, and the recovery eps_p,n+1 = eps_p,n + dgamma N(T), T = E : (eps -
@@ -279,7 +307,10 @@ def local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives=True, k
 
     Returns dict(z (B, 13) = (T, eps_p,n+1, alpha_n+1), dgamma, plastic, iters, converged, ftr)
     and, if derivatives, dz (B, 13, 13) = dz/dp for p = (eps, eps_p,n, alpha_n) by implicit
-    differentiation of the converged local system (App. D)."""
+    differentiation of the converged local system (App. D); with param_derivatives (isotropic
+    elasticity only) dz is (B, 13, 13 + N_PARAMS), the last columns dz/dq for the material
+    parameters q = params(model, E, nu, h), by the same implicit differentiation with the
+    parameter derivatives of G and z taken by complex step."""
     from .material import LOCAL_KMAX
     kmax = LOCAL_KMAX if kmax is None else kmax
     eps = np.asarray(eps, dtype=np.float64)
@@ -331,6 +362,32 @@ def local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives=True, k
         zy = complex_step_jacobian(lambda yy: z_of(yy, pP), y, 13)
         zp = complex_step_jacobian(lambda pc: z_of(y.astype(pc.dtype), pc), pP, 13)
         dz[P] = zy @ ydot + zp
+    if param_derivatives:
+        if np.ndim(E) == 4:
+            raise NotImplementedError("parameter derivatives are written for isotropic elasticity")
+        q = params(model, E, nu, h)
+        m, Th = model.m, model.Theta
+        dq = np.empty((B, 13, N_PARAMS))
+        if Eidx.size:
+            pE = p_all[Eidx]
+
+            def z_el_q(qc):
+                _, Ec, nuc, _ = unpack(qc, m, Th)
+                return np.concatenate([elastic(Ec, nuc, pE[:, 0:6] - pE[:, 6:12]), pE[:, 6:12], pE[:, 12:13]], axis=1)
+            dq[Eidx] = _cs_params(z_el_q, q, 13, Eidx.size)
+        if P.size:
+            def G_q(qc):
+                mc, Ec, nuc, hc = unpack(qc, m, Th)
+                return residual(mc, Ec, nuc, hardening, hc, y, elastic(Ec, nuc, pP[:, 0:6] - pP[:, 6:12]), pP[:, 12])
+
+            def z_q(qc):
+                mc, Ec, nuc, _ = unpack(qc, m, Th)
+                N, _ = mc.flow(y[:, :6])
+                epnew = pP[:, 6:12] + y[:, 7:8] * N
+                return np.concatenate([elastic(Ec, nuc, pP[:, 0:6] - epnew), epnew, y[:, 6:7]], axis=1)
+            ydot_q = -np.linalg.solve(Jy, _cs_params(G_q, q, 8, P.size))
+            dq[P] = zy @ ydot_q + _cs_params(z_q, q, 13, P.size)
+        dz = np.concatenate([dz, dq], axis=2)
     out["dz"] = dz
     return out
 
@@ -338,6 +395,7 @@ def local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives=True, k
 def local(model, E, nu, hardening, h, kmax=None):
     """The update above as the callable (eps, epn, alpn, derivatives) that
     material.gauss_point takes in place of the Hill-48 update."""
-    def f(eps, epn, alpn, derivatives=True):
-        return local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives, kmax)
+    def f(eps, epn, alpn, derivatives=True, param_derivatives=False):
+        return local_update(model, E, nu, hardening, h, eps, epn, alpn, derivatives, kmax, param_derivatives)
+    f.n_params = N_PARAMS
     return f

@@ -392,8 +392,9 @@ def gauss_point(F, epn, alpn, theta, hardening, Theta=None, jacobians="tangent",
     dP/dh_old, dP/dtheta, dh/dF, dh/dh_old, dh/dtheta for the adjoint).
     History h = (eps_p (6), alpha).  local: None for the Hill-48 update, or another model's
     strain-driven update (eps, epn, alpn, derivatives) -> dict(z, dz, ...) with dz over
-    (eps, eps_p,n, alpha_n) (e.g. barlat.local); theta, hardening and Theta are then unused
-    and jacobians "all" is not available.
+    (eps, eps_p,n, alpha_n) (e.g. barlat.local); theta, hardening and Theta are then unused,
+    and jacobians "all" needs a model that declares `n_params` and returns the parameter
+    columns of dz (dP/dtheta and dh/dtheta then run over that model's parameters).
     """
     F = np.asarray(F, dtype=np.float64)
     B = F.shape[0]
@@ -408,9 +409,10 @@ def gauss_point(F, epn, alpn, theta, hardening, Theta=None, jacobians="tangent",
         lu = local_update(eps, np.asarray(epn, float), np.asarray(alpn, float), theta, hardening,
                           Theta, derivatives=jacobians is not None)
     else:
-        if jacobians == "all":
-            raise NotImplementedError("parameter derivatives are available for the Hill-48 update only")
-        lu = local(eps, np.asarray(epn, float), np.asarray(alpn, float), derivatives=jacobians is not None)
+        if jacobians == "all" and not hasattr(local, "n_params"):
+            raise NotImplementedError("this local model provides no parameter derivatives")
+        extra = {"param_derivatives": True} if jacobians == "all" else {}
+        lu = local(eps, np.asarray(epn, float), np.asarray(alpn, float), derivatives=jacobians is not None, **extra)
     z = lu["z"]
     T = sym(z[:, :6])
     S = 2.0 * dk1(w, Q, T)                       # S = P_L : T   (Eq. proj_lagrange)
@@ -453,8 +455,8 @@ def gauss_point(F, epn, alpn, theta, hardening, Theta=None, jacobians="tangent",
 
     out["dP_dh"] = through_T(dz[:, :, 6:13])
     out["dh_dh"] = dz[:, 6:13, 6:13]
-    out["dP_dtheta"] = through_T(dz[:, :, 13:24])
-    out["dh_dtheta"] = dz[:, 6:13, 13:24]
+    out["dP_dtheta"] = through_T(dz[:, :, 13:])
+    out["dh_dtheta"] = dz[:, 6:13, 13:]
     return out
 
 

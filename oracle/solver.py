@@ -186,17 +186,27 @@ def _dofs_from_F_cotangent(prob, es, Fbar):
     return assemble_R(prob, ue)
 
 
+def n_params(prob):
+    """Length of the parameter vector the adjoint differentiates: Hill-48's 11, or the local
+    model's own (e.g. Barlat's 23; uniform parameters only)."""
+    if prob.local is None:
+        return 11
+    if not hasattr(prob.local, "n_params"):
+        raise NotImplementedError("this local model provides no parameter derivatives")
+    return prob.local.n_params
+
+
 def adjoint(prob, t_steps, us, hs, u_gt, w=1.0, per_element=False):
-    """dJ/dtheta by the discrete adjoint; (11,) for uniform theta, (n_el, 11) if per_element."""
+    """dJ/dtheta by the discrete adjoint; (n_p,) for uniform parameters, (n_el, n_p) if
+    per_element, with n_p = n_params(prob) (Hill-48's theta, or the local model's vector)."""
     if prob.fbar:
         raise NotImplementedError("the adjoint of the F-bar element is not part of the oracle")
-    if prob.local is not None:
-        raise NotImplementedError("the adjoint is written for the Hill-48 parameters")
+    npar = n_params(prob)
     free = free_mask(prob)
     n_el = prob.n_el
     N = len(t_steps)
     mu = np.zeros((n_el, 8, 7))
-    gth = np.zeros((n_el, 11))
+    gth = np.zeros((n_el, npar))
     for n in range(N - 1, -1, -1):
         R, K, es = residual(prob, us[n], hs[n], t_steps[n], jacobians="all")
         gp = es["gp"]
@@ -211,21 +221,21 @@ def adjoint(prob, t_steps, us, hs, u_gt, w=1.0, per_element=False):
             np.einsum("bj,bjk->bk", mu_f, gp["dh_dh"])
         tbar = np.einsum("biJ,biJj->bj", Pbar, gp["dP_dtheta"]) + \
             np.einsum("bj,bjk->bk", mu_f, gp["dh_dtheta"])
-        gth += tbar.reshape(n_el, 8, 11).sum(axis=1)
+        gth += tbar.reshape(n_el, 8, npar).sum(axis=1)
         mu = hbar.reshape(n_el, 8, 7)
     return gth if per_element else gth.sum(axis=0)
 
 
 def direct_sensitivity(prob, t_steps, us, hs, u_gt, dtheta, w=1.0):
-    """dJ/dtheta . dtheta by forward (tangent) propagation; dtheta (11,) or (n_el, 11)."""
+    """dJ/dtheta . dtheta by forward (tangent) propagation; dtheta (n_p,) or (n_el, n_p) with
+    n_p = n_params(prob)."""
     if prob.fbar:
         raise NotImplementedError("the sensitivity of the F-bar element is not part of the oracle")
-    if prob.local is not None:
-        raise NotImplementedError("the sensitivity is written for the Hill-48 parameters")
+    npar = n_params(prob)
     free = free_mask(prob)
     n_el = prob.n_el
-    dth = np.broadcast_to(np.asarray(dtheta, dtype=np.float64), (n_el, 11))
-    dth_gp = np.repeat(dth[:, None, :], 8, axis=1).reshape(-1, 11)
+    dth = np.broadcast_to(np.asarray(dtheta, dtype=np.float64), (n_el, npar))
+    dth_gp = np.repeat(dth[:, None, :], 8, axis=1).reshape(-1, npar)
     hdot = np.zeros((n_el * 8, 7))
     dJ = 0.0
     for n in range(len(t_steps)):
