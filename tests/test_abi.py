@@ -1,9 +1,11 @@
-"""The C-ABI library loads and exports every entry point that include/hfe.h declares, and the
-host-only entry point fills the documented defaults (CPU only, no compute call)."""
+"""The C-ABI library loads and exports every entry point that include/hfe.h declares, the
+host-only entry points fill the documented defaults, the binding's structs match the
+header's layouts and its marshalling is consistent (CPU only, no compute call)."""
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2606_17390_b300 import hfe
@@ -84,3 +86,30 @@ def test_ctypes_mirrors_match_the_header_layout(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_marshalling_without_device_work():
+    """Host-side argument marshalling of the binding: parameter arrays (uniform or per element,
+    material frames dropped when they are the identity, one frame repeated for per-element
+    parameters), the Barlat material record, and the local-projection options, whose Python
+    defaults equal the library's hfe_default_cpp_options."""
+    th = np.arange(11.0)
+    a, T = hfe.material_arrays(th)
+    assert a.shape == (1, 11) and T is None
+    a, T = hfe.material_arrays(np.tile(th, (3, 1)), np.eye(3))
+    assert a.shape == (3, 11) and T is None
+    R = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    a, T = hfe.material_arrays(np.tile(th, (3, 1)), R)
+    assert T.shape == (3, 9) and np.array_equal(T[2], R.ravel())
+    from paper_2606_17390_b300 import inputs
+    m = inputs.barlat_verification_material()
+    s = hfe.barlat_material(m)
+    assert list(s.c1) == list(m.c1) and list(s.c2) == list(m.c2) and s.m == m.m
+    assert s.orthotropic == 0 and list(s.Theta) == list(np.eye(3).ravel())
+    L = hfe.lib()
+    o = hfe.CppOptions()
+    L.hfe_default_cpp_options.argtypes = [ctypes.POINTER(hfe.CppOptions)]
+    L.hfe_default_cpp_options.restype = None
+    L.hfe_default_cpp_options(ctypes.byref(o))
+    p = hfe.cpp_options()
+    assert [getattr(o, f) for f, _ in o._fields_] == [getattr(p, f) for f, _ in p._fields_]
