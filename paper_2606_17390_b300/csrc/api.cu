@@ -873,6 +873,7 @@ hfe_status warm_reserve(hfe_handle* h, int n_steps) {
       }
       cudaFree(h->warm_u);
     }
+    h->device_bytes += sizeof(double) * (size_t)(n_steps - h->warm_cap) * h->n_dof;
     h->warm_u = nu;
     h->warm_cap = n_steps;
   }
@@ -887,6 +888,7 @@ extern "C" hfe_status hfe_set_warm_start(hfe_handle* h, int mode) {
     StreamScope scope(h);
     cudaStreamSynchronize(h->s);
     cudaFree(h->warm_u);
+    h->device_bytes -= sizeof(double) * (size_t)h->warm_cap * h->n_dof;
     h->warm_u = nullptr;
     h->warm_cap = 0;
     h->warm_t.clear();
@@ -1156,6 +1158,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
       }
       p = static_cast<double*>(q);
     }
+    h->device_bytes += 3 * sizeof(double) * (size_t)h->n_dof;
     h->extrap_n = 0;
   }
   double inc_carry = 0.0;
