@@ -286,24 +286,26 @@ hfe_status hfe_set_warm_start(hfe_handle* h, int mode);
 hfe_status hfe_adjoint(hfe_handle* h, int n_steps, const double* t, const double* u_target,
                        double w, double* J_out, double* grad_out, hfe_stats* stats);
 
-/* ||r_free||_2 = sqrt(sum of r[d]^2 over the dofs with free_mask[d] != 0), the FP64 norm of
- * the global Newton convergence test (Sec. 2.2.5), without a handle and without allocating
- * any device memory: its reduction scratch is a static device array of the library (8,448
- * bytes per device).  The paper has no counterpart; it serves callers that cannot allocate
- * (device memory held by a caching allocator or exhausted, e.g. on an error path).
+/* ||r_free||_2 = sqrt(sum of r[d]^2 over the dofs with free_mask[d] != 0): the FP64 norm the
+ * Newton iteration tests for convergence (the same quantity hfe_gp_sweep returns), here
+ * without a handle and without allocating any device memory: its reduction scratch is a
+ * static device array of the library (8,448 bytes per device, held until the process exits).
+ * The paper has no counterpart.  It serves callers that cannot allocate: device memory held
+ * by a caching allocator or exhausted, e.g. an error path that must still report the
+ * residual, or a loop that has fixed its memory budget.
  *   r[n_dof] float64, free_mask[n_dof] uint8 (0 = Dirichlet dof), norm_out[1] float64: all
  *   device memory of the calling thread's current device, owned by the caller; n_dof = 0
  *   writes +0.0.  cuda_stream: the cudaStream_t the work is queued on (NULL = legacy
  *   default stream); the call does not synchronise, norm_out is valid once the stream has
  *   reached it.  The summation order is fixed, so the result is reproducible bit for bit.
  * Errors: HFE_EINVAL if n_dof < 0, n_dof > HFE_FREE_NORM_STATIC_MAX_DOF, a required pointer
- * is NULL or not on the current device (nothing is launched); HFE_ECUDA if the set-up or
- * the launch fails.
+ * is NULL or not on the current device (nothing is launched); HFE_ECUDA if a CUDA error was
+ * already pending when the call began (it is left pending, nothing is launched), or if the
+ * address look-up, the counter reset or the launch fails.
  * Rules: calls that overlap on one device (two host threads, or two streams with no
- * ordering between them) share the scratch and race — serialise them.  The first call on
- * each device looks up the scratch address and the kernel (cudaGetSymbolAddress,
- * cudaFuncGetAttributes, with that device current), which may load the module; make it
- * before any stream capture begins. */
+ * ordering between them) share the scratch and race — serialise them.  Every call looks up
+ * the scratch's address in the current context (cudaGetSymbolAddress); the first call on a
+ * device may load the module, so make it before any stream capture begins. */
 #define HFE_FREE_NORM_STATIC_MAX_DOF 4194304
 hfe_status hfe_free_norm_static(const double* r, const uint8_t* free_mask, int64_t n_dof, double* norm_out,
                                 void* cuda_stream);

@@ -142,8 +142,14 @@ def sigma_y(theta, alpha, hardening):
 
 
 def hill_phi(Hg, T):
+    """phi = sqrt(T : H : T) (Eq. Phi_hill) and H : T.  H is positive semi-definite with the
+    hydrostatic direction in its null space, so T : H : T >= 0; near a hydrostatic T the sum
+    can round slightly below zero, and is then taken as 0 (real part compared, so that a
+    complex-step argument keeps its imaginary part elsewhere)."""
     HT = np.einsum("...ijkl,...kl->...ij", Hg, T)
-    return np.sqrt(ddot(T, HT)), HT
+    q = ddot(T, HT)
+    q = np.where(np.real(q) > 0.0, q, 0.0 * q)
+    return np.sqrt(q), HT
 
 
 def local_residual(y, eps, epn, alpn, theta, hardening, Theta):

@@ -1,6 +1,6 @@
 // FP64 norm of the free entries of a residual vector, with no device allocation of any kind.
 //
-// This is the S9 norm ||R_free||_2 of the global Newton convergence test (Sec. 2.2.5) in a
+// This is the norm ||R_free||_2 that the global Newton iteration tests for convergence, in a
 // form that needs no solver handle and takes no memory: the reduction's scratch (one partial
 // sum per CTA and the CTAs' arrival counter) lives in the file-scope static device array
 // below instead of a handle's workspace.  The paper has no counterpart.
@@ -22,13 +22,16 @@
 //   every call clears it again with cudaMemsetAsync on the caller's stream before its
 //   launch, and the last CTA leaves it at zero.  The partial sums are written before they
 //   are read and need no initial value.
-// * The first call on each device does the set-up (cudaGetSymbolAddress of the scratch and
-//   cudaFuncGetAttributes of the kernel, with that device current; both may load the module
-//   and so may take memory once).  Make that first call before any stream capture begins.
+// * Every call looks up the scratch's device address with cudaGetSymbolAddress, with the
+//   caller's device current, and passes it to the kernel.  The address is not cached: a
+//   context that is destroyed and created again (cudaDeviceReset) reloads the module, and
+//   the array may then sit elsewhere.  The first call on a device (or in a new context) may
+//   load the module and so may take memory once; make it before any stream capture begins.
+// * An error left pending by the caller's earlier CUDA work is not consumed: the call then
+//   returns HFE_ECUDA without launching anything, and the error stays for the caller.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "hfe.h"
 
@@ -103,31 +106,13 @@ __global__ void __launch_bounds__(kThreads) free_norm_static_kernel(const double
   }
 }
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, looked up once per device.
-cudaError_t scratch_address(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
-    if (e != cudaSuccess) return e;
-    cudaFuncAttributes attr;
-    e = cudaFuncGetAttributes(&attr, free_norm_static_kernel);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
-  return cudaSuccess;
-}
-
-// True when p is device (or managed) memory of device dev.
+// True when p is device (or managed) memory of device dev.  Called only while no error is
+// pending, so the error that cudaPointerGetAttributes raises for a pointer CUDA does not
+// know is the only one consumed here.
 bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();   // consume the (non-sticky) error of a pointer CUDA does not know
+    cudaGetLastError();
     return false;
   }
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
@@ -139,18 +124,30 @@ extern "C" hfe_status hfe_free_norm_static(const double* r, const uint8_t* free_
                                            double* norm_out, void* cuda_stream) {
   if (norm_out == nullptr || n_dof < 0 || n_dof > HFE_FREE_NORM_STATIC_MAX_DOF) return HFE_EINVAL;
   if (n_dof > 0 && (r == nullptr || free_mask == nullptr)) return HFE_EINVAL;
+  if (cudaPeekAtLastError() != cudaSuccess) return HFE_ECUDA;   // the caller's error: left pending
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HFE_ECUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return HFE_ECUDA;
   if (!on_device(norm_out, dev)) return HFE_EINVAL;
   if (n_dof > 0 && (!on_device(r, dev) || !on_device(free_mask, dev))) return HFE_EINVAL;
-  double* scratch = nullptr;
-  if (scratch_address(dev, &scratch) != cudaSuccess) return HFE_ECUDA;
+  // the scratch's address in the current context (looked up on every call, see the header)
+  void* sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_norm_scratch) != cudaSuccess || sym == nullptr) {
+    cudaGetLastError();
+    return HFE_ECUDA;
+  }
+  double* scratch = static_cast<double*>(sym);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (n_dof == 0) {   // empty sum: the norm is +0.0 (all-zero bits)
-    return cudaMemsetAsync(norm_out, 0, sizeof(double), s) == cudaSuccess ? HFE_OK : HFE_ECUDA;
+    if (cudaMemsetAsync(norm_out, 0, sizeof(double), s) == cudaSuccess) return HFE_OK;
+    cudaGetLastError();
+    return HFE_ECUDA;
   }
-  if (cudaMemsetAsync(scratch + kTicketSlot, 0, sizeof(unsigned), s) != cudaSuccess) return HFE_ECUDA;
+  if (cudaMemsetAsync(scratch + kTicketSlot, 0, sizeof(unsigned), s) != cudaSuccess) {
+    cudaGetLastError();
+    return HFE_ECUDA;
+  }
   const unsigned blocks = (unsigned)((n_dof + kChunk - 1) / kChunk);   // <= kMaxCtas by the check above
   free_norm_static_kernel<<<blocks, kThreads, 0, s>>>(r, free_mask, n_dof, scratch, norm_out);
+  // no error was pending at entry, so one raised now is this launch's own
   return cudaGetLastError() == cudaSuccess ? HFE_OK : HFE_ECUDA;
 }

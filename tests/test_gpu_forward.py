@@ -205,3 +205,23 @@ def test_extrapolation_history_restarts_after_set_state():
     assert np.array_equal(u1, u2) and st1["newton_iters"] == st2["newton_iters"]
     with pytest.raises(hfe.HfeError):
         hfe.from_inputs(mesh, bc, mat, precision="fp64", predictor=4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_voce_homogeneous_closed_form(precision):
+    """Voce hardening through the whole GPU forward: the config-0 cube with roller BCs and
+    config 1's Voce material (sigma0 = 150, Q = 120, b = 12), 10 steps to 5 %, against the
+    uniaxial closed form eps11 = sigma_y(alpha)/E + alpha (Eq. Hard, reading R1), which the
+    test writes out itself: FP64 1e-10, mixed 1e-5 in displacement; alpha 1e-12 / 1e-6."""
+    from tests.test_oracle_global import _uniaxial_closed_form, config0_voce_problem
+    mesh, bc, mat, ts = config0_voce_problem()
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, **opts) as s:
+        hist = np.empty((7, mesh.n_el * 8))
+        u, st = s.forward(ts, hist_out=hist)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for k, t in enumerate(ts):
+        uex = _uniaxial_closed_form(t, mesh, "voce")[0]
+        assert np.abs(u[k] - uex).max() < tol * np.abs(uex).max(), (k, precision)
+    a = _uniaxial_closed_form(ts[-1], mesh, "voce")[1]
+    assert np.abs(hist[6] - a).max() < (1e-12 if precision == "fp64" else 1e-6) * max(a, 1.0)

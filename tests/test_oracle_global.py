@@ -1,7 +1,8 @@
 """Pins of the oracle's element, global Newton and adjoint (CPU only).
 
 * P2: homogeneous uniaxial closed form of the whole forward solve (config-0 cube, roller
-  symmetry BCs, Swift hardening, 10 steps to 5 % engineering strain).
+  symmetry BCs, 10 steps to 5 % engineering strain), with Swift hardening and with Voce
+  hardening (config 1's sigma0, Q, b).
 * P3: elastic and plastic patch tests on a distorted mesh (affine boundary data).
 * P5: K^e equals central FD of R^e (consistent tangent, Eq. Stiffness_mat); K symmetric.
 * R12: symmetric elimination and identity-row elimination (Algorithm
@@ -17,17 +18,28 @@ from oracle import element, solver
 from paper_2606_17390_b300 import inputs
 
 
-def _uniaxial_closed_form(t, mesh):
-    """eps11 = ln(1 + 0.05 t) = sigma_y(alpha)/E + alpha (G + H = 1, r11 = 1), T22 = T33 = 0,
-    eps_p = alpha diag(1, -H, -G)."""
-    E, nu, K, e0, n, G_, H_ = 70000.0, 0.33, 500.0, 0.01, 0.2, 0.30, 0.70
-    e11 = np.log1p(0.05 * t)
+def _uniaxial_closed_form(t, mesh, law="swift", strain=0.05):
+    """eps11 = ln(1 + strain t) = sigma_y(alpha)/E + alpha (G + H = 1, r11 = 1), T22 = T33 = 0,
+    eps_p = alpha diag(1, -H, -G).  law "swift": sigma_y = K (eps0 + alpha)^n with the
+    config-0 values; "voce": sigma_y = sigma0 + Q (1 - exp(-b alpha)) with the config-1 values
+    (Eq. Hard with the sqrt(2/3) moved into the yield function, reading R1).  The hardening
+    law is written out here, independently of the oracle, and alpha solved by 1-D Newton."""
+    E, nu, G_, H_ = 70000.0, 0.33, 0.30, 0.70
+    if law == "swift":
+        K, e0, n = 500.0, 0.01, 0.2
+        sy = lambda a: K * (e0 + a) ** n
+        dsy = lambda a: K * n * (e0 + a) ** (n - 1)
+    else:
+        s0, Q, b = 150.0, 120.0, 12.0
+        sy = lambda a: s0 + Q * (1.0 - np.exp(-b * a))
+        dsy = lambda a: Q * b * np.exp(-b * a)
+    e11 = np.log1p(strain * t)
     a = 0.0
-    if K * e0 ** n / E < e11:
+    if sy(0.0) / E < e11:
         for _ in range(60):
-            r = K * (e0 + a) ** n / E + a - e11
-            a -= r / (K * n * (e0 + a) ** (n - 1) / E + 1.0)
-    T11 = K * (e0 + a) ** n if a > 0 else E * e11
+            r = sy(a) / E + a - e11
+            a -= r / (dsy(a) / E + 1.0)
+    T11 = sy(a) if a > 0 else E * e11
     e22 = -nu * T11 / E - H_ * a
     e33 = -nu * T11 / E - G_ * a
     X = mesh.X
@@ -35,13 +47,25 @@ def _uniaxial_closed_form(t, mesh):
     return u.ravel(), a, T11, e11
 
 
-def test_homogeneous_uniaxial_closed_form():
-    mesh, bc, mat, ts = inputs.config0_problem()
+def config0_voce_problem():
+    """The config-0 cube and roller BCs with config 1's Voce material (same Hill constants)."""
+    mesh, bc, _, ts = inputs.config0_problem()
+    return mesh, bc, inputs.config1_material(), ts
+
+
+@pytest.mark.parametrize("law", ["swift", "voce"])
+def test_homogeneous_uniaxial_closed_form(law):
+    if law == "swift":
+        mesh, bc, mat, ts = inputs.config0_problem()
+    else:
+        mesh, bc, mat, ts = config0_voce_problem()
     prob = solver.from_inputs(mesh, bc, mat)
     us, hs, infos = solver.forward(prob, ts, rtol=1e-13)
+    alphas = []
     for n, t in enumerate(ts):
-        uex, a, T11, e11 = _uniaxial_closed_form(t, mesh)
+        uex, a, T11, e11 = _uniaxial_closed_form(t, mesh, law)
         assert a > 0                                   # every step is plastic
+        alphas.append(a)
         assert np.abs(us[n] - uex).max() < 1e-12 * np.abs(uex).max()
         assert np.abs(hs[n + 1][..., 6] - a).max() < 1e-13
         ep = hs[n + 1][..., :6]
@@ -50,6 +74,10 @@ def test_homogeneous_uniaxial_closed_form():
         R, _, _ = solver.residual(prob, us[n], hs[n], t, jacobians=None)
         face = bc.dof[(bc.value != 0.0)]
         assert abs(R[face].sum() - T11 / np.exp(e11)) < 1e-9 * T11
+    if law == "voce":
+        # the steps span b alpha from ~0.04 to ~0.6: the exponential's curvature is exercised,
+        # so a misplaced factor on Q or b, or a sign in the exponent, moves u beyond 1e-12
+        assert 12.0 * alphas[0] < 0.1 and 12.0 * alphas[-1] > 0.5
 
 
 @pytest.mark.parametrize("plastic", [False, True])

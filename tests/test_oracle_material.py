@@ -250,3 +250,27 @@ def test_first_pk_tangent_vs_fd():
             fd = (M.gauss_point(Fp, ep, al, th, hd, None, None)["P"] -
                   M.gauss_point(Fm, ep, al, th, hd, None, None)["P"]) / (2 * h)
             assert np.abs(fd - o["A"][..., k, l]).max() < 1e-6 * np.abs(o["A"]).max()
+
+
+def test_hydrostatic_trial_stress_is_elastic_and_finite():
+    """A purely volumetric strain gives a hydrostatic trial stress, which lies in the null
+    space of the Hill tensor (App. A.1: p4..p6 make H deviatoric), so phi = 0 and the point is
+    elastic (Eq. KT) at any pressure.  In rotated frames T : H : T rounds to small negative
+    values in about half the cases; phi must still come out finite (0), never NaN."""
+    th = inputs.config0_material().theta_vector()
+    B = 200
+    rng = np.random.default_rng(0)
+    Th = np.stack([inputs.random_rotation(s) for s in range(B)])
+    mag = 10.0 ** rng.uniform(-4.0, -1.0, B) * rng.choice([-1.0, 1.0], B)
+    eps = np.zeros((B, 6))
+    eps[:, :3] = mag[:, None]
+    thb = np.tile(th, (B, 1))
+    Hg = M.hill_tensor(thb, Th)
+    T = M.elastic_stress(thb, M.sym(eps))
+    phi, _ = M.hill_phi(Hg, T)
+    assert np.all(np.isfinite(phi))
+    assert np.all(phi <= 1e-6 * np.abs(T).max(axis=(1, 2)))   # sqrt of the rounding of T:H:T
+    o = M.local_update(eps, np.zeros((B, 6)), np.zeros(B), thb, "swift", Th, derivatives=False)
+    assert np.all(np.isfinite(o["ftr"])) and not o["plastic"].any()
+    lam, mu = M.lame(th)
+    assert np.allclose(o["z"][:, 0], (3.0 * lam + 2.0 * mu) * mag, rtol=1e-13, atol=0.0)
