@@ -59,7 +59,11 @@ typedef enum {
   HFE_ELOCAL = 2,       /* a local return mapping did not converge (count in stats) */
   HFE_EPCG = 3,         /* Krylov solve did not reach pcg_rtol within pcg_maxit, broke down, or (hfe_solve)
                            the matrix has diagonal blocks that are not positive definite */
-  HFE_ENONFINITE = 4    /* a non-finite value appeared in a residual, stress or solve */
+  HFE_ENONFINITE = 4,   /* a non-finite value appeared in a residual, stress or solve */
+  HFE_EBARRIER = 5      /* a grid-barrier wait of a one-launch Krylov solve ran out (options.
+                           barrier_spin_limit): the solve was abandoned and every CTA left; the
+                           handle stays usable.  Not retried by adaptive stepping: hfe_forward
+                           returns it with the state of the last converged step */
 } hfe_status;
 
 typedef struct hfe_handle hfe_handle;
@@ -151,6 +155,11 @@ typedef struct {
                              Fbar = (Jbar/J)^(1/3) F, Jbar the element average of J; K is then
                              non-symmetric and every Krylov solve is BiCGSTAB (hfe_adjoint solves
                              with the transposed blocks).  0 (default): the standard element */
+  int64_t barrier_spin_limit; /* polls (each >= 32 ns, backing off to 256 ns) after which a CTA
+                             waiting at a grid barrier of a one-launch Krylov solve gives up; the
+                             solve then returns HFE_EBARRIER.  Default 2^25 (seconds: a wait that
+                             long means the CTAs are not all resident).  0 makes every wait give
+                             up at its first poll (a way to exercise the failure path) */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */
@@ -277,6 +286,11 @@ hfe_status hfe_forward(hfe_handle* h, int n_steps, const double* t, double* u_ou
 #define HFE_WARM_RECORD 1
 #define HFE_WARM_USE 2
 hfe_status hfe_set_warm_start(hfe_handle* h, int mode);
+
+/* Replaces the handle's options.barrier_spin_limit (>= 0) for the calls that follow, e.g. to
+ * restore the default after a test of the failure path.  Errors: HFE_EINVAL for a NULL
+ * handle or a negative limit. */
+hfe_status hfe_set_barrier_spin_limit(hfe_handle* h, int64_t limit);
 
 /* Misfit J = w sum_n ||u^n - u_target^n||^2 of a forward run from zero state over t, and its
  * gradient by the discrete adjoint (Eq. dR_u, Eq. main_grad) with the per-Gauss-point

@@ -243,12 +243,13 @@ hfe_status indefinite_fallback(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs<
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
   const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
   HFE_TRY(cuda_check(h, bicgstab_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
-                                               h->opt.pcg_maxit, h->sc, h->part, partial_slots(), h->s),
+                                               h->opt.pcg_maxit, h->sc, h->part, partial_slots(),
+                                               (uint64_t)h->opt.barrier_spin_limit, h->s),
                      "BiCGSTAB launch"));
   HFE_TRY(read_status(h));
   h->n_bicgstab++;
   h->h_sc->iters += cg_iters;
-  if (h->h_sc->gs.timeout) return fail(h, HFE_ECUDA, "BiCGSTAB: a grid barrier wait ran out");
+  if (h->h_sc->gs.timeout) return fail(h, HFE_EBARRIER, "BiCGSTAB: a grid barrier wait ran out");
   if (h->h_sc->done) return HFE_OK;
   if (have_truncated && h->allow_truncated) {
     HFE_TRY(cuda_check(h, cudaMemcpyAsync(v.x, ls.vxt, bytes, cudaMemcpyDeviceToDevice, h->s), "copy"));
@@ -265,13 +266,14 @@ hfe_status pcg_solve_persistent(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs
                                 double bscale, int64_t* iters_out) {
   const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
   HFE_TRY(cuda_check(h, pcg_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
-                                          h->opt.pcg_maxit, h->sc, h->part, partial_slots(), h->s),
+                                          h->opt.pcg_maxit, h->sc, h->part, partial_slots(),
+                                          (uint64_t)h->opt.barrier_spin_limit, h->s),
                      "persistent CG launch"));
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
   HFE_TRY(read_status(h));
   const PcgScalars& sc = *h->h_sc;
   if (iters_out) *iters_out = sc.iters;
-  if (sc.gs.timeout) return fail(h, HFE_ECUDA, "persistent CG: a grid barrier wait ran out");
+  if (sc.gs.timeout) return fail(h, HFE_EBARRIER, "persistent CG: a grid barrier wait ran out");
   // a Newton correction may run on a tangent that is indefinite at some nodes (the surrogate
   // blocks keep the preconditioner SPD and truncated CG stops at negative curvature); a plain
   // solve of a matrix that is not SPD is refused
@@ -360,13 +362,14 @@ hfe_status bicg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale,
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->sc, 0, sizeof(PcgScalars), h->s), "memset"));
   const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
   HFE_TRY(cuda_check(h, bicgstab_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
-                                               h->opt.pcg_maxit, h->sc, h->part, partial_slots(), h->s),
+                                               h->opt.pcg_maxit, h->sc, h->part, partial_slots(),
+                                               (uint64_t)h->opt.barrier_spin_limit, h->s),
                      "BiCGSTAB launch"));
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->h_bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->s), "copy"));
   HFE_TRY(read_status(h));
   const PcgScalars& sc = *h->h_sc;
   if (iters_out) *iters_out = sc.iters;
-  if (sc.gs.timeout) return fail(h, HFE_ECUDA, "BiCGSTAB: a grid barrier wait ran out");
+  if (sc.gs.timeout) return fail(h, HFE_EBARRIER, "BiCGSTAB: a grid barrier wait ran out");
   if (!std::isfinite(sc.rr0)) return fail(h, HFE_ENONFINITE, "non-finite right-hand side");
   if (sc.done) return HFE_OK;
   if (sc.breakdown)
@@ -437,6 +440,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->cutback = 0.5;
   o->max_cutbacks = 8;
   o->fbar = 0;
+  o->barrier_spin_limit = (int64_t)1 << 25;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
@@ -456,6 +460,7 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     return fail(h, HFE_EINVAL, "options: cutback must lie in (0, 1)");
   if (h->opt.max_cutbacks < 0) return fail(h, HFE_EINVAL, "options: max_cutbacks must be >= 0");
   if (h->opt.predictor < 0 || h->opt.predictor > 3) return fail(h, HFE_EINVAL, "options: predictor must be 0 to 3");
+  if (h->opt.barrier_spin_limit < 0) return fail(h, HFE_EINVAL, "options: barrier_spin_limit must be >= 0");
   h->fp64 = h->opt.precision == HFE_PRECISION_FP64;
   h->user = reinterpret_cast<cudaStream_t>(stream);
   HFE_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"));
@@ -894,6 +899,12 @@ extern "C" hfe_status hfe_set_warm_start(hfe_handle* h, int mode) {
     h->warm_t.clear();
   }
   h->warm_mode = mode;
+  return HFE_OK;
+}
+
+extern "C" hfe_status hfe_set_barrier_spin_limit(hfe_handle* h, int64_t limit) {
+  if (h == nullptr || limit < 0) return HFE_EINVAL;
+  h->opt.barrier_spin_limit = limit;
   return HFE_OK;
 }
 

@@ -380,13 +380,14 @@ __global__ void predictor_rhs_kernel(const double* __restrict__ R_, const R* __r
 // search direction p = z + beta p_prev is formed on the fly inside the SpMV (for the
 // gathered columns from z and the previous direction, for the own rows also stored), with
 // p_prev and p in two buffers that swap each iteration.
-constexpr unsigned long long kBarrierSpinLimit = 1ull << 25;   // x >= 32 ns: about a second
-
 // Grid barrier fused with a reduction: every CTA publishes its partial pair in part, the
 // last CTA to arrive sums all pairs in CTA order (the same fixed order whichever CTA is
-// last) into gs.tot and releases the others, who read the totals.  Waits are bounded;
-// returns false once any wait has run out (sticky), after which every CTA leaves the solve.
-__device__ __forceinline__ bool grid_allreduce(GridSync* gs, const double* part, double& t0, double& t1) {
+// last) into gs.tot and releases the others, who read the totals.  Waits are bounded by
+// spin_limit polls; returns false once any wait has run out (sticky), after which every CTA
+// leaves the solve (a CTA released just before another gave up meets the next barrier,
+// whose count can no longer complete, and gives up there).
+__device__ __forceinline__ bool grid_allreduce(GridSync* gs, const double* part, double& t0, double& t1,
+                                               unsigned long long spin_limit) {
   __shared__ int s_last, s_ok;
   __shared__ double s_t0, s_t1;
   __syncthreads();
@@ -399,7 +400,7 @@ __device__ __forceinline__ bool grid_allreduce(GridSync* gs, const double* part,
       unsigned long long spins = 0;
       unsigned ns = 32;
       while (*(volatile unsigned*)&gs->gen == g0) {
-        if (++spins > kBarrierSpinLimit) {
+        if (++spins > spin_limit) {
           atomicExch(&gs->timeout, 1);
           break;
         }
@@ -522,6 +523,7 @@ struct PersistArgs {
   int block3;
   PcgScalars* sc;
   double* part;   // 2 buffers x gridDim.x pairs
+  unsigned long long spin_limit;   // bound of each grid-barrier wait (polls)
 };
 
 template <typename R>
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
       pp[2 * blockIdx.x + 1] = v1;
     }
     ++red;
-    return grid_allreduce(&sc->gs, pp, t0, t1);
+    return grid_allreduce(&sc->gs, pp, t0, t1, a.spin_limit);
   };
   // x = x0 (or 0), r = b - K x0 on the free dofs, z = M^-1 r, p_prev = 0 (beta = 0 in the
   // first iteration); convergence is measured against |b|, as for a zero start
@@ -736,6 +738,7 @@ struct BicgArgs {
   int block3;
   PcgScalars* sc;
   double* part;
+  unsigned long long spin_limit;   // bound of each grid-barrier wait (polls)
 };
 
 template <typename R>
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 8 ? 3 : 4) bicgstab_persi
       pp[2 * blockIdx.x + 1] = v1;
     }
     ++red;
-    return grid_allreduce(&sc->gs, pp, t0, t1);
+    return grid_allreduce(&sc->gs, pp, t0, t1, a.spin_limit);
   };
   // x = 0, r = rh = b on the free dofs, p = v = 0
   double rr = 0.0, dummy = 0.0;
@@ -925,7 +928,7 @@ void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>
 template <typename R>
 cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
-                           double* part, int64_t part_slots, cudaStream_t s, const R* x0) {
+                           double* part, int64_t part_slots, uint64_t spin_limit, cudaStream_t s, const R* x0) {
   constexpr int kMinb = sizeof(R) == 8 ? 3 : 4;   // FP64 blocks need the registers of 3 CTAs per SM
   const void* fn = (const void*)pcg_persistent_kernel<R, kMinb>;
   const int cap = kMinb;
@@ -942,7 +945,7 @@ cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, Pc
   if (grid > useful) grid = useful;
   if (grid < 1) grid = 1;
   PersistArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.z, v.p, v.p2, v.q, x0,
-                   K.n_nodes, maxit, block3, sc, part};
+                   K.n_nodes, maxit, block3, sc, part, (unsigned long long)spin_limit};
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
 }
@@ -951,7 +954,7 @@ cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, Pc
 template <typename R>
 cudaError_t bicgstab_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                                 const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
-                                double* part, int64_t part_slots, cudaStream_t s) {
+                                double* part, int64_t part_slots, uint64_t spin_limit, cudaStream_t s) {
   const void* fn = (const void*)bicgstab_persistent_kernel<R>;
   int dev = 0, n_sm = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -964,7 +967,7 @@ cudaError_t bicgstab_persistent(const Csr& K, const R* vals, const uint8_t* free
   if (grid > useful) grid = useful;
   if (grid < 1) grid = 1;
   BicgArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.rh, v.p, v.q, v.y, v.p2, v.z,
-                v.t, K.n_nodes, maxit, block3, sc, part};
+                v.t, K.n_nodes, maxit, block3, sc, part, (unsigned long long)spin_limit};
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
 }
@@ -1016,16 +1019,16 @@ template void pcg_iteration<double>(const Csr&, const double*, const uint8_t*, P
                                     double*, cudaStream_t);
 template cudaError_t pcg_persistent<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int,
                                             const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
-                                            cudaStream_t, const float*);
+                                            uint64_t, cudaStream_t, const float*);
 template cudaError_t pcg_persistent<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int,
                                              const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
-                                             cudaStream_t, const double*);
+                                             uint64_t, cudaStream_t, const double*);
 template cudaError_t bicgstab_persistent<float>(const Csr&, const float*, const uint8_t*, PcgVecs<float>&, int,
                                                  const double*, double, double, int64_t, PcgScalars*, double*, int64_t,
-                                                 cudaStream_t);
+                                                 uint64_t, cudaStream_t);
 template cudaError_t bicgstab_persistent<double>(const Csr&, const double*, const uint8_t*, PcgVecs<double>&, int,
                                                   const double*, double, double, int64_t, PcgScalars*, double*,
-                                                  int64_t, cudaStream_t);
+                                                  int64_t, uint64_t, cudaStream_t);
 template void precond_setup<float>(const Csr&, const float*, const int64_t*, const uint8_t*, float*, int, int*,
                                    cudaStream_t);
 template void precond_setup<double>(const Csr&, const double*, const int64_t*, const uint8_t*, double*, int, int*,

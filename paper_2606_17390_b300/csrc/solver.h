@@ -66,17 +66,19 @@ void pcg_iteration(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>
 // to |r| <= sqrt(rtol2) |b| or maxit iterations, from x0 (nullptr = 0; must not alias v's
 // vectors); results in *sc (iters, rr, rr0 = |b|^2, rz, pq, breakdown, done, gs.timeout).
 // *sc must be zeroed before the launch.
+// spin_limit bounds every grid-barrier wait (polls); a wait that runs out sets sc->gs.timeout.
 template <typename R>
 cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
-                           double* part, int64_t part_slots, cudaStream_t s, const R* x0 = nullptr);
+                           double* part, int64_t part_slots, uint64_t spin_limit, cudaStream_t s,
+                           const R* x0 = nullptr);
 // Preconditioned BiCGSTAB in one cooperative launch for a symmetric indefinite (or
 // nonsymmetric) K with the same SPD block-Jacobi preconditioner: x (v.x) = K^-1 b; uses v.r,
 // v.rh, v.p, v.q (as v), v.y, v.p2 (as s), v.z, v.t.  Results in *sc as for pcg_persistent.
 template <typename R>
 cudaError_t bicgstab_persistent(const Csr& K, const R* vals, const uint8_t* freem, PcgVecs<R>& v, int block3,
                                 const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
-                                double* part, int64_t part_slots, cudaStream_t s);
+                                double* part, int64_t part_slots, uint64_t spin_limit, cudaStream_t s);
 template <typename R>
 void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
                    int block3, int* bad, cudaStream_t s);

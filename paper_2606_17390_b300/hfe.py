@@ -18,7 +18,7 @@ __all__ = ["HfeError", "Solver", "lib", "LIB_PATH", "STATUS", "material_arrays"]
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhfe.so")
 
 STATUS = {0: "HFE_OK", -1: "HFE_EINVAL", -2: "HFE_ENOMEM", -3: "HFE_ECUDA", -4: "HFE_EDETJ",
-          1: "HFE_ENEWTON", 2: "HFE_ELOCAL", 3: "HFE_EPCG", 4: "HFE_ENONFINITE"}
+          1: "HFE_ENEWTON", 2: "HFE_ELOCAL", 3: "HFE_EPCG", 4: "HFE_ENONFINITE", 5: "HFE_EBARRIER"}
 PRECISION = {"fp64": 0, "mixed": 1}
 HARDENING = {"swift": 0, "voce": 1}
 SWEEP_RESIDUAL, SWEEP_TANGENT = 0, 1
@@ -48,7 +48,8 @@ class Options(C.Structure):
                 ("pcg_maxit", C.c_int), ("pcg_check_every", C.c_int), ("precond", C.c_int),
                 ("local_maxit", C.c_int), ("local_tol", C.c_double), ("ckpt_every", C.c_int),
                 ("predictor", C.c_int), ("ew_forcing", C.c_int), ("pcg_persistent", C.c_int),
-                ("adaptive", C.c_int), ("cutback", C.c_double), ("max_cutbacks", C.c_int), ("fbar", C.c_int)]
+                ("adaptive", C.c_int), ("cutback", C.c_double), ("max_cutbacks", C.c_int), ("fbar", C.c_int),
+                ("barrier_spin_limit", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -104,9 +105,11 @@ def lib():
     L.hfe_solve.argtypes = [vp, vp, vp, C.POINTER(Stats)]
     L.hfe_forward.argtypes = [vp, i32, vp, vp, vp, vp, C.POINTER(Stats)]
     L.hfe_adjoint.argtypes = [vp, i32, vp, vp, dbl, vp, vp, C.POINTER(Stats)]
+    L.hfe_set_barrier_spin_limit.argtypes = [vp, C.c_int64]
     for name in ("hfe_create", "hfe_get_info", "hfe_set_material", "hfe_set_state", "hfe_get_state",
                  "hfe_set_load", "hfe_get_load",
-                 "hfe_gp_sweep", "hfe_get_bsr", "hfe_spmv", "hfe_solve", "hfe_forward", "hfe_adjoint"):
+                 "hfe_gp_sweep", "hfe_get_bsr", "hfe_spmv", "hfe_solve", "hfe_forward", "hfe_adjoint",
+                 "hfe_set_barrier_spin_limit"):
         getattr(L, name).restype = i32
     _LIB = L
     return L
@@ -283,6 +286,12 @@ class Solver:
         f.argtypes = [C.c_void_p, C.c_int]
         f.restype = C.c_int
         self._check(f(self._h, self.WARM_MODES[mode] if isinstance(mode, str) else int(mode)))
+
+    def set_barrier_spin_limit(self, limit):
+        """hfe_set_barrier_spin_limit: the bound (polls) of every grid-barrier wait in the
+        one-launch Krylov solves of the calls that follow."""
+        self._check(lib().hfe_set_barrier_spin_limit(self._h, int(limit)))
+        self.options.barrier_spin_limit = int(limit)
 
     def solve(self, b):
         b = np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b

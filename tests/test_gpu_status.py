@@ -54,3 +54,45 @@ def test_local_return_mapping_cut_off_reports_elocal():
         with pytest.raises(hfe.HfeError) as e:
             s.sweep(u)
         assert e.value.status == HFE_ELOCAL
+
+
+HFE_EBARRIER = 5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_barrier_wait_that_runs_out(precision):
+    """The one-launch Krylov solves wait at grid barriers with a bounded number of polls
+    (options.barrier_spin_limit).  With the bound set to 0 every waiting CTA gives up at its
+    first poll (no flag is left set for ever, no GPU fault): hfe_solve and hfe_forward return
+    HFE_EBARRIER, the forward leaves the stored state at its last converged step, and the same
+    handle, given the default bound again, solves bit for bit like a fresh handle."""
+    mesh, bc, mat, ts = inputs.config2_problem(n=12, n_steps=4)
+    b = np.random.default_rng(1).standard_normal(mesh.n_dof)
+    b[bc.dof] = 0.0
+    with hfe.from_inputs(mesh, bc, mat, precision=precision) as ref:
+        ref.sweep(np.zeros(mesh.n_dof), 0.0)
+        x_ref, st_ref = ref.solve(b)
+        ref.set_state(None, None)
+        u_ref, _ = ref.forward(ts)
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, barrier_spin_limit=0) as s:
+        default = hfe.Options()
+        hfe.lib().hfe_default_options(__import__("ctypes").byref(default), hfe.PRECISION[precision])
+        s.sweep(np.zeros(mesh.n_dof), 0.0)
+        with pytest.raises(hfe.HfeError, match="grid barrier") as e:
+            s.solve(b)
+        assert e.value.status == HFE_EBARRIER
+        with pytest.raises(hfe.HfeError) as e:
+            s.forward(ts[:1])
+        assert e.value.status == HFE_EBARRIER
+        u0, _ = s.get_state()
+        assert s.get_load() == 0.0 and not np.any(u0)
+        s.set_barrier_spin_limit(default.barrier_spin_limit)
+        s.sweep(np.zeros(mesh.n_dof), 0.0)
+        x, st = s.solve(b)
+        assert np.array_equal(x, x_ref) and st["pcg_iters"] == st_ref["pcg_iters"]
+        s.set_state(None, None)
+        u, _ = s.forward(ts)
+        assert np.array_equal(u, u_ref)
+    with pytest.raises(hfe.HfeError) as e:
+        hfe.from_inputs(mesh, bc, mat, precision=precision, barrier_spin_limit=-1)
+    assert e.value.status == -1

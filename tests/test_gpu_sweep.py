@@ -93,3 +93,57 @@ def test_sweep_zero_state_is_linear_elastic():
     u = np.zeros(mesh.n_dof)
     hist = np.zeros((mesh.n_el, 8, 7))
     _compare(mesh, u, hist, inputs.config0_material().theta_vector(), "swift", min_plastic=0.0, max_plastic=0.0)
+
+
+BAND = np.array([-1e-3, -1e-5, -3e-6, -1e-6, -1e-7, 0.0, 1e-7, 1e-6, 3e-6, 1e-5, 1e-3])
+
+
+def _band_state():
+    """Trial states placed at a relative distance delta from the yield surface, delta cycling
+    through BAND over the Gauss points: the mixed path's FP32 elastic test leaves
+    |phi_tr^2 - phi_y^2| < 1e-5 phi_y^2 to FP64 (reading R10), and most of these points lie
+    inside that band.  alpha_n is set per Gauss point so that sqrt(2/3) sigma_y(alpha_n) =
+    phi_tr / (1 + delta), with phi_tr the oracle's trial value (it does not depend on alpha_n)
+    and Swift sigma_y inverted in closed form."""
+    mesh = inputs.distorted_box_mesh(3, seed=8, amp=0.15)
+    rng = np.random.default_rng(5)
+    G = 0.001 * rng.uniform(-1, 1, (3, 3)) + np.diag([0.004, -0.002, -0.002])
+    u = (mesh.X @ G.T + 0.0004 * rng.uniform(-1, 1, mesh.X.shape)).ravel()
+    ep, _ = inputs.random_history(8 * mesh.n_el, 6, 0.0008, 0.0)
+    hist = np.concatenate([ep, np.zeros((ep.shape[0], 1))], axis=1).reshape(mesh.n_el, 8, 7)
+    mat = inputs.config0_material()
+    th = mat.theta_vector()
+    es = element.element_sweep(mesh.X, mesh.conn.astype(np.int64), u, hist, th, "swift", jacobians=None)
+    K, e0, n = th[8], th[9], th[10]
+    phi_tr = es["gp"]["ftr"] + np.sqrt(2.0 / 3.0) * K * e0 ** n
+    delta = BAND[np.arange(phi_tr.size) % BAND.size]
+    sy = phi_tr / (np.sqrt(2.0 / 3.0) * (1.0 + delta))
+    assert np.all(sy > 1.05 * K * e0 ** n)          # every target lies above the initial yield
+    hist[..., 6] = ((sy / K) ** (1.0 / n) - e0).reshape(mesh.n_el, 8)
+    return mesh, u, hist, th, delta
+
+
+def test_sweep_trial_states_in_the_fp64_decision_band():
+    """R, K and the trial history of both precisions against the oracle where the
+    elastic/plastic decision is a near tie.  FP64 takes the oracle's decision at every point;
+    the mixed path's trial stress carries FP32 rounding (~1e-7 relative), so it may decide the
+    other way only within |delta| <= 1e-6, where both outcomes give the same stress to the
+    mixed tolerances."""
+    mesh, u, hist, th, delta = _band_state()
+    Ro, Ko, es = _oracle(mesh, u, hist, th, "swift", None)
+    pl_o = es["gp"]["plastic"]
+    off = delta != 0.0                                 # delta = 0 is a tie up to rounding
+    assert np.array_equal(pl_o[off], delta[off] > 0.0)  # the oracle sees the intended side
+    ho = hist_oracle_to_soa(es["h_new"])
+    for prec in ("fp64", "mixed"):
+        R, K, Ht, st = _gpu(mesh, u, hist, th, "swift", None, prec)
+        tol = TOL[prec]
+        assert st["local_fail"] == 0
+        n_off = abs(int(st["plastic_gps"]) - int(pl_o.sum()))
+        assert n_off <= (0 if prec == "fp64" else int(np.sum(np.abs(delta) <= 1e-6))), (prec, n_off)
+        assert rel_inf(R, Ro) < tol["R"], (prec, rel_inf(R, Ro))
+        dK = (K - Ko).tocsr()
+        kerr = np.abs(dK.data).max() / np.abs(Ko.data).max() if dK.nnz else 0.0
+        assert kerr < tol["K"], (prec, kerr)
+        herr = np.abs(Ht - ho).max() / max(np.abs(ho[:6]).max(), 1e-12)
+        assert herr < tol["h"], (prec, herr)
