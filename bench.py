@@ -118,6 +118,41 @@ def whole_job_rate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
+def measured_fp32_tflops(dev, stream, n=8192, reps=10):
+    """FP32 throughput of a plain library GEMM on this GPU: cuBLAS SGEMM (C = A B, n^3, TF32
+    off, so every product is an FP32 FMA on the CUDA cores), best of reps after 3 warm-ups,
+    CUDA events on the launching stream: 2 n^3 / t.  The denominator of the sweep kernel's
+    ALU roofline, measured the way the driver measures the bf16 peak."""
+    import torch
+    mm = torch.backends.cuda.matmul
+    old = (getattr(mm, "fp32_precision", None), mm.allow_tf32)
+    if old[0] is not None:
+        mm.fp32_precision = "ieee"
+    mm.allow_tf32 = False
+    try:
+        with torch.cuda.stream(stream):
+            g = torch.Generator(device=dev).manual_seed(0)
+            a = torch.randn(n, n, device=dev, generator=g)
+            b = torch.randn(n, n, device=dev, generator=g)
+            c = torch.empty(n, n, device=dev)
+            for _ in range(3):
+                torch.matmul(a, b, out=c)
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                torch.matmul(a, b, out=c)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            del a, b, c
+    finally:
+        if old[0] is not None:
+            mm.fp32_precision = old[0]
+        mm.allow_tf32 = old[1]
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
 def workload(n):
     mesh, bc, mat, _ = inputs.config2_problem(n=n)
     u, hist = inputs.compression_state(mesh, LOAD)
@@ -217,25 +252,51 @@ def cpu_oracle_rate_all_cores(mesh, mat, u, hist, per_worker_s=6.0, seed=0, core
     return 8 * k * cores / wall, desc, cores, wall
 
 
+def _von_mises6(sig):
+    """von Mises stress of Cauchy stresses given as 6 components (11, 22, 33, 12, 23, 13)."""
+    s11, s22, s33, s12, s23, s13 = (sig[:, k] for k in range(6))
+    return np.sqrt(0.5 * ((s11 - s22) ** 2 + (s22 - s33) ** 2 + (s33 - s11) ** 2) + 3.0 * (s12 ** 2 + s23 ** 2 + s13 ** 2))
+
+
 def config1_forward_section(stream):
-    """Config 1's forward (perforated 200 x 100 x 4 plate, Voce, 20 load steps) in FP32-mixed
-    and in FP64 on the same inputs: wall time and Newton / CG counts of each; a run that fails
-    reports its error instead of ending the benchmark."""
+    """Config 1's forward (perforated 200 x 100 x 4 plate, Voce, 20 load steps) in FP64 and in
+    FP32-mixed on the same inputs, one requested step per hfe_forward call (the handle carries
+    its state, its extrapolation history and any reduced increment from call to call), with the
+    displacement and the Cauchy stress of every step copied out: wall time and Newton / CG
+    counts of each precision, and per step the mixed result's error against the FP64 one,
+    max|du| / max|u| and max|dvm| / max vm.  A run that fails reports its error instead of
+    ending the benchmark."""
     from paper_2606_17390_b300 import hfe
     m1, bc1, mat1, t1 = inputs.config1_problem()
     out = {"workload": f"config 1: perforated plate 200x100x4 ({m1.n_el} elements, {m1.n_dof} dofs), Voce, "
-                       f"{len(t1)} steps"}
-    for prec in ("mixed", "fp64"):
+                       f"{len(t1)} steps; one hfe_forward call per step, u and sigma copied out each step"}
+    res = {}
+    for prec in ("fp64", "mixed"):
         try:
+            us, vms = [], []
+            tot = {"newton_iters": 0, "pcg_iters": 0, "substeps": 0, "cutbacks": 0}
+            sig = np.empty((8 * m1.n_el, 6))
             with hfe.from_inputs(m1, bc1, mat1, precision=prec, stream=stream.cuda_stream) as s1:
                 t0 = time.perf_counter()
-                _, st = s1.forward(t1, want_u=False)
-                out[prec] = {"wall_s": time.perf_counter() - t0, "newton_iters": st["newton_iters"],
-                             "pcg_iters": st["pcg_iters"], "substeps": st["substeps"], "cutbacks": st["cutbacks"]}
+                for t in t1:
+                    u, st = s1.forward(np.array([t]), sigma_out=sig)
+                    us.append(u[0].copy())
+                    vms.append(_von_mises6(sig))
+                    for k in tot:
+                        tot[k] += st[k]
+                wall = time.perf_counter() - t0
+            res[prec] = (us, vms)
+            out[prec] = {"wall_s": wall, **tot}
         except Exception as e:
             out[prec] = {"error": f"{type(e).__name__}: {e}"[:200]}
-    if "wall_s" in out.get("mixed", {}) and "wall_s" in out.get("fp64", {}):
+    if "fp64" in res and "mixed" in res:
+        (u64, vm64), (umx, vmmx) = res["fp64"], res["mixed"]
+        du = [float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(umx, u64)]
+        dvm = [float(np.abs(a - b).max() / b.max()) for a, b in zip(vmmx, vm64)]
         out["fp64_over_mixed"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+        out["mixed_vs_fp64"] = {"u_rel_per_step": du, "vm_rel_per_step": dvm, "u_rel_max": max(du),
+                                "vm_rel_max": max(dvm), "tolerance": {"u": 1e-5, "vm": 1e-4},
+                                "within_tolerance": bool(max(du) <= 1e-5 and max(dvm) <= 1e-4)}
     return out
 
 
@@ -349,18 +410,25 @@ def barlat_fe_section(n, stream, dev, reps=5):
 
 
 def reference_arm(args, rank):
+    """The oracle timed as it stands: each step is a bounded sample (a seeded random set of
+    elements of the same state, about ref_step_s seconds of CPU work); ms_per_step is the
+    measured time of one such sample, value the Gauss points of the samples over their time."""
     if rank != 0:
         return
     mesh, bc, mat, u, hist = workload(args.n)
-    rates, times = [], []
+    gps, times = [], []
     for i in range(args.warmup + args.steps):
         r, desc, cores, dt = cpu_oracle_rate(mesh, mat, u, hist, target_s=args.ref_step_s, seed=i)
         if i >= args.warmup:
-            rates.append(r)
+            gps.append(r * dt)
             times.append(dt)
-    value = float(np.mean(rates))
+    value = float(np.sum(gps) / np.sum(times))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * 8 * mesh.n_el / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "step": "one bounded sample of the workload (see cpu_baseline.sample), timed as measured",
+            "full_workload_ms_extrapolated": 1e3 * 8 * mesh.n_el / value,
+            "extrapolated": "full_workload_ms_extrapolated scales the measured rate to all "
+                            f"{8 * mesh.n_el} Gauss points; it was not run",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"hex8 cube {args.n}^3, {mesh.n_dof} dofs, {8 * mesh.n_el} Gauss points, "
                                    "Hill-48 + Swift, clamped compression, mid-step state; CPU oracle on a sample",
@@ -393,8 +461,8 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
-    ap.add_argument("--config1-forward", action="store_true",
-                    help="also run config 1's full-size forward in FP32-mixed and in FP64")
+    ap.add_argument("--no-config1-forward", dest="config1_forward", action="store_false",
+                    help="skip config 1's full-size forward in FP64 and FP32-mixed (per-step errors)")
     ap.add_argument("--forward-predictors", default="2",
                     help="comma-separated options.predictor values of the forward run (first one reported); "
                          "0 restarts each step from the previous displacement, which inverts the elements "
@@ -489,13 +557,18 @@ def main():
     launch_ms = sweep_ms_avg / info["n_colors"]
     el_per_launch = mesh.n_el / info["n_colors"]
     flops_launch = ALG_FLOPS_PER_GP * 8 * el_per_launch
-    peak_fp32 = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
+    peak_derived = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
+    peak_fp32 = measured_fp32_tflops(dev, stream)
     roofline = {"bound": "alu", "achieved": flops_launch / (launch_ms * 1e-3) / 1e12, "peak": peak_fp32,
                 "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "kernel": "gp_sweep_kernel<float,true>", "launch_ms": launch_ms,
                 "alg_flops_per_launch": flops_launch, "alg_bytes_per_launch": ALG_BYTES_PER_EL * el_per_launch,
-                "hbm_frac_of_measured": None, "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+                "hbm_frac_of_measured": None,
+                "peak_source": "measured in this run: cuBLAS FP32 SGEMM 8192^3, TF32 off, best of 10",
+                "peak_derived": peak_derived, "frac_of_derived": None,
+                "derived_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz"}
     roofline["frac"] = roofline["achieved"] / peak_fp32
+    roofline["frac_of_derived"] = roofline["achieved"] / peak_derived
     peaks, src = _peaks()
     roofline["hbm_frac_of_measured"] = ALG_BYTES_PER_EL * el_per_launch / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
     traffic_file = os.path.join(HERE, "profiles", "gp_sweep_traffic.json")
