@@ -184,6 +184,123 @@ template <> struct MatOf<float> { using T = MatRecF; };
 template <> struct MatOf<double> { using T = MatRec; };
 
 // ----------------------------------------------------------------------------------------
+// Phase 2 of the symmetric tangent sweep (standard element): thread (element le, node row a =
+// g) contracts the eight Gauss-point records into the blocks (a, a + d mod 8), d = 0..3 (and
+// d = 4 for a < 4) — each unordered block pair once, as K^e is symmetric (A is stored with
+// its major symmetry) — and into R_a.  The blocks and their transposes are then staged in the
+// warp's own (already consumed) record area, row-major [a][b][3x3] per element, and the warp
+// writes its four elements out with consecutive lanes on consecutive entries: a block's nine
+// values are contiguous in K and an element row's blocks lie close together, so each warp
+// store covers a few 32-byte sectors.  The first colour that touches a block stores (bit 31 of
+// the slot), later colours add: one writer per block per launch, launches in colour order, so
+// the sums are deterministic.
+constexpr int kStageEl = 584;   // staging words per element: 576 used; 584 = 8 mod 32 spreads
+                                // the four elements of a warp over the banks
+
+template <typename R>
+__device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, const int32_t* sSlot, int le, int g,
+                                              unsigned lane, bool valid, int node, unsigned cta, int64_t ccount) {
+  constexpr int kGpStride = Lay<false>::kGpStride;
+  constexpr int kElStride = Lay<false>::kElStride;
+  static_assert(4 * kStageEl <= 4 * kElStride, "staging must fit in the warp's records");
+  const int arow = g;
+  constexpr int kNb = 5;
+  const int nb = (arow < 4) ? 5 : 4;
+  R Kr[kNb][9];
+#pragma unroll
+  for (int d = 0; d < kNb; ++d)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Kr[d][c] = R(0);
+  R Ra[3] = {R(0), R(0), R(0)};
+  if (valid) {
+    const R* G = sGp + (size_t)le * kElStride;
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      const R* Aq = G + q * kGpStride;
+      const R* gt = Aq + kOffG;
+      const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
+      R A[48];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) V4<R>::ld(Aq + 4 * k, A + 4 * k);
+      R U[3][3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int L = 0; L < 3; ++L)
+            U[i][k][L] = ga0 * A[asym(i * 3 + 0, k * 3 + L)] + ga1 * A[asym(i * 3 + 1, k * 3 + L)] +
+                         ga2 * A[asym(i * 3 + 2, k * 3 + L)];
+#pragma unroll
+      for (int d = 0; d < kNb; ++d) {
+        if (d < nb) {
+          const int b = (arow + d) & 7;
+          const R gb0 = gt[b * 3], gb1 = gt[b * 3 + 1], gb2 = gt[b * 3 + 2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Kr[d][i * 3 + k] += U[i][k][0] * gb0 + U[i][k][1] * gb1 + U[i][k][2] * gb2;
+        }
+      }
+      R P[12];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffP + 4 * k, P + 4 * k);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
+    }
+  }
+  // every lane of the warp has read its records: the warp's four record areas become staging
+  __syncwarp();
+  R* stage = sGp + (size_t)(le & ~3) * kElStride;
+  if (valid) {
+    R* se = stage + (le & 3) * kStageEl;
+#pragma unroll
+    for (int d = 0; d < kNb; ++d) {
+      if (d < nb) {
+        const int b = (arow + d) & 7;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            se[(arow * 8 + b) * 9 + i * 3 + k] = Kr[d][i * 3 + k];
+            if (d != 0) se[(b * 8 + arow) * 9 + k * 3 + i] = Kr[d][i * 3 + k];
+          }
+      }
+    }
+  }
+  __syncwarp();
+  R* Kv = reinterpret_cast<R*>(a.K);
+  const int w0 = le & ~3;
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    if ((int64_t)cta * kElemsPerCta + w0 + j >= ccount) break;   // the same for every lane
+    const R* sej = stage + j * kStageEl;
+    const int32_t* slj = sSlot + (w0 + j) * 64;
+#pragma unroll 2
+    for (int r = (int)lane; r < 576; r += 32) {
+      const int blk = r / 9, c = r - 9 * blk;
+      const int32_t sv = slj[blk];
+      R* dst = Kv + (int64_t)(sv & 0x7fffffff) * 9 + c;
+      const R v = sej[r];
+      if (sv < 0) *dst = v;
+      else atomicAdd(dst, v);
+    }
+  }
+  if (!valid) return;
+  // node of row a = g is the node this thread gathered in phase 1
+  const bool store = sSlot[le * 64 + arow * 9] < 0;   // diagonal block (a, a)
+  double* Rg = a.R + 3 * (int64_t)node;
+  if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
+    atomicAdd(&a.status->nonfinite, 1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double v = (double)Ra[i];
+    if (store) Rg[i] = v - (a.f_ext ? a.load * a.f_ext[3 * (int64_t)node + i] : 0.0);
+    else atomicAdd(Rg + i, v);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
 // UNIF: one material for all elements, passed by value so that its entries are kernel-
 // parameter (constant-bank) operands rather than loads.
 // MAT: 0 the Hill-48 update in the kernel; 1 the strain pass of an external material model
@@ -838,6 +955,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   if constexpr (MAT == 1) return;   // the strain pass assembles nothing
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
+  if constexpr (TANGENT && !FBAR) {
+    // the symmetric element matrix: contraction as below, then the warp's four elements are
+    // staged row-major in shared memory and written out with consecutive lanes on consecutive
+    // entries (a block's 9 values are contiguous in K), so that a warp store touches a few
+    // 32-byte sectors instead of 32 scattered ones
+    phase2_staged<R>(a, sGp, sSlot, le, g, lane, valid, node, blockIdx.x, ccount);
+    return;
+  }
   if (!valid) return;
   const R* G = sGp + (size_t)le * kElStride;
   R Ra[3] = {R(0), R(0), R(0)};

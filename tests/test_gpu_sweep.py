@@ -95,7 +95,10 @@ def test_sweep_zero_state_is_linear_elastic():
     _compare(mesh, u, hist, inputs.config0_material().theta_vector(), "swift", min_plastic=0.0, max_plastic=0.0)
 
 
-BAND = np.array([-1e-3, -1e-5, -3e-6, -1e-6, -1e-7, 0.0, 1e-7, 1e-6, 3e-6, 1e-5, 1e-3])
+# relative distances delta of the trial phi from the yield value: |phi^2 - phi_y^2| ~ 2|delta|
+# phi_y^2, so +-2e-6 and +-4e-6 lie inside the mixed path's FP64 band (1e-5) and +-1e-5 just
+# outside it; FP32 rounding of the trial stress (~1e-7) cannot move any of them across
+BAND = np.array([-1e-3, -1e-5, -4e-6, -2e-6, 2e-6, 4e-6, 1e-5, 1e-3])
 
 
 def _band_state():
@@ -125,26 +128,24 @@ def _band_state():
 
 def test_sweep_trial_states_in_the_fp64_decision_band():
     """R, K and the trial history of both precisions against the oracle where the
-    elastic/plastic decision is a near tie.  FP64 takes the oracle's decision at every point
-    but the exact ties (delta = 0, decided by rounding on either side); the mixed path's trial
-    stress carries FP32 rounding (~1e-7 relative), so it may decide the other way within
-    |delta| <= 1e-6, where both outcomes give the same stress to the mixed tolerances."""
+    elastic/plastic decision is a near tie: both precisions must take the oracle's decision at
+    every point (the tangent jumps between the elastic and the plastic form there, so a wrong
+    decision would show in K), the mixed path by its FP64 test inside the band."""
     mesh, u, hist, th, delta = _band_state()
     Ro, Ko, es = _oracle(mesh, u, hist, th, "swift", None)
     pl_o = es["gp"]["plastic"]
-    off = delta != 0.0                                 # delta = 0 is a tie up to rounding
-    assert np.array_equal(pl_o[off], delta[off] > 0.0)  # the oracle sees the intended side
+    assert np.array_equal(pl_o, delta > 0.0)           # the oracle sees the intended side
     ho = hist_oracle_to_soa(es["h_new"])
     for prec in ("fp64", "mixed"):
         R, K, Ht, st = _gpu(mesh, u, hist, th, "swift", None, prec)
         tol = TOL[prec]
         assert st["local_fail"] == 0
-        n_off = abs(int(st["plastic_gps"]) - int(pl_o.sum()))
-        n_tie = int(np.sum(delta == 0.0)) if prec == "fp64" else int(np.sum(np.abs(delta) <= 1e-6))
-        assert n_off <= n_tie, (prec, n_off, n_tie)
+        assert int(st["plastic_gps"]) == int(pl_o.sum()), (prec, st["plastic_gps"], int(pl_o.sum()))
         assert rel_inf(R, Ro) < tol["R"], (prec, rel_inf(R, Ro))
         dK = (K - Ko).tocsr()
         kerr = np.abs(dK.data).max() / np.abs(Ko.data).max() if dK.nnz else 0.0
         assert kerr < tol["K"], (prec, kerr)
-        herr = np.abs(Ht - ho).max() / max(np.abs(ho[:6]).max(), 1e-12)
-        assert herr < tol["h"], (prec, herr)
+        # eps_p and alpha each against their own scale (alpha_n reaches ~1.8 here, eps_p ~3e-3)
+        herr = np.abs(Ht[:6] - ho[:6]).max() / np.abs(ho[:6]).max()
+        aerr = np.abs(Ht[6] - ho[6]).max() / np.abs(ho[6]).max()
+        assert herr < tol["h"] and aerr < tol["h"], (prec, herr, aerr)
