@@ -141,8 +141,10 @@ typedef struct {
                              Newton solve to pcg_rtol */
   int pcg_persistent;     /* 1 (default): each CG solve is one cooperative kernel launch that runs
                              every iteration on the device (grid barriers, convergence tested each
-                             iteration); 0: chunks of pcg_check_every iterations as CUDA-graph
-                             launches with a host convergence check between chunks */
+                             iteration), its SpMV streaming FP32 K through shared memory by bulk
+                             asynchronous copies in row chunks (FP64 K is loaded directly);
+                             2: the same launch with K always loaded directly by the SpMV's lanes; 0: chunks of pcg_check_every iterations
+                             as CUDA-graph launches with a host convergence check between chunks */
   int adaptive;           /* 1 (default): adaptive load stepping - a load step whose Newton
                              fails is rejected, the state restored, and retried with the
                              increment times cutback (substeps between the requested load

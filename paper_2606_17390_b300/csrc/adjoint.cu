@@ -825,7 +825,7 @@ hfe_status ensure_work(hfe_handle* h, int n_steps) {
     w->ls.graph_len = 0;
   } else {
     double* b;
-    HFE_TRY(aalloc(h, w, &b, 9 * (size_t)h->P.n_blocks)); w->ls.K = b;
+    HFE_TRY(aalloc(h, w, &b, 9 * (size_t)h->P.n_blocks + kKPad)); w->ls.K = b;
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vx = b;
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vr = b;
     HFE_TRY(aalloc(h, w, &b, ndof)); w->ls.vz = b;
@@ -1013,7 +1013,7 @@ hfe_status ensure_transpose(hfe_handle* h, AdjointWork* w) {
       if (ts[b] < 0) return fail(h, HFE_EINVAL, "adjoint: the block pattern is not structurally symmetric");
     }
   HFE_TRY(aalloc(h, w, &w->tslot, (size_t)P.n_blocks));
-  HFE_TRY(aalloc(h, w, &w->KT, 9 * (size_t)P.n_blocks));
+  HFE_TRY(aalloc(h, w, &w->KT, 9 * (size_t)P.n_blocks + kKPad));
   return cuda_check(h, cudaMemcpy(w->tslot, ts.data(), ts.size() * sizeof(int64_t), cudaMemcpyHostToDevice),
                     "copy");
 }

@@ -215,7 +215,7 @@ hfe_status build_pcg_graph(hfe_handle* h, LinSys& ls, int len) {
     cudaGraphExecDestroy(ls.graph);
     ls.graph = nullptr;
   }
-  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  Csr K = csr_of(h);
   PcgVecs<R> v = vecs<R>(ls);
   const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
   cudaGraph_t g;
@@ -262,9 +262,13 @@ hfe_status indefinite_fallback(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs<
 // The solve as one cooperative launch (preconditioner set up and scalars zeroed by the
 // caller); the same outcomes as the chunked form below.
 template <typename R>
-hfe_status pcg_solve_persistent(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs<R>& v, int block3, const double* b,
+hfe_status pcg_solve_persistent(hfe_handle* h, LinSys& ls, Csr K, PcgVecs<R>& v, int block3, const double* b,
                                 double bscale, int64_t* iters_out) {
   const double rt = h->pcg_rtol_now > 0.0 ? h->pcg_rtol_now : h->opt.pcg_rtol;
+  if (h->opt.pcg_persistent == 2) {   // direct loads of K: no row chunks
+    K.chunk32 = K.chunk64 = nullptr;
+    K.n_chunk32 = K.n_chunk64 = 0;
+  }
   HFE_TRY(cuda_check(h, pcg_persistent<R>(K, (const R*)ls.K, h->freem, v, block3, b, bscale, rt * rt,
                                           h->opt.pcg_maxit, h->sc, h->part, partial_slots(),
                                           (uint64_t)h->opt.barrier_spin_limit, h->s),
@@ -293,7 +297,7 @@ hfe_status pcg_solve_persistent(hfe_handle* h, LinSys& ls, const Csr& K, PcgVecs
 // Solve Kt x = bscale * b with PCG (b device FP64 [n_dof]); x left in h->vx (precision R).
 template <typename R>
 hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters_out) {
-  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  Csr K = csr_of(h);
   PcgVecs<R> v = vecs<R>(ls);
   const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
@@ -354,7 +358,7 @@ hfe_status pcg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
 // Non-symmetric K (F-bar element): preconditioned BiCGSTAB in one cooperative launch.
 template <typename R>
 hfe_status bicg_solve(hfe_handle* h, LinSys& ls, const double* b, double bscale, int64_t* iters_out) {
-  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  Csr K = csr_of(h);
   PcgVecs<R> v = vecs<R>(ls);
   const int block3 = h->opt.precond == HFE_PRECOND_BLOCK3;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->bad, 0, sizeof(int), h->s), "memset"));
@@ -389,7 +393,7 @@ hfe_status solve_sys(hfe_handle* h, LinSys& ls, const double* b, double bscale, 
   LinSys& l64 = h->ls_fb64;
   if (l64.K == nullptr) {
     unsigned char* p = nullptr;
-    HFE_TRY(dalloc(h, &p, sizeof(double) * 9 * h->P.n_blocks)); l64.K = p;
+    HFE_TRY(dalloc(h, &p, sizeof(double) * (9 * h->P.n_blocks + kKPad))); l64.K = p;
     for (void** v : {&l64.vx, &l64.vr, &l64.vz, &l64.vp, &l64.vq, &l64.vp2, &l64.vrh, &l64.vy, &l64.vt, &l64.vxt}) {
       HFE_TRY(dalloc(h, &p, sizeof(double) * h->n_dof));
       *v = p;
@@ -511,13 +515,13 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));
   }
   HFE_TRY(dalloc(h, &h->rowptr, h->n_nodes + 1));
-  HFE_TRY(dalloc(h, &h->cols, h->P.n_blocks));
+  HFE_TRY(dalloc(h, &h->cols, h->P.n_blocks + kKPad));
   HFE_TRY(dalloc(h, &h->diag_slot, h->n_nodes));
   HFE_TRY(dalloc(h, &h->slot, h->n_el * 64));
   HFE_TRY(dalloc(h, &h->elems, h->n_el));
   {
     unsigned char* k = nullptr;
-    HFE_TRY(dalloc(h, &k, rsz * 9 * h->P.n_blocks));
+    HFE_TRY(dalloc(h, &k, rsz * (9 * h->P.n_blocks + kKPad)));
     h->K = k;
   }
   HFE_TRY(dalloc(h, &h->R, h->n_dof));
@@ -558,6 +562,25 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
                      "copy"));
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->slot, h->P.slot.data(), 4 * h->P.slot.size(), cudaMemcpyHostToDevice, h->s),
                      "copy"));
+  {
+    // row chunks of the streamed SpMV of the one-launch CG (FP32 and FP64 block values)
+    std::vector<int32_t> c32, c64;
+    stream_chunks(h->P.rowptr.data(), h->n_nodes, stream_rows<float>(), stream_max_blocks<float>(), c32);
+    stream_chunks(h->P.rowptr.data(), h->n_nodes, stream_rows<double>(), stream_max_blocks<double>(), c64);
+    if (!c32.empty()) {
+      HFE_TRY(dalloc(h, &h->chunk32, c32.size()));
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->chunk32, c32.data(), 4 * c32.size(), cudaMemcpyHostToDevice, h->s),
+                         "copy"));
+      h->n_chunk32 = (int64_t)c32.size() - 1;
+    }
+    if (!c64.empty()) {
+      HFE_TRY(dalloc(h, &h->chunk64, c64.size()));
+      HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->chunk64, c64.data(), 4 * c64.size(), cudaMemcpyHostToDevice, h->s),
+                         "copy"));
+      h->n_chunk64 = (int64_t)c64.size() - 1;
+    }
+    HFE_TRY(cuda_check(h, cudaStreamSynchronize(h->s), "sync"));   // c32, c64 live on this frame
+  }
   HFE_TRY(cuda_check(h, cudaMemcpyAsync(h->elems, h->P.elems.data(), 4 * h->n_el, cudaMemcpyHostToDevice, h->s), "copy"));
   // boundary data
   std::vector<uint8_t> freem(h->n_dof, 1);
@@ -780,7 +803,7 @@ hfe_status hfe_spmv(hfe_handle* h, const double* x, double* y) {
   if (h == nullptr || x == nullptr || y == nullptr) return HFE_EINVAL;
   StreamScope scope(h);
   HFE_TRY(copy_in(h, h->tmp64, x, sizeof(double) * h->n_dof));
-  Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  Csr K = csr_of(h);
   if (h->fp64) {
     spmv<double>(K, (const double*)h->K, h->freem, h->tmp64, (double*)h->vq, nullptr, nullptr, h->s);
     HFE_TRY(copy_out(h, y, h->vq, sizeof(double) * h->n_dof));
@@ -959,7 +982,7 @@ hfe_status hfe::newton_steps(hfe_handle* h, int n_steps, const double* t, double
         h->pred_valid = false;
         HFE_TRY(cuda_check(h, cudaMemsetAsync(h->tmp64, 0, sizeof(double) * h->n_dof, h->s), "memset"));
         set_dirichlet(h->tmp64, h->fixed_dof, h->fixed_val, t_new - t_prev, h->n_fixed, h->s);
-        Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+        Csr K = csr_of(h);
         if (h->fp64) {
           spmv_rows<double>(K, (const double*)h->K, h->freem, h->tmp64, (double*)h->vq, h->s);
           predictor_rhs<double>(h->R, (const double*)h->vq, h->f_ext, t_new - t_prev, h->freem, h->b64, h->n_dof, h->s);

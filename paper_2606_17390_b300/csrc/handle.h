@@ -62,6 +62,9 @@ struct hfe_handle {
   double* hist_io = nullptr;    // FP64 [7][n_gp] staging for state transfer (lazy)
   int64_t* rowptr = nullptr;
   int32_t* cols = nullptr;
+  int32_t* chunk32 = nullptr;   // row chunks of the streamed CG SpMV, FP32 / FP64 values
+  int32_t* chunk64 = nullptr;
+  int64_t n_chunk32 = 0, n_chunk64 = 0;
   int64_t* diag_slot = nullptr;
   int32_t* slot = nullptr;
   int32_t* elems = nullptr;
@@ -119,6 +122,16 @@ struct hfe_handle {
   std::vector<void*> allocs;
   hfe::AdjointWork* adj = nullptr;
 };
+
+// The handle's block-CSR pattern with the row chunks of the streamed CG SpMV.
+inline hfe::Csr csr_of(const hfe_handle* h) {
+  hfe::Csr K{h->rowptr, h->cols, h->n_nodes, h->P.n_blocks};
+  K.chunk32 = h->chunk32;
+  K.n_chunk32 = h->n_chunk32;
+  K.chunk64 = h->chunk64;
+  K.n_chunk64 = h->n_chunk64;
+  return K;
+}
 
 
 namespace hfe {

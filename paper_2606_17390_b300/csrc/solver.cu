@@ -717,6 +717,300 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
 
 
 // ---------------------------------------------------------------------------------------
+// One-launch CG with the streamed SpMV.  The iteration is that of pcg_persistent_kernel (same
+// fixed-order reductions, the same two barriers, p formed on the fly from z and p_prev); what
+// changes is how K reaches the SMs.  Each CTA owns a contiguous range of row chunks; a chunk's
+// values and column indices are one contiguous range each in block-CSR order, and one thread
+// brings them into shared memory with bulk asynchronous copies (cp.async.bulk, completion on
+// an mbarrier), two stages deep, so that the HBM stream of K runs ahead of the arithmetic and
+// arrives as whole 16-byte-aligned transfers.  The copy pipeline runs across iterations (K
+// does not change during a solve): the copies of the next pass start while the current one
+// finishes; the kernel drains the copies in flight before it exits.  Every wait is bounded.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bulk copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// counted on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Bounded wait for phase `parity` of bar; false if the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit) {
+  unsigned long long spins = 0;
+  unsigned ns = 32;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++spins > limit) return false;
+    __nanosleep(ns);
+    if (ns < 256) ns *= 2;
+  }
+  return true;
+}
+
+template <typename R>
+struct StreamPipe {
+  unsigned char* base;  // stage s at base + s * kStreamStageBytes
+  uint64_t* bar;
+  int64_t kc0;        // first chunk of this CTA
+  int nck;            // chunks of this CTA
+  long long seq;      // chunks consumed so far (across passes)
+  long long issued;   // chunks issued so far
+};
+
+// Thread 0: start the copy of the CTA's chunk (issued mod nck) into stage (issued mod 2).
+template <typename R>
+__device__ __forceinline__ void stream_issue(StreamPipe<R>& sp, const int32_t* chunk, const int64_t* rowptr,
+                                             const R* vals, const int32_t* cols) {
+  const int st = (int)(sp.issued % kStreamStages);
+  const int64_t c = sp.kc0 + (int64_t)(sp.issued % sp.nck);
+  const int64_t b0 = rowptr[chunk[c]], b1 = rowptr[chunk[c + 1]];
+  const uintptr_t v0 = (uintptr_t)(vals + 9 * b0), v1 = (uintptr_t)(vals + 9 * b1);
+  const uintptr_t c0 = (uintptr_t)(cols + b0), c1 = (uintptr_t)(cols + b1);
+  const uintptr_t va = v0 & ~(uintptr_t)15, vb = (v1 + 15) & ~(uintptr_t)15;
+  const uintptr_t ca = c0 & ~(uintptr_t)15, cb = (c1 + 15) & ~(uintptr_t)15;
+  const unsigned vbytes = (unsigned)(vb - va), cbytes = (unsigned)(cb - ca);
+  uint64_t* bar = sp.bar + st;
+  fence_proxy_async_smem();   // the stage's earlier contents were read through the generic proxy
+  mbar_arrive_expect_tx(bar, vbytes + cbytes);
+  unsigned char* dst = sp.base + (size_t)st * kStreamStageBytes;
+  bulk_g2s(dst, (const void*)va, vbytes, bar);
+  bulk_g2s(dst + stream_val_bytes<R>(), (const void*)ca, cbytes, bar);
+  ++sp.issued;
+}
+
+// Thread 0, before the CTA exits: wait (bounded) for the copies still in flight.
+template <typename R>
+__device__ __forceinline__ void stream_drain(StreamPipe<R>& sp, unsigned long long limit) {
+  for (long long k = sp.seq; k < sp.issued; ++k)
+    mbar_wait(sp.bar + (int)(k % kStreamStages), (unsigned)((k / kStreamStages) & 1), limit);
+}
+
+template <typename R, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) pcg_stream_kernel(const PersistArgs<R> a, const int32_t* chunk,
+                                                                  int64_t n_chunks) {
+  extern __shared__ __align__(128) unsigned char s_stage[];
+  __shared__ __align__(8) uint64_t s_bar[kStreamStages];
+  __shared__ int s_fail;
+  PcgScalars* sc = a.sc;
+  StreamPipe<R> sp;
+  sp.kc0 = (int64_t)blockIdx.x * n_chunks / gridDim.x;
+  const int64_t kc1 = (int64_t)(blockIdx.x + 1) * n_chunks / gridDim.x;
+  sp.nck = (int)(kc1 - sp.kc0);
+  sp.bar = s_bar;
+  sp.seq = 0;
+  sp.issued = 0;
+  sp.base = s_stage;
+  const int64_t n0 = chunk[sp.kc0], n1 = chunk[kc1];
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+#pragma unroll
+    for (int s2 = 0; s2 < kStreamStages; ++s2) mbar_init(&s_bar[s2], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // the first chunk of the first pass is on its way while the set-up below runs
+  if (threadIdx.x == 0 && sp.nck > 0) stream_issue<R>(sp, chunk, a.rowptr, a.vals, a.cols);
+
+  int red = 0;
+  auto allreduce = [&](double v0, double v1, double& t0, double& t1) -> bool {
+    block_sum2(v0, v1);
+    double* pp = a.part + 2 * (size_t)gridDim.x * (red & 1);
+    if (threadIdx.x == 0) {
+      pp[2 * blockIdx.x] = v0;
+      pp[2 * blockIdx.x + 1] = v1;
+    }
+    ++red;
+    return grid_allreduce(&sc->gs, pp, t0, t1, a.spin_limit);
+  };
+  bool alive = true;   // false once a wait has run out: skip to the drain
+  if (a.x0 != nullptr) {
+    spmv_range(a.rowptr, a.cols, a.vals, a.freem, a.x0, a.q, a.x0, n0, n1);
+    __syncthreads();
+  }
+  double rz = 0.0, rr = 0.0, bb = 0.0, unused0 = 0.0;
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
+    R rv[3], zv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t d = 3 * n + i;
+      const R bd = a.freem[d] ? (R)(a.bscale * a.b[d]) : R(0);
+      bb += (double)bd * (double)bd;
+      rv[i] = a.x0 != nullptr ? bd - a.q[d] : bd;
+      a.r[d] = rv[i];
+      a.x[d] = a.x0 != nullptr ? a.x0[d] : R(0);
+      a.pa[d] = R(0);
+    }
+    precond_apply(a.minv, a.block3, n, rv, zv);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a.z[3 * n + i] = zv[i];
+      rz += (double)rv[i] * (double)zv[i];
+      rr += (double)rv[i] * (double)rv[i];
+    }
+  }
+  double rr0 = 0.0, target = 0.0, beta = 0.0, pq = 0.0;
+  int breakdown = 0, done = 0;
+  int64_t it = 0;
+  if (!allreduce(rz, rr, rz, rr) || !allreduce(bb, 0.0, bb, unused0)) alive = false;
+  if (alive) {
+    rr0 = bb;
+    target = a.rtol2 * rr0;
+    breakdown = (isfinite(rz) && isfinite(rr) && isfinite(bb)) ? 0 : 1;
+    done = (!breakdown && rr <= target) ? 1 : 0;
+    if (!breakdown && bb == 0.0) {   // b = 0: x = 0 whatever the initial guess
+      for (int64_t d = 3 * n0 + threadIdx.x; d < 3 * n1; d += kBlock) a.x[d] = R(0);
+      rr = 0.0;
+      done = 1;
+    }
+  }
+  R* pprev = a.pa;
+  R* pcur = a.pb;
+  constexpr int kL = stream_lanes<R>();          // lanes per row
+  constexpr int kU = 32 / kL;                     // blocks per lane and round (32 per row and round)
+  const int grp = threadIdx.x / kL, gl = threadIdx.x % kL;
+  while (alive && !done && !breakdown && it < a.maxit) {
+    const R bt = (R)beta;
+    double dot = 0.0;
+    for (int k = 0; k < sp.nck; ++k) {
+      // chunk k is in stage seq mod 2; once every thread has seen it there and is done with
+      // the previous chunk, that previous stage takes the copy of the next chunk (the next
+      // pass's first after the last), which then runs while this one is computed
+      const int st = (int)(sp.seq % kStreamStages);
+      const bool ok = mbar_wait(&s_bar[st], (unsigned)((sp.seq / kStreamStages) & 1), a.spin_limit);
+      if (__syncthreads_or(!ok)) { alive = false; break; }
+      if (threadIdx.x == 0) stream_issue<R>(sp, chunk, a.rowptr, a.vals, a.cols);
+      const int64_t c = sp.kc0 + k;
+      const int64_t r0 = chunk[c], r1 = chunk[c + 1];
+      const int64_t cb0 = a.rowptr[r0];
+      // the chunk's first value and column sit at these offsets of the stage (alignment slack)
+      const unsigned char* stg = s_stage + (size_t)st * kStreamStageBytes;
+      const R* sv = reinterpret_cast<const R*>(stg + (((uintptr_t)(a.vals + 9 * cb0)) & 15));
+      const int32_t* scol =
+          reinterpret_cast<const int32_t*>(stg + stream_val_bytes<R>() + (((uintptr_t)(a.cols + cb0)) & 15));
+      // rows past the chunk's end take an empty range, so that every lane runs the shuffles
+      const int64_t r = r0 + grp;
+      const bool has = r < r1;
+      const int64_t b = has ? a.rowptr[r] : 0, e = has ? a.rowptr[r + 1] : 0;
+      R a0 = R(0), a1 = R(0), a2 = R(0);
+      for (int64_t j0 = b; j0 < e; j0 += 32) {
+        // all column reads, then all gathers of p = z + beta p_prev, then the arithmetic
+        int64_t col[kU];
+        bool okj[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int64_t j = j0 + gl + u * kL;
+          okj[u] = j < e;
+          col[u] = okj[u] ? (int64_t)scol[j - cb0] : 0;
+        }
+        R x[kU][3];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            x[u][i] = okj[u] ? a.z[3 * col[u] + i] + bt * pprev[3 * col[u] + i] : R(0);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          if (okj[u]) {
+            const R* v = sv + 9 * (j0 + gl + u * kL - cb0);
+            a0 += v[0] * x[u][0] + v[1] * x[u][1] + v[2] * x[u][2];
+            a1 += v[3] * x[u][0] + v[4] * x[u][1] + v[5] * x[u][2];
+            a2 += v[6] * x[u][0] + v[7] * x[u][1] + v[8] * x[u][2];
+          }
+        }
+      }
+#pragma unroll
+      for (int o = kL / 2; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+      }
+      if (has && gl < 3) {
+        const int64_t d = 3 * r + gl;
+        const R o = gl == 0 ? a0 : (gl == 1 ? a1 : a2);
+        const R pd = a.z[d] + bt * pprev[d];
+        const R qd = a.freem[d] ? o : R(0);
+        pcur[d] = pd;
+        a.q[d] = qd;
+        dot += (double)pd * (double)qd;
+      }
+      ++sp.seq;
+    }
+    if (!alive) break;
+    double unused;
+    if (!allreduce(dot, 0.0, pq, unused)) { alive = false; break; }
+    if (!(pq > 0.0) || !isfinite(pq)) {   // negative curvature or breakdown: x stays at the last iterate
+      breakdown = 1;
+      break;
+    }
+    const R al = (R)(rz / pq);
+    double rzn = 0.0, rrn = 0.0;
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += kBlock) {
+      R rv[3], zv[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int64_t d = 3 * n + i;
+        a.x[d] += al * pcur[d];
+        rv[i] = a.r[d] - al * a.q[d];
+        a.r[d] = rv[i];
+      }
+      precond_apply(a.minv, a.block3, n, rv, zv);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        a.z[3 * n + i] = zv[i];
+        rzn += (double)rv[i] * (double)zv[i];
+        rrn += (double)rv[i] * (double)rv[i];
+      }
+    }
+    if (!allreduce(rzn, rrn, rzn, rrn)) { alive = false; break; }
+    ++it;
+    if (!isfinite(rzn) || !isfinite(rrn)) { breakdown = 1; break; }
+    beta = rz > 0.0 ? rzn / rz : 0.0;
+    rz = rzn;
+    rr = rrn;
+    if (rr <= target) done = 1;
+    R* tmp = pprev;
+    pprev = pcur;
+    pcur = tmp;
+  }
+  if (threadIdx.x == 0) {
+    stream_drain<R>(sp, a.spin_limit);
+    if (!alive) atomicExch(&sc->gs.timeout, 1);
+  }
+  if (alive && blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->rr0 = rr0;
+    sc->pq = pq;
+    sc->target = target;
+    sc->iters = (int)it;
+    sc->breakdown = breakdown;
+    sc->done = done;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Persistent BiCGSTAB (van der Vorst 1992) with the same block-Jacobi preconditioner applied
 // on the right, for Newton corrections whose tangent turned out indefinite (CG met p.Kp <= 0).
 // Same row split, fixed-order reductions and fused barriers as the CG kernel: one plain
@@ -930,22 +1224,34 @@ cudaError_t pcg_persistent(const Csr& K, const R* vals, const uint8_t* freem, Pc
                            const double* b, double bscale, double rtol2, int64_t maxit, PcgScalars* sc,
                            double* part, int64_t part_slots, uint64_t spin_limit, cudaStream_t s, const R* x0) {
   constexpr int kMinb = sizeof(R) == 8 ? 3 : 4;   // FP64 blocks need the registers of 3 CTAs per SM
-  const void* fn = (const void*)pcg_persistent_kernel<R, kMinb>;
-  const int cap = kMinb;
+  // FP32 blocks are streamed; FP64 blocks are loaded directly (measured at 3.09M dofs: FP32
+  // 0.311 ms per iteration streamed against 0.343 direct; FP64 1.61 against 1.18 ms, its
+  // 402-block stages holding only half as many rows)
+  const int32_t* chunk = sizeof(R) == 4 ? K.chunk32 : nullptr;
+  const int64_t n_chunks = sizeof(R) == 4 ? K.n_chunk32 : 0;
+  const bool streamed = chunk != nullptr && n_chunks > 0;
+  const void* fn = streamed ? (const void*)pcg_stream_kernel<R, 3> : (const void*)pcg_persistent_kernel<R, kMinb>;
+  const int cap = streamed ? 3 : kMinb;
+  const size_t smem = streamed ? (size_t)kStreamStages * kStreamStageBytes : 0;
   int dev = 0, n_sm = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+  if (e == cudaSuccess && streamed) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem);
   if (e != cudaSuccess) return e;
   // every CTA must be resident (cooperative launch); at most cap per SM, and the partial
   // buffers hold 2 x 2 doubles per CTA
   int64_t grid = (int64_t)n_sm * (per_sm < cap ? per_sm : cap);
   if (grid > part_slots / 4) grid = part_slots / 4;
-  const int64_t useful = (K.n_nodes + kBlock / 8 - 1) / (kBlock / 8);   // an 8-lane group per row at least
-  if (grid > useful) grid = useful;
+  const int64_t useful = streamed ? n_chunks : (K.n_nodes + kBlock / 8 - 1) / (kBlock / 8);
+  if (grid > useful) grid = useful;   // streamed: every CTA owns at least one chunk
   if (grid < 1) grid = 1;
   PersistArgs<R> a{K.rowptr, K.cols, vals, freem, v.minv, b, bscale, rtol2, v.x, v.r, v.z, v.p, v.p2, v.q, x0,
                    K.n_nodes, maxit, block3, sc, part, (unsigned long long)spin_limit};
+  if (streamed) {
+    void* args[] = {&a, (void*)&chunk, (void*)&n_chunks};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, smem, s);
+  }
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kBlock), args, 0, s);
 }
@@ -976,6 +1282,21 @@ template <typename R>
 void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const uint8_t* freem, R* minv,
                    int block3, int* bad, cudaStream_t s) {
   precond_kernel<R><<<nblk(K.n_nodes, 128), 128, 0, s>>>(vals, diag_slot, freem, minv, block3, K.n_nodes, bad);
+}
+
+void stream_chunks(const int64_t* rowptr, int64_t n_nodes, int max_rows, int max_blocks, std::vector<int32_t>& out) {
+  out.clear();
+  out.push_back(0);
+  int64_t r = 0;
+  while (r < n_nodes) {
+    const int64_t r0 = r;
+    while (r < n_nodes && r - r0 < max_rows && rowptr[r + 1] - rowptr[r0] <= max_blocks) ++r;
+    if (r == r0) {   // a row longer than a chunk: no streamed SpMV for this pattern
+      out.clear();
+      return;
+    }
+    out.push_back((int32_t)r);
+  }
 }
 
 void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace hfe {
 
 constexpr int kMaxRedBlocks = 148 * 16;   // grid cap of the reducing kernels (grid-stride)
@@ -13,7 +15,48 @@ struct Csr {            // block-CSR pattern of K over node pairs (3x3 blocks)
   const int32_t* cols;
   int64_t n_nodes;
   int64_t n_blocks;
+  // row chunks of the streamed SpMV of the one-launch CG, for FP32 and FP64 values: chunk c is
+  // rows [chunk[c], chunk[c+1]) (at most kStreamRows rows and stream_max_blocks<R>() blocks);
+  // nullptr / 0 when the pattern has a row too long for a chunk (the CG then loads directly)
+  const int32_t* chunk32 = nullptr;
+  int64_t n_chunk32 = 0;
+  const int32_t* chunk64 = nullptr;
+  int64_t n_chunk64 = 0;
 };
+
+// Streamed SpMV: each CTA of the one-launch CG copies its chunks of K (values and column
+// indices, contiguous in block-CSR order) into shared memory with bulk asynchronous copies,
+// two stages deep.  kStreamStageBytes bounds one stage; a chunk holds at most
+// stream_rows<R>() rows: one row per group of stream_lanes<R>() lanes of the 256-thread CTA.
+template <typename R>
+__host__ __device__ constexpr int stream_lanes() { return sizeof(R) == 4 ? 8 : 16; }
+template <typename R>
+__host__ __device__ constexpr int stream_rows() { return 256 / stream_lanes<R>(); }
+constexpr int kStreamStages = 2;
+constexpr int kStreamStageBytes = 30 * 1024;
+// values (9 R per block) and columns (4 B per block) of a chunk, each with up to 16 B of
+// alignment slack at its start and rounded up to 16 B at its end
+template <typename R>
+__host__ __device__ constexpr int stream_max_blocks() {
+  return (kStreamStageBytes - 128) / (9 * (int)sizeof(R) + 4);
+}
+// a copy of n bytes starting anywhere covers at most n + 30 bytes once both ends are rounded
+template <typename R>
+__host__ __device__ constexpr int stream_val_bytes() {
+  return ((stream_max_blocks<R>() * 9 * (int)sizeof(R) + 32 + 15) / 16) * 16;
+}
+template <typename R>
+__host__ __device__ constexpr int stream_col_bytes() {
+  return ((stream_max_blocks<R>() * 4 + 32 + 15) / 16) * 16;
+}
+static_assert(stream_val_bytes<float>() + stream_col_bytes<float>() <= kStreamStageBytes, "stage");
+static_assert(stream_val_bytes<double>() + stream_col_bytes<double>() <= kStreamStageBytes, "stage");
+// Elements of padding past the end of every K value and column array: the bulk copies round
+// their end up to 16 bytes.
+constexpr int kKPad = 16;
+// Host: greedy row chunks (at most max_rows rows and max_blocks blocks each); empty when a
+// single row has more than max_blocks blocks.
+void stream_chunks(const int64_t* rowptr, int64_t n_nodes, int max_rows, int max_blocks, std::vector<int32_t>& out);
 
 // Grid-barrier words of the persistent solver, each in its own 128-byte line so that the
 // CTAs polling the generation do not contend with the arrivals.
