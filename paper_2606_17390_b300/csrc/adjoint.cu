@@ -758,6 +758,12 @@ __global__ void sub_free_kernel(double* rhs, const double* ubar, const uint8_t* 
   if (d < n && freem[d]) rhs[d] -= ubar[d];
 }
 
+// r = b - K x on the free dofs, 0 on the fixed ones (the FP64 residual of iterative refinement)
+__global__ void refine_residual_kernel(double* r, const double* b, const double* Kx, const uint8_t* freem, int64_t n) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < n) r[d] = freem[d] ? b[d] - Kx[d] : 0.0;
+}
+
 // FP64 history [8][n_gp] -> mixed history (float [7][n_gp] + double cache)
 __global__ void hist64_to_mixed_kernel(const double* h64, void* hm, int64_t n_gp) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -792,6 +798,56 @@ struct AdjointWork {
 };
 
 void adjoint_free(AdjointWork* w) { delete w; }
+
+namespace {
+
+// Mixed path: K lambda = rhs (K the FP64 tangent in w->ls.K, symmetric) by iterative
+// refinement in the precision of the handle's own system: lambda = 0, then repeatedly the
+// FP64 residual r = rhs - K lambda, its correction solved with the FP32 copy of K in FP32 CG
+// (to kInnerRtol, BiCGSTAB if indefinite), lambda += correction, until |r| <= pcg_rtol |rhs|
+// in FP64, the accuracy the FP64 CG solve would be asked for.  Each pass contracts the error
+// by about max(kInnerRtol, kappa eps_32), at the FP32 iteration's cost; a system that stalls
+// is handed to FP64 CG.  lambda is left in w->ls.vx (FP64), the iterations added to *iters.
+hfe_status refined_reverse_solve(hfe_handle* h, AdjointWork* w, int64_t* iters) {
+  constexpr double kInnerRtol = 1e-3;
+  constexpr int kMaxPasses = 8;
+  const int64_t ndof = h->n_dof;
+  const unsigned blocks = (unsigned)((ndof + 255) / 256);
+  double* lam = reinterpret_cast<double*>(w->ls.vx);
+  double* Kx = reinterpret_cast<double*>(w->ls.vq);
+  to_float(reinterpret_cast<const double*>(w->ls.K), reinterpret_cast<float*>(h->K), 9 * h->P.n_blocks, h->s);
+  HFE_TRY(cuda_check(h, cudaMemsetAsync(lam, 0, ndof * sizeof(double), h->s), "memset"));
+  HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->R64, w->rhs, ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
+                     "copy"));
+  const Csr K = csr_of(h);
+  double target = -1.0;
+  for (int pass = 0;; ++pass) {
+    free_norm(w->R64, h->freem, ndof, h->sc, h->part, h->s, nullptr);
+    HFE_TRY(read_status(h));
+    const double rn = std::sqrt(h->h_sc->norm2);
+    if (!std::isfinite(rn)) return fail(h, HFE_ENONFINITE, "adjoint: non-finite residual");
+    if (target < 0.0) target = h->opt.pcg_rtol * rn;
+    if (rn <= target) return HFE_OK;
+    if (pass == kMaxPasses) break;
+    int64_t it = 0;
+    h->pcg_rtol_now = kInnerRtol;
+    const hfe_status st = solve_sys(h, h->ls, w->R64, 1.0, &it);
+    h->pcg_rtol_now = 0.0;
+    HFE_TRY(st);
+    *iters += h->h_sc->iters;
+    add_update<float>(lam, reinterpret_cast<const float*>(h->ls.vx), h->freem, ndof, h->s);
+    spmv<double>(K, reinterpret_cast<const double*>(w->ls.K), h->freem, lam, Kx, nullptr, nullptr, h->s);
+    refine_residual_kernel<<<blocks, 256, 0, h->s>>>(w->R64, w->rhs, Kx, h->freem, ndof);
+    HFE_TRY(cuda_check(h, cudaGetLastError(), "refinement residual"));
+  }
+  // refinement stalled (kappa eps_32 near one): FP64 CG on the whole system
+  const hfe_status st = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
+  HFE_TRY(st);
+  *iters += h->h_sc->iters;
+  return HFE_OK;
+}
+
+}  // namespace
 
 namespace {
 
@@ -1085,11 +1141,16 @@ hfe_status adjoint_run(hfe_handle* h, int n_steps, const double* t_in, const dou
       transpose_blocks_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, h->s>>>((const double*)Kn, w->tslot, w->KT, nb);
       w->ls.K = w->KT;
     }
-    const hfe_status ast = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
+    hfe_status ast;
+    if (!h->fp64 && !h->opt.fbar) {   // mixed: FP32 solves inside FP64 iterative refinement
+      ast = refined_reverse_solve(h, w, &adj_pcg);
+    } else {
+      ast = solve_sys(h, w->ls, w->rhs, 1.0, nullptr);
+      if (ast == HFE_OK) adj_pcg += h->h_sc->iters;
+    }
     w->ls.K = Kn;
     h->allow_indefinite = false;
     HFE_TRY(ast);
-    adj_pcg += h->h_sc->iters;
     launch_vjp(h, w, false, un, w->h_prev, reinterpret_cast<const double*>(w->ls.vx));   // pass B
     HFE_TRY(cuda_check(h, cudaMemcpyAsync(w->mu, w->hbar, 7 * ngp * sizeof(double), cudaMemcpyDeviceToDevice, h->s),
                        "copy"));
