@@ -47,13 +47,6 @@ template <bool FBAR> struct Lay {
   static constexpr int kElStride = 8 * kGpStride + 8;
 };
 
-// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned); completion
-// is awaited by cp_async_wait_all in the copying thread, then made visible by a barrier
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // 4-vector shared-memory stores and loads of R values (16-byte aligned addresses)
 template <typename R> struct V4;
@@ -198,12 +191,14 @@ constexpr int kStageEl = 584;   // staging words per element: 576 used; 584 = 8 
                                 // the four elements of a warp over the banks
 
 template <typename R>
-__device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, const int32_t* sSlot, int le, int g,
-                                              unsigned lane, bool valid, int node, unsigned cta, int64_t ccount) {
+__device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le, int g, int e, unsigned lane,
+                                              bool valid, int node, unsigned cta, int64_t ccount) {
   constexpr int kGpStride = Lay<false>::kGpStride;
   constexpr int kElStride = Lay<false>::kElStride;
   static_assert(4 * kStageEl <= 4 * kElStride, "staging must fit in the warp's records");
   const int arow = g;
+  // the element's slot-map row is read during the write-out: start bringing it into L1
+  if (valid && g < 2) asm volatile("prefetch.global.L1 [%0];\n" ::"l"(a.slot + (int64_t)e * 64 + 32 * g));
   constexpr int kNb = 5;
   const int nb = (arow < 4) ? 5 : 4;
   R Kr[kNb][9];
@@ -273,9 +268,10 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, const 
   const int w0 = le & ~3;
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
+    const int ej = __shfl_sync(0xffffffffu, e, 8 * j);             // element of lanes 8j..8j+7
     if ((int64_t)cta * kElemsPerCta + w0 + j >= ccount) break;   // the same for every lane
     const R* sej = stage + j * kStageEl;
-    const int32_t* slj = sSlot + (w0 + j) * 64;
+    const int32_t* slj = a.slot + (int64_t)ej * 64;
 #pragma unroll 2
     for (int r = (int)lane; r < 576; r += 32) {
       const int blk = r / 9, c = r - 9 * blk;
@@ -288,7 +284,7 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, const 
   }
   if (!valid) return;
   // node of row a = g is the node this thread gathered in phase 1
-  const bool store = sSlot[le * 64 + arow * 9] < 0;   // diagonal block (a, a)
+  const bool store = a.slot[(int64_t)e * 64 + arow * 9] < 0;   // diagonal block (a, a)
   double* Rg = a.R + 3 * (int64_t)node;
   if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
     atomicAdd(&a.status->nonfinite, 1);
@@ -312,9 +308,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   constexpr int kGpStride = Lay<FBAR>::kGpStride;
   constexpr int kElStride = Lay<FBAR>::kElStride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sNode = reinterpret_cast<R*>(smem_raw);                     // [16][8][6]: dX(3), du(3)
-  R* sGp = sNode + kElemsPerCta * 8 * 6;                           // [16][kElStride]
-  int32_t* sSlot = reinterpret_cast<int32_t*>(sGp + kElemsPerCta * kElStride);   // [16][64]
+  // [16][kElStride] Gauss-point records; an element's first 48 words hold its nodal data
+  // [8][6] (dX, du) until the kinematics have read them
+  R* sGp = reinterpret_cast<R*>(smem_raw);
 
   const int tid = threadIdx.x;
   const int le = tid >> 3;
@@ -329,13 +325,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   const MR* matR = reinterpret_cast<const MR*>(a.mat);
   const int mi = a.mat_per_element ? e : 0;
 
-  // the element's 64 slot-map entries (used by phase 2), copied to shared memory while
-  // phase 1 runs: 16 chunks of 16 bytes, two per thread of the element
-  if (valid) {
-    const int32_t* srow = a.slot + (int64_t)e * 64;
-    cp_async16(sSlot + le * 64 + 4 * g, srow + 4 * g);
-    cp_async16(sSlot + le * 64 + 4 * (g + 8), srow + 4 * (g + 8));
-  }
+  // the element's 64 slot-map entries (256 B, read in phase 2): into L2 while phase 1 runs
+  if (valid && g < 2) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.slot + (int64_t)e * 64 + 32 * g));
 
   // history of this Gauss point, loaded first so that it arrives during the kinematics
   const int64_t ng = a.n_gp;
@@ -363,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     double u0 = a.u[3 * (int64_t)node], u1 = a.u[3 * (int64_t)node + 1], u2 = a.u[3 * (int64_t)node + 2];
     const int src = lane & 24;
     double bu0 = __shfl_sync(gmask, u0, src), bu1 = __shfl_sync(gmask, u1, src), bu2 = __shfl_sync(gmask, u2, src);
-    R* dst = sNode + (le * 8 + g) * 6;
+    R* dst = sGp + (size_t)le * kElStride + g * 6;
     if constexpr (sizeof(R) == 8) {
       double x0 = a.X[3 * (int64_t)node], x1 = a.X[3 * (int64_t)node + 1], x2 = a.X[3 * (int64_t)node + 2];
       double bx0 = __shfl_sync(gmask, x0, src), bx1 = __shfl_sync(gmask, x1, src), bx2 = __shfl_sync(gmask, x2, src);
@@ -381,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   int flag_detj = 0, flag_local = 0, flag_plastic = 0, local_iters = 0;
 
   if (valid) {
-    const R* nd = sNode + le * 8 * 6;
+    const R* nd = sGp + (size_t)le * kElStride;
     // ---- S2 kinematics: dN/dxi at Gauss point g, J0 = dX/dxi, g_a = J0^{-T} dN_a
     const R c3 = R(0.57735026918962576451);
     const R xg = (g & 1) ? c3 : -c3, yg = (g & 2) ? c3 : -c3, zg = (g & 4) ? c3 : -c3;
@@ -438,6 +429,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
         for (int n = 1; n < 8; ++n) s += nd[n * 6 + 3 + i] * gN[n][j];
         H[i][j] = s;
       }
+    // the nodal data share the element's record area: every thread of the element has read
+    // them before any writes its record
+    __syncwarp(gmask);
     R F[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -948,9 +942,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       if (mx > 0) atomicMax(&a.status->max_local_iters, mx);
     }
   }
-  // an element's shared data (Gauss-point records, slot rows) is written and read by its own
-  // 8 threads, all in one warp: a warp barrier suffices, and warps move on independently
-  cp_async_wait_all();
+  // an element's Gauss-point records are written and read by its own 8 threads, all in one
+  // warp: a warp barrier suffices, and warps move on independently
   __syncwarp();
   if constexpr (MAT == 1) return;   // the strain pass assembles nothing
 
@@ -960,7 +953,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     // staged row-major in shared memory and written out with consecutive lanes on consecutive
     // entries (a block's 9 values are contiguous in K), so that a warp store touches a few
     // 32-byte sectors instead of 32 scattered ones
-    phase2_staged<R>(a, sGp, sSlot, le, g, lane, valid, node, blockIdx.x, ccount);
+    phase2_staged<R>(a, sGp, le, g, e, lane, valid, node, blockIdx.x, ccount);
     return;
   }
   if (!valid) return;
@@ -1013,7 +1006,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
     }
     R* Kv = reinterpret_cast<R*>(a.K);
-    const int32_t* sl = sSlot + le * 64;
+    const int32_t* sl = a.slot + (int64_t)e * 64;
 #pragma unroll
     for (int d = 0; d < kNb; ++d) {
       if (d < nb) {
@@ -1089,7 +1082,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   }
   {
     // node of row a = g is the node this thread gathered in phase 1
-    const bool store = sSlot[le * 64 + arow * 9] < 0;   // diagonal block (a, a)
+    const bool store = a.slot[(int64_t)e * 64 + arow * 9] < 0;   // diagonal block (a, a)
     double* Rg = a.R + 3 * (int64_t)node;
     if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
       atomicAdd(&a.status->nonfinite, 1);
@@ -1297,8 +1290,7 @@ void launch_hist_export(const void* hist, double* user, bool fp64, int64_t n_gp,
 template <typename R, bool TANGENT, bool UNIF, bool FBAR, int MAT = 0>
 static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cudaStream_t s) {
   using MR = typename MatOf<R>::T;
-  const size_t smem = sizeof(R) * (kElemsPerCta * 8 * 6 + (size_t)kElemsPerCta * Lay<FBAR>::kElStride) +
-                     sizeof(int32_t) * kElemsPerCta * 64;
+  const size_t smem = sizeof(R) * (size_t)kElemsPerCta * Lay<FBAR>::kElStride;
   // the dynamic shared-memory limit is a per-device function attribute: set it on every call
   // (a host-side call, no synchronisation) so that each device the handle runs on has it
   cudaFuncSetAttribute(gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
