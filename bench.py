@@ -300,6 +300,95 @@ def config1_forward_section(stream):
     return out
 
 
+def config3_fd_section(stream, h=1e-6):
+    """Config 3's gradient check at full size (200 x 100 x 4 plate, Swift, 20 steps, the nine
+    uniform parameters at the seeded +-20 % point, target = FP64 forward at the true
+    parameters + N(0, (1e-3 max|u|)^2)): the adjoint gradient (FP64 handle, and the default
+    mixed handle with the FP64 refinement) against central differences of J with a relative
+    step h per parameter, each J from an FP64 forward solve (Newton 1e-12) that starts every
+    load step from the pass at the evaluation point (warm start).  Compared as
+    theta_i dJ/dtheta_i."""
+    from paper_2606_17390_b300 import hfe
+    m3, bc3, mat3, t3 = inputs.config3_problem()
+    th_true = mat3.theta_vector()
+    th = inputs.perturbed_theta(th_true)
+    idx = np.arange(2, 11)
+    fp64 = dict(newton_rtol=1e-12, pcg_rtol=1e-13)
+    t0 = time.perf_counter()
+    with hfe.from_inputs(m3, bc3, mat3, precision="fp64", theta=th_true, stream=stream.cuda_stream, **fp64) as s:
+        u_true, _ = s.forward(t3)
+    u_gt = u_true + inputs.noise(u_true.shape, 1e-3 * np.abs(u_true).max())
+    out = {"workload": f"config 3: perforated plate 200x100x4 ({m3.n_el} elements, {m3.n_dof} dofs), Swift, "
+                       f"{len(t3)} steps, 9 parameters (F, G, H, L, M, N, K, eps0, n)", "relative_step": h}
+    grads = {}
+    for prec, opts in (("fp64", fp64), ("mixed", {})):
+        with hfe.from_inputs(m3, bc3, mat3, precision=prec, theta=th, stream=stream.cuda_stream, **opts) as s:
+            J, g, _ = s.adjoint(t3, u_gt)
+        grads[prec] = th[idx] * g[0][idx]
+        out[f"J_{prec}"] = J
+    d_fd = np.empty(idx.size)
+    with hfe.from_inputs(m3, bc3, mat3, precision="fp64", theta=th, stream=stream.cuda_stream, **fp64) as s:
+        s.set_warm_start("record")
+        s.forward(t3, want_u=False)
+        s.set_warm_start("use")
+        for k, i in enumerate(idx):
+            Jpm = []
+            for sgn in (1.0, -1.0):
+                tp = th.copy()
+                tp[i] *= 1.0 + sgn * h
+                s.set_material(tp, mat3.Theta)
+                s.set_state(None, None)
+                u, _ = s.forward(t3)
+                Jpm.append(float(np.sum((u - u_gt) ** 2)))
+            d_fd[k] = (Jpm[0] - Jpm[1]) / (2.0 * h)
+        s.set_warm_start("off")
+    names = ["F", "G", "H", "L", "M", "N", "K", "eps0", "n"]
+    out["theta_dJ_dtheta_fd"] = dict(zip(names, d_fd.tolist()))
+    for prec, d in grads.items():
+        out[f"theta_dJ_dtheta_{prec}"] = dict(zip(names, d.tolist()))
+        out[f"{prec}_vs_fd_rel_norm"] = float(np.linalg.norm(d - d_fd) / np.linalg.norm(d_fd))
+        out[f"{prec}_vs_fd_rel_per_parameter"] = dict(zip(names, (np.abs(d - d_fd) / np.abs(d_fd)).tolist()))
+    out["mixed_vs_fp64_rel_norm"] = float(np.linalg.norm(grads["mixed"] - grads["fp64"]) / np.linalg.norm(grads["fp64"]))
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def inverse_section(nx, stream, maxfun=90):
+    """The inverse loop on config 3 (Sec. 3.3 normalisation rho in [-1, 1], L-BFGS-B with the
+    paper's stopping criteria, warm start under the 10 % rule): nine parameters from the seeded
+    +-20 % start, bounds theta_true x [0.5, 1.5], noisy target from the mixed forward at the true
+    parameters; w scales J at the start to 1e3 (so that the relative stopping tests act).
+    Reports the recovered parameters against the true ones, iterations, evaluations and the
+    time per evaluation (one gradient call each)."""
+    from paper_2606_17390_b300 import hfe, inverse
+    m3, bc3, mat3, t3 = inputs.config3_problem(nx, nx // 2, 4 if nx >= 200 else 2)
+    th_true = mat3.theta_vector()
+    th0 = inputs.perturbed_theta(th_true)
+    idx = np.arange(2, 11)
+    tmin, tref = 0.5 * th_true[idx], th_true[idx]
+    with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th_true, stream=stream.cuda_stream) as s:
+        u_true, _ = s.forward(t3)
+    u_gt = u_true + inputs.noise(u_true.shape, 1e-3 * np.abs(u_true).max())
+    with hfe.from_inputs(m3, bc3, mat3, precision="mixed", theta=th0, stream=stream.cuda_stream) as s:
+        J0, _, _ = s.adjoint(t3, u_gt)
+        w = 1e3 / J0
+        res = inverse.identify(s, t3, u_gt, th0, idx, tmin, tref, w=w, criteria=dict(maxfun=maxfun),
+                               warm_start=True)
+    names = ["F", "G", "H", "L", "M", "N", "K", "eps0", "n"]
+    rel = (res.theta[idx] - th_true[idx]) / th_true[idx]
+    rel0 = (th0[idx] - th_true[idx]) / th_true[idx]
+    return {"workload": f"config 3: perforated plate {nx}x{nx // 2} ({m3.n_el} elements, {m3.n_dof} dofs), "
+                        f"{len(t3)} steps, 9 parameters, mixed forward with FP64 refinement, warm start",
+            "w": w, "J_start": float(res.history[0][0]), "J_end": res.J, "iterations": res.iterations,
+            "evaluations": res.evaluations, "warm_passes": res.warm_passes, "success": res.success,
+            "message": res.message, "seconds": res.seconds, "seconds_per_evaluation": res.seconds / max(1, res.evaluations),
+            "theta_true": dict(zip(names, th_true[idx].tolist())),
+            "theta_start": dict(zip(names, th0[idx].tolist())),
+            "theta_recovered": dict(zip(names, res.theta[idx].tolist())),
+            "relative_error_start": dict(zip(names, rel0.tolist())),
+            "relative_error_recovered": dict(zip(names, rel.tolist()))}
+
+
 def barlat_map_section(reps, stream, dev, with_cpu):
     """Device time of hfe_barlat_return_map on the App. B robustness map and on a 64-times
     larger batch (CUDA events on the launching stream, after 3 warm-up launches), outcome
@@ -461,6 +550,11 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
+    ap.add_argument("--config3-fd", action="store_true",
+                    help="config 3's full-size gradient against FP64 central differences (18 forward solves)")
+    ap.add_argument("--inverse-nx", type=int, default=0,
+                    help="plate resolution of the config-3 inverse loop (0 = skip; 200 = config 3)")
+    ap.add_argument("--inverse-maxfun", type=int, default=90)
     ap.add_argument("--no-config1-forward", dest="config1_forward", action="store_false",
                     help="skip config 1's full-size forward in FP64 and FP32-mixed (per-step errors)")
     ap.add_argument("--forward-predictors", default="2",
@@ -753,6 +847,17 @@ def main():
         barlat_fe = barlat_fe_section(args.barlat_fe_n, stream, dev)
 
     config1 = config1_forward_section(stream) if args.config1_forward else None
+    config3_fd = inverse_run = None
+    if args.config3_fd:
+        try:
+            config3_fd = config3_fd_section(stream)
+        except Exception as e:   # reported in the line instead of ending the benchmark
+            config3_fd = {"error": f"{type(e).__name__}: {e}"[:200]}
+    if args.inverse_nx > 0:
+        try:
+            inverse_run = inverse_section(args.inverse_nx, stream, args.inverse_maxfun)
+        except Exception as e:
+            inverse_run = {"error": f"{type(e).__name__}: {e}"[:200]}
 
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -778,7 +883,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
-                "pcg": pcg, "adjoint": adjoint, "forward": forward, "config1_forward": config1, "fbar_sweep": fbar,
+                "pcg": pcg, "adjoint": adjoint, "forward": forward, "config1_forward": config1, "config3_gradient_fd": config3_fd,
+                "inverse": inverse_run, "fbar_sweep": fbar,
                 "barlat_map": barlat, "barlat_fe_sweep": barlat_fe,
                 "gpu_launches": (info["n_colors"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
