@@ -830,8 +830,10 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_stream_kernel(const PersistA
     mbar_fence_init();
   }
   __syncthreads();
-  // the first chunk of the first pass is on its way while the set-up below runs
-  if (threadIdx.x == 0 && sp.nck > 0) stream_issue<R>(sp, chunk, a.rowptr, a.vals, a.cols);
+  // the first kStreamStages - 1 chunks of the first pass are on their way while the set-up
+  // below runs
+  if (threadIdx.x == 0 && sp.nck > 0)
+    for (int k = 0; k < kStreamStages - 1; ++k) stream_issue<R>(sp, chunk, a.rowptr, a.vals, a.cols);
 
   int red = 0;
   auto allreduce = [&](double v0, double v1, double& t0, double& t1) -> bool {
@@ -894,9 +896,10 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_stream_kernel(const PersistA
     const R bt = (R)beta;
     double dot = 0.0;
     for (int k = 0; k < sp.nck; ++k) {
-      // chunk k is in stage seq mod 2; once every thread has seen it there and is done with
-      // the previous chunk, that previous stage takes the copy of the next chunk (the next
-      // pass's first after the last), which then runs while this one is computed
+      // chunk k is in stage seq mod kStreamStages; once every thread has seen it there and
+      // is done with the previous chunk, that previous stage takes the copy of the chunk
+      // kStreamStages - 1 ahead (wrapping into the next pass), so that kStreamStages - 1
+      // copies run while this chunk is computed
       const int st = (int)(sp.seq % kStreamStages);
       const bool ok = mbar_wait(&s_bar[st], (unsigned)((sp.seq / kStreamStages) & 1), a.spin_limit);
       if (__syncthreads_or(!ok)) { alive = false; break; }

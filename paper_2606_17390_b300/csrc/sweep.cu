@@ -311,6 +311,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   // [16][kElStride] Gauss-point records; an element's first 48 words hold its nodal data
   // [8][6] (dX, du) until the kinematics have read them
   R* sGp = reinterpret_cast<R*>(smem_raw);
+  // the next colour's launch may start its CTAs once every CTA of this one has started: its
+  // phase 1 reads nothing this launch writes, and its phase 2 waits for this launch below
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 
   const int tid = threadIdx.x;
   const int le = tid >> 3;
@@ -946,6 +949,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   // warp: a warp barrier suffices, and warps move on independently
   __syncwarp();
   if constexpr (MAT == 1) return;   // the strain pass assembles nothing
+  // launched as a dependent of the previous colour: its writes to K and R must be complete
+  // and visible before this colour adds to the same blocks (a no-op for other launches)
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
   if constexpr (TANGENT && !FBAR) {
@@ -1298,11 +1304,31 @@ static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cu
   MR rec;
   if (UNIF) memcpy(&rec, a.mat_host, sizeof(MR));   // host copy of the single record
   else memset(&rec, 0, sizeof(MR));
+  // colours after the first are programmatic dependents of the previous colour's launch: a
+  // colour's Gauss-point updates (phase 1) overlap the previous colour's last CTAs, and its
+  // assembly (phase 2) waits for that launch to complete (griddepcontrol.wait).  The first
+  // colour is an ordinary launch: it reads what the kernels before the sweep wrote (u).
+  bool first = true;
   for (size_t c = 0; c + 1 < off.size(); ++c) {
     int64_t cnt = off[c + 1] - off[c];
     if (cnt <= 0) continue;
     unsigned blocks = (unsigned)((cnt + kElemsPerCta - 1) / kElemsPerCta);
-    gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
+    if (first) {
+      gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT><<<blocks, kThreads, smem, s>>>(a, rec, off[c], cnt);
+      first = false;
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT>, a, rec, off[c], cnt);
   }
 }
 
