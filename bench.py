@@ -353,6 +353,36 @@ def config3_fd_section(stream, h=1e-6):
     return out
 
 
+def directional_fd_check(mesh, bc, mat, ts, theta, grad, u_gt, stream, h=1e-6, seed=41):
+    """The adjoint gradient along a seeded direction against central differences of J: v with
+    entries U(-1, 1) on the nine identified parameters, theta(s) = theta * (1 + s v), and
+    dJ/ds = sum_i grad_i theta_i v_i against (J(h) - J(-h)) / 2h, each J from an FP64 forward
+    (Newton 1e-12) that starts every load step from a recorded pass at theta (warm start)."""
+    from paper_2606_17390_b300 import hfe
+    idx = np.arange(2, 11)
+    v = np.zeros_like(theta)
+    v[idx] = np.random.default_rng(seed).uniform(-1.0, 1.0, idx.size)
+    d_adj = float(np.sum(grad * theta * v))
+    t0 = time.perf_counter()
+    Js = []
+    with hfe.from_inputs(mesh, bc, mat, precision="fp64", theta=theta, stream=stream.cuda_stream,
+                         newton_rtol=1e-12, pcg_rtol=1e-13) as s:
+        s.set_warm_start("record")
+        s.forward(ts, want_u=False)
+        s.set_warm_start("use")
+        for sgn in (1.0, -1.0):
+            s.set_material(theta * (1.0 + sgn * h * v), mat.Theta)
+            s.set_state(None, None)
+            u, _ = s.forward(ts)
+            Js.append(float(np.sum((u - u_gt) ** 2)))
+        s.set_warm_start("off")
+    d_fd = (Js[0] - Js[1]) / (2.0 * h)
+    return {"direction": f"theta_i (1 + s v_i), v_i ~ U(-1, 1) on the 9 parameters (seed {seed})",
+            "relative_step": h, "dJ_ds_adjoint": d_adj, "dJ_ds_central_difference": d_fd,
+            "relative_error": abs(d_adj - d_fd) / abs(d_fd), "seconds": time.perf_counter() - t0,
+            "forward": "FP64, Newton 1e-12, warm-started from a pass at the evaluation point"}
+
+
 def inverse_section(nx, stream, maxfun=90):
     """The inverse loop on config 3 (Sec. 3.3 normalisation rho in [-1, 1], L-BFGS-B with the
     paper's stopping criteria, warm start under the 10 % rule): nine parameters from the seeded
@@ -550,6 +580,8 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
+    ap.add_argument("--no-gradient-check", dest="gradient_check", action="store_false",
+                    help="skip the directional central-difference check of the config-3 gradient")
     ap.add_argument("--config3-fd", action="store_true",
                     help="config 3's full-size gradient against FP64 central differences (18 forward solves)")
     ap.add_argument("--inverse-nx", type=int, default=0,
@@ -772,6 +804,12 @@ def main():
             t0 = time.perf_counter()
             J3, g3, ast = s3.adjoint(t3, u_gt)
             t_adj = time.perf_counter() - t0
+            gcheck = None
+            if args.adjoint_config == 3 and args.gradient_check:
+                try:
+                    gcheck = directional_fd_check(m3, bc3, mat3, t3, th_eval, g3[0], u_gt, stream)
+                except Exception as e:   # reported in the line instead of ending the benchmark
+                    gcheck = {"error": f"{type(e).__name__}: {e}"[:200]}
             if args.warm_delta > 0:
                 # warm start (Sec. 3.6): the next evaluation of an inverse loop, parameters moved
                 # by up to warm_delta (relative, seeded), forward from the record vs cold
@@ -804,7 +842,7 @@ def main():
                    "gradient_over_forward": t_adj / t_fwd, "reverse_over_forward": ast["solve_ms"] * 1e-3 / t_fwd,
                    "forward_newton_iters": fst["newton_iters"], "forward_pcg_iters": fst["pcg_iters"],
                    "forward_substeps": fst["substeps"], "gradient_substeps": ast["substeps"],
-                   "warm_start": warm}
+                   "warm_start": warm, "gradient_check": gcheck}
 
     # end-to-end forward solve of the 100^3 clamped-platen compression (10 load steps, mixed):
     # Newton, PCG and substep counts, and the in-solve Gauss-point update rate
