@@ -162,6 +162,12 @@ typedef struct {
                              solve then returns HFE_EBARRIER.  Default 2^25 (seconds: a wait that
                              long means the CTAs are not all resident).  0 makes every wait give
                              up at its first poll (a way to exercise the failure path) */
+  int64_t assembly_l2_bytes; /* launch order of the sweeps (set at hfe_create): the elements are
+                             grouped into slabs by the K rows they write, each slab's rows holding
+                             about this many bytes of K, and one launch runs one colour of one
+                             slab; the colours of a slab then add into rows that are still in L2.
+                             0: one launch per colour over the whole mesh.  Results differ from
+                             one setting to another by the order of the additions only */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */
@@ -196,6 +202,8 @@ typedef struct {
   int32_t n_colors;
   int32_t precision;
   int64_t device_bytes;
+  int64_t n_slabs;        /* slabs of the launch order (options.assembly_l2_bytes) */
+  int64_t n_launches;     /* launches of one sweep: the non-empty (slab, colour) groups */
 } hfe_info;
 
 /* Fill *opt with defaults for the given precision. */
@@ -203,8 +211,8 @@ void hfe_default_options(hfe_options* opt, int precision);
 
 /* Build the handle: copies the mesh, boundary data and material to the device, builds the
  * block-CSR pattern of K (3x3 blocks, one block per node pair sharing an element), the
- * element-to-block slot map, and a conflict-free element colouring (Sec. 2.2.5 "GPU-
- * accelerated global sparse matrix assembly" describes the assembly it replaces).
+ * element-to-block slot map, a conflict-free element colouring and the launch order of the
+ * sweeps (options.assembly_l2_bytes); Sec. 2.2.5 describes the assembly this replaces.
  * stream: a cudaStream_t the library orders its work after and before (NULL = legacy
  * default stream).  Returns HFE_EINVAL for out-of-range node ids, HFE_EDETJ for an
  * element with det(dX/dxi) <= 0 at a Gauss point. */

@@ -52,7 +52,7 @@ struct VjpArgs {
   const int32_t* slot;
   const double* lam;         // pass B: adjoint solution [n_dof]
   const double* mu;          // pass A: history cotangent [7][n_gp]
-  double* ubar;              // pass A: nodal cotangent (first colour stores, later colours add)
+  double* ubar;              // pass A: nodal cotangent (first launch stores, later launches add)
   double* hbar;              // [7][n_gp]: pass A writes, pass B adds
   double* thbar;             // [n_el][11], accumulated
   DevStatus* status;
@@ -1041,7 +1041,7 @@ void launch_vjp(hfe_handle* h, AdjointWork* w, bool pass_a, const double* u, con
   a.local_maxit = h->opt.local_maxit;
   a.local_tol = h->opt.local_tol;
   a.fbar = h->opt.fbar != 0;
-  const auto& off = h->P.color_off;
+  const auto& off = h->P.launch_off;
   for (size_t c = 0; c + 1 < off.size(); ++c) {
     const int64_t cnt = off[c + 1] - off[c];
     if (cnt <= 0) continue;

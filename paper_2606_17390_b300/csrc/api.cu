@@ -175,13 +175,13 @@ hfe_status sweep_ex(hfe_handle* h, const double* u_dev, double load, int mode, d
   a.ext_plastic = h->ext_pl;
   HFE_TRY(cuda_check(h, cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->s), "memset"));
   if (h->barlat != nullptr) {   // Barlat: strain pass, the Gauss-point update, assembly pass
-    launch_gp_sweep_ext(a, fp64, 1, mode, h->P.color_off, h->s);
+    launch_gp_sweep_ext(a, fp64, 1, mode, h->P.launch_off, h->s);
     launch_barlat_gp(h->barlat, fp64, h->ext_eps, hist, hist_trial, h->n_gp, h->ext_T, h->ext_D, h->ext_pl,
                      mode == HFE_SWEEP_TANGENT ? 1 : 0, h->status, h->ext_work, h->ext_it, h->ext_st, h->s);
-    launch_gp_sweep_ext(a, fp64, 2, mode, h->P.color_off, h->s);
+    launch_gp_sweep_ext(a, fp64, 2, mode, h->P.launch_off, h->s);
     return HFE_OK;
   }
-  launch_gp_sweep(a, fp64, mode, h->P.color_off, h->s);
+  launch_gp_sweep(a, fp64, mode, h->P.launch_off, h->s);
   return HFE_OK;
 }
 
@@ -445,6 +445,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->max_cutbacks = 8;
   o->fbar = 0;
   o->barrier_spin_limit = (int64_t)1 << 25;
+  o->assembly_l2_bytes = 0;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
@@ -465,6 +466,7 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   if (h->opt.max_cutbacks < 0) return fail(h, HFE_EINVAL, "options: max_cutbacks must be >= 0");
   if (h->opt.predictor < 0 || h->opt.predictor > 3) return fail(h, HFE_EINVAL, "options: predictor must be 0 to 3");
   if (h->opt.barrier_spin_limit < 0) return fail(h, HFE_EINVAL, "options: barrier_spin_limit must be >= 0");
+  if (h->opt.assembly_l2_bytes < 0) return fail(h, HFE_EINVAL, "options: assembly_l2_bytes must be >= 0");
   h->fp64 = h->opt.precision == HFE_PRECISION_FP64;
   h->user = reinterpret_cast<cudaStream_t>(stream);
   HFE_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"));
@@ -485,7 +487,11 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     std::memcpy(conn_h.data(), mesh->conn, conn_h.size() * 4);
   }
   std::string perr;
-  if (!build_pattern(h->n_nodes, h->n_el, conn_h.data(), h->P, perr)) return fail(h, HFE_EINVAL, "mesh: " + perr);
+  // slabs of about assembly_l2_bytes of K rows (blocks of 9 values of the handle's precision)
+  const int64_t slab_blocks =
+      h->opt.assembly_l2_bytes > 0 ? std::max<int64_t>(1, h->opt.assembly_l2_bytes / (9 * (h->fp64 ? 8 : 4))) : 0;
+  if (!build_pattern(h->n_nodes, h->n_el, conn_h.data(), slab_blocks, h->P, perr))
+    return fail(h, HFE_EINVAL, "mesh: " + perr);
   StreamScope scope(h);
   // device allocations
   const bool f64 = h->fp64 != 0;
@@ -691,6 +697,8 @@ hfe_status hfe_get_info(const hfe_handle* h, hfe_info* info) {
   info->n_blocks = h->P.n_blocks;
   info->n_fixed = h->n_fixed;
   info->n_colors = h->P.n_colors;
+  info->n_slabs = h->P.n_slabs;
+  info->n_launches = (int64_t)h->P.launch_off.size() - 1;
   info->precision = h->opt.precision;
   info->device_bytes = (int64_t)h->device_bytes;
   return HFE_OK;

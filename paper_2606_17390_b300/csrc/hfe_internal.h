@@ -66,7 +66,7 @@ struct SweepArgs {
   const void* mat_host;    // host copy of the record when one material serves every element, else nullptr
   int mat_per_element;
   int hardening;
-  const int32_t* elems;    // colour-sorted element ids
+  const int32_t* elems;    // element ids in launch order (conflict-free ranges)
   const int32_t* slot;     // [n_el*64] block index | store flag (bit 31)
   void* K;                 // [n_blocks*9] float or double
   double* R;               // [n_dof]
@@ -89,7 +89,7 @@ struct SweepArgs {
 void launch_material_setup(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,
                            MatRecF* outf, int* bad, cudaStream_t s);
 // mode: HFE_SWEEP_RESIDUAL / HFE_SWEEP_TANGENT; fp64 selects the plain FP64 kernel.
-void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
+void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& launch_off,
                      cudaStream_t s);
 // The Barlat Yld2004-18p material of a handle (barlat.cu): parameters and local controls,
 // and the strain-driven update of every Gauss point between the two external sweep passes.
@@ -103,7 +103,7 @@ void launch_barlat_gp(const BarlatModel* m, bool fp64_hist, const double* eps_M,
                       DevStatus* status, double* work, int32_t* iters, int8_t* st, cudaStream_t s);
 // External material model (FP64 or mixed sweep): pass 1 = strain pass (ext_eps out), pass 2 =
 // assembly with ext_T / ext_D / ext_plastic (mode HFE_SWEEP_RESIDUAL or HFE_SWEEP_TANGENT).
-void launch_gp_sweep_ext(const SweepArgs& a, bool fp64, int pass, int mode, const std::vector<int64_t>& color_off,
+void launch_gp_sweep_ext(const SweepArgs& a, bool fp64, int pass, int mode, const std::vector<int64_t>& launch_off,
                          cudaStream_t s);
 void launch_sigma_cache(void* hist, bool fp64, const MatRec* mat, int mat_per_element, int hardening,
                         int64_t n_gp, cudaStream_t s);

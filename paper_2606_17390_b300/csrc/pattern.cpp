@@ -2,7 +2,7 @@
 // of nodes that share an element), a conflict-free element colouring, and the element-to-
 // block slot map that replaces the paper's triplet -> COO -> CSR assembly (App. E,
 // Algorithm gpu_chunked_assembly): slot[e][a][b] is the index of block (conn[e][a],
-// conn[e][b]); bit 31 marks the first colour (in launch order) that writes the block, which
+// conn[e][b]); bit 31 marks the first launch (in launch order) that writes the block, which
 // stores instead of adding, so K needs no clearing pass.
 #include "pattern.h"
 
@@ -28,7 +28,8 @@ static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>&
   for (auto& x : th) x.join();
 }
 
-bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, Pattern& P, std::string& err) {
+bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, int64_t slab_blocks, Pattern& P,
+                   std::string& err) {
   for (int64_t i = 0; i < n_el * 8; ++i) {
     if (conn[i] < 0 || conn[i] >= n_nodes) {
       err = "conn[" + std::to_string(i) + "] out of range";
@@ -113,14 +114,40 @@ bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, Pattern& 
     ncol = std::max(ncol, c + 1);
   }
   P.n_colors = ncol;
-  P.color_off.assign(ncol + 1, 0);
-  for (int64_t e = 0; e < n_el; ++e) P.color_off[color[e] + 1]++;
-  for (int c = 0; c < ncol; ++c) P.color_off[c + 1] += P.color_off[c];
-  P.elems.resize(n_el);
-  {
-    std::vector<int64_t> fill(P.color_off.begin(), P.color_off.end() - 1);
-    for (int64_t e = 0; e < n_el; ++e) P.elems[fill[color[e]]++] = (int32_t)e;
+  // launch order.  A launch is one colour, so its elements share no node; the launches are
+  // ordered by slab, then colour: the eight or so colours of a slab add into a band of K
+  // rows small enough to stay in L2 between them, instead of each colour sweeping all of K.
+  // The slab of an element is that of the first K block of its lowest-numbered node's row.
+  std::vector<int64_t> slab(n_el, 0);
+  P.n_slabs = 1;
+  if (slab_blocks > 0) {
+    for (int64_t e = 0; e < n_el; ++e) {
+      int32_t lo = conn[e * 8];
+      for (int a = 1; a < 8; ++a) lo = std::min(lo, conn[e * 8 + a]);
+      slab[e] = P.rowptr[lo] / slab_blocks;
+      P.n_slabs = std::max(P.n_slabs, slab[e] + 1);
+    }
   }
+  // colour order, then a stable counting sort by slab
+  std::vector<int64_t> coff(ncol + 1, 0);
+  for (int64_t e = 0; e < n_el; ++e) coff[color[e] + 1]++;
+  for (int c = 0; c < ncol; ++c) coff[c + 1] += coff[c];
+  std::vector<int32_t> by_colour(n_el);
+  for (int64_t e = 0; e < n_el; ++e) by_colour[coff[color[e]]++] = (int32_t)e;
+  std::vector<int64_t> soff(P.n_slabs + 1, 0);
+  for (int64_t e = 0; e < n_el; ++e) soff[slab[e] + 1]++;
+  for (int64_t g = 0; g < P.n_slabs; ++g) soff[g + 1] += soff[g];
+  P.elems.resize(n_el);
+  for (int64_t i = 0; i < n_el; ++i) {
+    const int32_t e = by_colour[i];
+    P.elems[soff[slab[e]]++] = e;
+  }
+  P.launch_off.assign(1, 0);
+  for (int64_t i = 1; i < n_el; ++i) {
+    const int32_t e0 = P.elems[i - 1], e1 = P.elems[i];
+    if (slab[e0] != slab[e1] || color[e0] != color[e1]) P.launch_off.push_back(i);
+  }
+  if (n_el > 0) P.launch_off.push_back(n_el);
   // slot map
   P.slot.resize(n_el * 64);
   parallel_for(n_el, [&](int64_t b, int64_t e_end) {
@@ -136,7 +163,7 @@ bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, Pattern& 
       }
     }
   });
-  // first-writer flags in launch order (colours in order; one writer per block per colour)
+  // first-writer flags in launch order (one writer per block per launch)
   std::vector<uint8_t> seen(P.n_blocks, 0);
   for (int64_t i = 0; i < n_el; ++i) {
     int64_t e = P.elems[i];

@@ -15,8 +15,9 @@
 // rotated first Piola-Kirchhoff stress in shared memory.  Phase 2: one thread per
 // (element, node row a) contracts the eight Gauss points into the 3x24 row block of K^e
 // and the 3 entries of R^e, and scatters them through the element-to-block slot map.
-// Elements of one launch share no node (colouring), so the scatter needs no atomics; the
-// first colour that touches a block stores, later colours add (bit 31 of the slot).
+// Elements of one launch share no node (one colour of one slab of the launch order), so
+// the scatter needs no atomics; the first launch that touches a block stores, later
+// launches add (bit 31 of the slot).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -184,9 +185,9 @@ template <> struct MatOf<double> { using T = MatRec; };
 // warp's own (already consumed) record area, row-major [a][b][3x3] per element, and the warp
 // writes its four elements out with consecutive lanes on consecutive entries: a block's nine
 // values are contiguous in K and an element row's blocks lie close together, so each warp
-// store covers a few 32-byte sectors.  The first colour that touches a block stores (bit 31 of
-// the slot), later colours add: one writer per block per launch, launches in colour order, so
-// the sums are deterministic.
+// store covers a few 32-byte sectors.  The first launch that touches a block stores (bit 31 of
+// the slot), later launches add: one writer per block per launch, launches in a fixed order,
+// so the sums are deterministic.
 constexpr int kStageEl = 584;   // staging words per element: 576 used; 584 = 8 mod 32 spreads
                                 // the four elements of a warp over the banks
 
@@ -272,13 +273,18 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
     if ((int64_t)cta * kElemsPerCta + w0 + j >= ccount) break;   // the same for every lane
     const R* sej = stage + j * kStageEl;
     const int32_t* slj = a.slot + (int64_t)ej * 64;
-#pragma unroll 2
-    for (int r = (int)lane; r < 576; r += 32) {
-      const int blk = r / 9, c = r - 9 * blk;
-      const int32_t sv = slj[blk];
-      R* dst = Kv + (int64_t)(sv & 0x7fffffff) * 9 + c;
+    // lane l writes entries l + 32 i (i < 18) of the 576: all 18 slot loads are issued
+    // before the first write so that their latencies overlap
+    int32_t sv[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) sv[i] = slj[((int)lane + 32 * i) / 9];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) {
+      const int r = (int)lane + 32 * i;
+      const int c = r - 9 * (r / 9);
+      R* dst = Kv + (int64_t)(sv[i] & 0x7fffffff) * 9 + c;
       const R v = sej[r];
-      if (sv < 0) *dst = v;
+      if (sv[i] < 0) *dst = v;
       else atomicAdd(dst, v);
     }
   }
@@ -311,8 +317,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   // [16][kElStride] Gauss-point records; an element's first 48 words hold its nodal data
   // [8][6] (dX, du) until the kinematics have read them
   R* sGp = reinterpret_cast<R*>(smem_raw);
-  // the next colour's launch may start its CTAs once every CTA of this one has started: its
-  // phase 1 reads nothing this launch writes, and its phase 2 waits for this launch below
+  // the next launch may start its CTAs once every CTA of this one has started: its phase 1
+  // reads nothing this launch writes, and its phase 2 waits for this launch below
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 
   const int tid = threadIdx.x;
@@ -949,8 +955,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   // warp: a warp barrier suffices, and warps move on independently
   __syncwarp();
   if constexpr (MAT == 1) return;   // the strain pass assembles nothing
-  // launched as a dependent of the previous colour: its writes to K and R must be complete
-  // and visible before this colour adds to the same blocks (a no-op for other launches)
+  // launched as a dependent of the previous launch: its writes to K and R must be complete
+  // and visible before this launch adds to the same blocks (a no-op for the first launch)
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
@@ -1027,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
             for (int i = 0; i < 3; ++i)
 #pragma unroll
               for (int k = 0; k < 3; ++k) dst[i * 3 + k] = tr == 0 ? Kr[d][i * 3 + k] : Kr[d][k * 3 + i];
-          } else {   // one writer per block per launch and launches in colour order: deterministic
+          } else {   // one writer per block per launch, launches in a fixed order: deterministic
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -1304,10 +1310,10 @@ static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cu
   MR rec;
   if (UNIF) memcpy(&rec, a.mat_host, sizeof(MR));   // host copy of the single record
   else memset(&rec, 0, sizeof(MR));
-  // colours after the first are programmatic dependents of the previous colour's launch: a
-  // colour's Gauss-point updates (phase 1) overlap the previous colour's last CTAs, and its
-  // assembly (phase 2) waits for that launch to complete (griddepcontrol.wait).  The first
-  // colour is an ordinary launch: it reads what the kernels before the sweep wrote (u).
+  // launches after the first are programmatic dependents of the previous launch: their
+  // Gauss-point updates (phase 1) overlap the previous launch's last CTAs, and their assembly
+  // (phase 2) waits for that launch to complete (griddepcontrol.wait).  The first launch is
+  // an ordinary one: it reads what the kernels before the sweep wrote (u).
   bool first = true;
   for (size_t c = 0; c + 1 < off.size(); ++c) {
     int64_t cnt = off[c + 1] - off[c];
@@ -1339,23 +1345,23 @@ static void launch_mode(const SweepArgs& a, int mode, const std::vector<int64_t>
   else u ? launch_typed<R, false, true, FBAR>(a, off, s) : launch_typed<R, false, false, FBAR>(a, off, s);
 }
 
-void launch_gp_sweep_ext(const SweepArgs& a, bool fp64, int pass, int mode, const std::vector<int64_t>& color_off,
+void launch_gp_sweep_ext(const SweepArgs& a, bool fp64, int pass, int mode, const std::vector<int64_t>& launch_off,
                          cudaStream_t s) {
   if (fp64) {
-    if (pass == 1) launch_typed<double, false, true, false, 1>(a, color_off, s);
-    else if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true, true, false, 2>(a, color_off, s);
-    else launch_typed<double, false, true, false, 2>(a, color_off, s);
+    if (pass == 1) launch_typed<double, false, true, false, 1>(a, launch_off, s);
+    else if (mode == HFE_SWEEP_TANGENT) launch_typed<double, true, true, false, 2>(a, launch_off, s);
+    else launch_typed<double, false, true, false, 2>(a, launch_off, s);
   } else {
-    if (pass == 1) launch_typed<float, false, true, false, 1>(a, color_off, s);
-    else if (mode == HFE_SWEEP_TANGENT) launch_typed<float, true, true, false, 2>(a, color_off, s);
-    else launch_typed<float, false, true, false, 2>(a, color_off, s);
+    if (pass == 1) launch_typed<float, false, true, false, 1>(a, launch_off, s);
+    else if (mode == HFE_SWEEP_TANGENT) launch_typed<float, true, true, false, 2>(a, launch_off, s);
+    else launch_typed<float, false, true, false, 2>(a, launch_off, s);
   }
 }
 
-void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& color_off,
+void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& launch_off,
                      cudaStream_t s) {
-  if (fp64) a.fbar ? launch_mode<double, true>(a, mode, color_off, s) : launch_mode<double, false>(a, mode, color_off, s);
-  else a.fbar ? launch_mode<float, true>(a, mode, color_off, s) : launch_mode<float, false>(a, mode, color_off, s);
+  if (fp64) a.fbar ? launch_mode<double, true>(a, mode, launch_off, s) : launch_mode<double, false>(a, mode, launch_off, s);
+  else a.fbar ? launch_mode<float, true>(a, mode, launch_off, s) : launch_mode<float, false>(a, mode, launch_off, s);
 }
 
 }  // namespace hfe

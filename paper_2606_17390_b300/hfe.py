@@ -49,7 +49,7 @@ class Options(C.Structure):
                 ("local_maxit", C.c_int), ("local_tol", C.c_double), ("ckpt_every", C.c_int),
                 ("predictor", C.c_int), ("ew_forcing", C.c_int), ("pcg_persistent", C.c_int),
                 ("adaptive", C.c_int), ("cutback", C.c_double), ("max_cutbacks", C.c_int), ("fbar", C.c_int),
-                ("barrier_spin_limit", C.c_int64)]
+                ("barrier_spin_limit", C.c_int64), ("assembly_l2_bytes", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -67,7 +67,8 @@ class Stats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_el", C.c_int64), ("n_dof", C.c_int64), ("n_gp", C.c_int64),
                 ("n_blocks", C.c_int64), ("n_fixed", C.c_int64), ("n_colors", C.c_int32),
-                ("precision", C.c_int32), ("device_bytes", C.c_int64)]
+                ("precision", C.c_int32), ("device_bytes", C.c_int64), ("n_slabs", C.c_int64),
+                ("n_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

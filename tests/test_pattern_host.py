@@ -2,8 +2,9 @@
 without CUDA) against an independent numpy construction: the block-CSR pattern (one 3x3
 block per pair of nodes sharing an element, sorted columns, the diagonal slot), the element
 colouring (no two elements of a colour share a node; 8 colours on a structured hex mesh),
-the element-to-block slot map, and the first-writer flags (exactly one per block, on its
-first touch in launch order); malformed meshes are refused with a message."""
+the launch order (one colour of one slab of K rows per launch, slabs in row order), the
+element-to-block slot map, and the first-writer flags (exactly one per block, on its first
+touch in launch order); malformed meshes are refused with a message."""
 import os
 import shutil
 import subprocess
@@ -27,20 +28,22 @@ template <typename T> static void put(FILE* f, const std::vector<T>& v) {
 }
 int main(int argc, char** argv) {
   FILE* in = fopen(argv[1], "rb");
-  long long nn, ne;
-  if (fread(&nn, 8, 1, in) != 1 || fread(&ne, 8, 1, in) != 1) return 3;
+  long long nn, ne, sb;
+  if (fread(&nn, 8, 1, in) != 1 || fread(&ne, 8, 1, in) != 1 || fread(&sb, 8, 1, in) != 1) return 3;
   std::vector<int32_t> conn(ne * 8);
   if (fread(conn.data(), 4, conn.size(), in) != conn.size()) return 3;
   fclose(in);
   hfe::Pattern P;
   std::string err;
-  if (!hfe::build_pattern(nn, ne, conn.data(), P, err)) {
+  if (!hfe::build_pattern(nn, ne, conn.data(), sb, P, err)) {
     fprintf(stderr, "%s\n", err.c_str());
     return 2;
   }
   FILE* out = fopen(argv[2], "wb");
   put(out, P.rowptr); put(out, P.cols); put(out, P.diag_slot); put(out, P.slot);
-  put(out, P.elems); put(out, P.color_off);
+  put(out, P.elems); put(out, P.launch_off);
+  std::vector<long long> ns(1, (long long)P.n_slabs);
+  put(out, ns);
   fclose(out);
   return 0;
 }
@@ -60,23 +63,23 @@ def driver(tmp_path_factory):
     return exe, d
 
 
-def _run(driver, n_nodes, conn):
+def _run(driver, n_nodes, conn, slab_blocks=0):
     exe, d = driver
     inp, out = d / "conn.bin", d / "pattern.bin"
     with open(inp, "wb") as f:
-        np.array([n_nodes, conn.shape[0]], dtype=np.int64).tofile(f)
+        np.array([n_nodes, conn.shape[0], slab_blocks], dtype=np.int64).tofile(f)
         np.ascontiguousarray(conn, dtype=np.int32).tofile(f)
     r = subprocess.run([str(exe), str(inp), str(out)], capture_output=True, text=True)
     if r.returncode != 0:
         return None, r.stderr.strip()
     buf = open(out, "rb").read()
     parts, off = [], 0
-    for dt in (np.int64, np.int32, np.int64, np.int32, np.int32, np.int64):
+    for dt in (np.int64, np.int32, np.int64, np.int32, np.int32, np.int64, np.int64):
         n = int(np.frombuffer(buf, np.int64, 1, off)[0])
         off += 8
         parts.append(np.frombuffer(buf, dt, n, off).copy())
         off += n * np.dtype(dt).itemsize
-    return dict(zip(("rowptr", "cols", "diag_slot", "slot", "elems", "color_off"), parts)), ""
+    return dict(zip(("rowptr", "cols", "diag_slot", "slot", "elems", "launch_off", "n_slabs"), parts)), ""
 
 
 def _check(P, n_nodes, conn):
@@ -95,9 +98,10 @@ def _check(P, n_nodes, conn):
     slot = (raw & 0x7FFFFFFF).astype(np.int64).reshape(n_el, 8, 8)
     assert np.array_equal(rows[slot], np.broadcast_to(conn[:, :, None], slot.shape))
     assert np.array_equal(P["cols"][slot], np.broadcast_to(conn[:, None, :], slot.shape))
-    # colouring: a permutation grouped by colour, no shared node inside a colour
-    elems, off = P["elems"], P["color_off"]
+    # launch ranges: a permutation cut into ranges, no shared node inside a range
+    elems, off = P["elems"], P["launch_off"]
     assert np.array_equal(np.sort(elems), np.arange(n_el)) and off[0] == 0 and off[-1] == n_el
+    assert np.all(np.diff(off) > 0)
     for c in range(len(off) - 1):
         nodes = conn[elems[off[c]:off[c + 1]]].ravel()
         assert np.unique(nodes).size == nodes.size, c
@@ -110,6 +114,23 @@ def _check(P, n_nodes, conn):
     assert np.array_equal(first.reshape(-1)[order], expect)
     assert first.sum() == P["cols"].size
     return len(off) - 1
+
+
+def _colours(conn):
+    """Greedy colouring in element order: an element takes the smallest colour that no earlier
+    element sharing a node has."""
+    n_el = conn.shape[0]
+    colour = np.full(n_el, -1)
+    by_node = {}
+    for e in range(n_el):
+        used = {colour[o] for n in conn[e] for o in by_node.get(int(n), [])}
+        c = 0
+        while c in used:
+            c += 1
+        colour[e] = c
+        for n in conn[e]:
+            by_node.setdefault(int(n), []).append(e)
+    return colour
 
 
 def test_structured_box_eight_colours(driver):
@@ -133,6 +154,34 @@ def test_unstructured_meshes(driver, case):
     P, err = _run(driver, mesh.n_nodes, conn)
     assert P is not None, err
     assert _check(P, mesh.n_nodes, np.asarray(conn, dtype=np.int64)) >= 8
+
+
+@pytest.mark.parametrize("slab_blocks", [60, 250, 10 ** 9])
+def test_slab_launch_order(driver, slab_blocks):
+    """Launches ordered by slab (slab_blocks consecutive K blocks, an element in the slab of
+    the first block of its lowest node's row), then by colour; one (slab, colour) per launch."""
+    mesh = inputs.box_mesh(6, 5, 4)
+    conn = np.asarray(mesh.conn, dtype=np.int64)
+    P, err = _run(driver, mesh.n_nodes, mesh.conn, slab_blocks)
+    assert P is not None, err
+    n_launch = _check(P, mesh.n_nodes, conn)
+    colour = _colours(conn)
+    slab = P["rowptr"][conn.min(axis=1)] // slab_blocks
+    assert int(P["n_slabs"][0]) == slab.max() + 1
+    elems, off = P["elems"], P["launch_off"]
+    key = slab[elems] * 64 + colour[elems]
+    assert np.all(np.diff(key) >= 0)                     # slabs in order, colours within a slab
+    for c in range(n_launch):                            # one (slab, colour) per launch, all of it
+        k = np.unique(key[off[c]:off[c + 1]])
+        assert k.size == 1 and np.count_nonzero(key == k[0]) == off[c + 1] - off[c]
+    assert n_launch == np.unique(slab * 64 + colour).size
+    if slab_blocks == 10 ** 9:
+        assert n_launch == 8 and int(P["n_slabs"][0]) == 1
+    else:
+        assert int(P["n_slabs"][0]) > 1
+    # within a launch the elements keep their id order
+    for c in range(n_launch):
+        assert np.all(np.diff(elems[off[c]:off[c + 1]]) > 0)
 
 
 def test_malformed_meshes_refused(driver):
