@@ -43,10 +43,11 @@ LOAD = 0.5
 # element contraction with the symmetric K^e 3.4k).
 ALG_FLOPS_PER_GP = 8.3e3
 # algorithmic DRAM bytes per element of a mixed tangent sweep (one node per element on a
-# large structured mesh): conn 32, nodal X (FP32) 12 and u (FP64) 24, history in and out
-# 8 Gauss points x (7 FP32 values + the FP64 sigma_y cache) = 288 each, R 24, K 27 blocks
-# x 36 B = 972
-ALG_BYTES_PER_EL = 32 + 12 + 24 + 288 + 288 + 24 + 972
+# large structured mesh): conn 32, nodal X (FP32) 12 and u (FP64) 24, history in 8 Gauss
+# points x (7 FP32 values + the FP64 sigma_y cache) = 288, history out 8 x 7 FP32 = 224 (the
+# trial cache is not written: it is recomputed from alpha when a step is committed), R 24,
+# K 27 blocks x 36 B = 972
+ALG_BYTES_PER_EL = 32 + 12 + 24 + 288 + 224 + 24 + 972
 
 
 def _peaks():
@@ -580,6 +581,9 @@ def main():
                     help="3: nine uniform parameters on the 200x100x4 plate; 4: per-element fields (use --adjoint-nx 400)")
     ap.add_argument("--forward-n", type=int, default=100, help="cube size of the end-to-end forward run (0 = skip)")
     ap.add_argument("--forward-steps", type=int, default=10)
+    ap.add_argument("--assembly-l2-mb", type=float, default=-1.0,
+                    help="K bytes (MB) of a slab of the sweep's launch order (-1: the library default, "
+                         "3/4 of L2; 0: colour order)")
     ap.add_argument("--no-gradient-check", dest="gradient_check", action="store_false",
                     help="skip the directional central-difference check of the config-3 gradient")
     ap.add_argument("--config3-fd", action="store_true",
@@ -620,12 +624,16 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def make(precision, **opts):
+        if args.assembly_l2_mb >= 0:
+            opts.setdefault("assembly_l2_bytes", int(args.assembly_l2_mb * 2 ** 20))
         s = hfe.from_inputs(mesh, bc, mat, precision=precision, stream=stream.cuda_stream, **opts)
         s.set_state(u, hist)
         return s
 
     solver = make(args.precision)
     info = solver.info()
+    hist_mb = (64 if args.precision == "fp64" else 36) * 8 * mesh.n_el / 1e6
+    k_mb = (72 if args.precision == "fp64" else 36) * info["n_blocks"] / 1e6
     u_d = torch.from_numpy(u).to(dev)
     R_d = torch.empty(mesh.n_dof, dtype=torch.float64, device=dev)
     rn_d = torch.empty(1, dtype=torch.float64, device=dev)
@@ -680,8 +688,8 @@ def main():
         _, _, st = solver.sweep(u_d, LOAD, tangent=True, R_out=R_d, rnorm_out=rn_d, stats=True)
         sweep_ms.append(st["sweep_ms"])
     sweep_ms_avg = float(np.mean(sweep_ms))
-    launch_ms = sweep_ms_avg / info["n_colors"]
-    el_per_launch = mesh.n_el / info["n_colors"]
+    launch_ms = sweep_ms_avg / info["n_launches"]
+    el_per_launch = mesh.n_el / info["n_launches"]
     flops_launch = ALG_FLOPS_PER_GP * 8 * el_per_launch
     peak_derived = 148 * 128 * 2 * 2.032e9 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
     peak_fp32 = measured_fp32_tflops(dev, stream)
@@ -701,7 +709,8 @@ def main():
     if os.path.exists(traffic_file):
         with open(traffic_file) as f:
             tr = json.load(f)
-        if tr.get("precision") == args.precision and tr.get("n") == args.n:
+        if (tr.get("precision") == args.precision and tr.get("n") == args.n
+                and tr.get("n_launches") == info["n_launches"]):
             roofline["traffic"] = tr.get("dram_bytes_per_launch")
 
     # end to end through the C ABI with host buffers (pinned): u in, R and |R_free| out
@@ -917,14 +926,17 @@ def main():
                                        "Hill-48 + Swift, clamped-platen compression, mid-step state, tangent sweep "
                                        "+ assembly + residual norm",
                            "n_el": mesh.n_el, "n_dof": mesh.n_dof, "n_blocks": info["n_blocks"],
-                           "precision": args.precision, "l2": "inputs larger than L2 (history 512 MB, K 982 MB)",
+                           "precision": args.precision,
+                           "l2": f"inputs larger than L2 (history {hist_mb:.0f} MB, K {k_mb:.0f} MB)",
+                           "launch_order": f"{info['n_slabs']} slabs of K rows x {info['n_colors']} colours = "
+                                           f"{info['n_launches']} launches per sweep",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "fp64": fp64,
                 "residual_sweep": {"ms_per_step": ms_res, "value": world * 8 * mesh.n_el / (ms_res * 1e-3)},
                 "pcg": pcg, "adjoint": adjoint, "forward": forward, "config1_forward": config1, "config3_gradient_fd": config3_fd,
                 "inverse": inverse_run, "fbar_sweep": fbar,
                 "barlat_map": barlat, "barlat_fe_sweep": barlat_fe,
-                "gpu_launches": (info["n_colors"] + 1) * args.steps,
+                "gpu_launches": (info["n_launches"] + 1) * args.steps,
                 "clocks": clk.summary(), "peaks_source": src,
                 "plastic_gps": st0["plastic_gps"], "max_local_iters": st0["max_local_iters"]}
         print(json.dumps(line), flush=True)

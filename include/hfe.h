@@ -166,8 +166,9 @@ typedef struct {
                              grouped into slabs by the K rows they write, each slab's rows holding
                              about this many bytes of K, and one launch runs one colour of one
                              slab; the colours of a slab then add into rows that are still in L2.
-                             0: one launch per colour over the whole mesh.  Results differ from
-                             one setting to another by the order of the additions only */
+                             -1 (default): 3/4 of the device's L2; 0: one launch per colour over
+                             the whole mesh.  Results differ from one setting to another by the
+                             order of the additions only */
 } hfe_options;
 
 /* Statistics of the last hfe_forward / hfe_adjoint / hfe_gp_sweep call. */

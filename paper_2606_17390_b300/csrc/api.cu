@@ -445,7 +445,7 @@ void hfe_default_options(hfe_options* o, int precision) {
   o->max_cutbacks = 8;
   o->fbar = 0;
   o->barrier_spin_limit = (int64_t)1 << 25;
-  o->assembly_l2_bytes = 0;
+  o->assembly_l2_bytes = -1;
 }
 
 hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material* mat, const hfe_options* opt,
@@ -466,7 +466,7 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
   if (h->opt.max_cutbacks < 0) return fail(h, HFE_EINVAL, "options: max_cutbacks must be >= 0");
   if (h->opt.predictor < 0 || h->opt.predictor > 3) return fail(h, HFE_EINVAL, "options: predictor must be 0 to 3");
   if (h->opt.barrier_spin_limit < 0) return fail(h, HFE_EINVAL, "options: barrier_spin_limit must be >= 0");
-  if (h->opt.assembly_l2_bytes < 0) return fail(h, HFE_EINVAL, "options: assembly_l2_bytes must be >= 0");
+  if (h->opt.assembly_l2_bytes < -1) return fail(h, HFE_EINVAL, "options: assembly_l2_bytes must be >= -1");
   h->fp64 = h->opt.precision == HFE_PRECISION_FP64;
   h->user = reinterpret_cast<cudaStream_t>(stream);
   HFE_TRY(cuda_check(h, cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"));
@@ -487,10 +487,31 @@ hfe_status hfe_create(const hfe_mesh* mesh, const hfe_bc* bc, const hfe_material
     std::memcpy(conn_h.data(), mesh->conn, conn_h.size() * 4);
   }
   std::string perr;
-  // slabs of about assembly_l2_bytes of K rows (blocks of 9 values of the handle's precision)
-  const int64_t slab_blocks =
-      h->opt.assembly_l2_bytes > 0 ? std::max<int64_t>(1, h->opt.assembly_l2_bytes / (9 * (h->fp64 ? 8 : 4))) : 0;
-  if (!build_pattern(h->n_nodes, h->n_el, conn_h.data(), slab_blocks, h->P, perr))
+  // launch order: slabs of K rows (blocks of 9 values of the handle's precision) of
+  // assembly_l2_bytes, or (-1) of 0.4-0.8 of this device's L2 as the planner picks, the rest
+  // of L2 left to the streamed per-point data
+  hfe::SlabPlan plan;
+  {
+    const int64_t bb = 9 * (h->fp64 ? 8 : 4);
+    int64_t lo = 0, hi = 0;
+    if (h->opt.assembly_l2_bytes == -1) {
+      int dev = 0, l2 = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        return fail(h, HFE_ECUDA, "L2 size query");
+      lo = (int64_t)l2 * 2 / 5;
+      hi = (int64_t)l2 * 4 / 5;
+    } else {
+      lo = hi = h->opt.assembly_l2_bytes;
+    }
+    if (hi > 0) {
+      plan.min_blocks = std::max<int64_t>(1, lo / bb);
+      plan.max_blocks = std::max<int64_t>(1, hi / bb);
+      plan.resident_ctas = sweep_resident_ctas(h->fp64 != 0, h->opt.fbar != 0);
+      plan.el_per_cta = sweep_elems_per_cta();
+      if (plan.resident_ctas <= 0) return fail(h, HFE_ECUDA, "sweep occupancy query");
+    }
+  }
+  if (!build_pattern(h->n_nodes, h->n_el, conn_h.data(), plan, h->P, perr))
     return fail(h, HFE_EINVAL, "mesh: " + perr);
   StreamScope scope(h);
   // device allocations

@@ -89,6 +89,10 @@ struct SweepArgs {
 void launch_material_setup(const double* theta, const double* Theta, int64_t n_mat, MatRec* out,
                            MatRecF* outf, int* bad, cudaStream_t s);
 // mode: HFE_SWEEP_RESIDUAL / HFE_SWEEP_TANGENT; fp64 selects the plain FP64 kernel.
+// CTAs of the tangent sweep kernel resident on the current device at once (occupancy x SMs;
+// <= 0 on a failed query), and the elements one CTA takes
+int64_t sweep_resident_ctas(bool fp64, bool fbar);
+int64_t sweep_elems_per_cta();
 void launch_gp_sweep(const SweepArgs& a, bool fp64, int mode, const std::vector<int64_t>& launch_off,
                      cudaStream_t s);
 // The Barlat Yld2004-18p material of a handle (barlat.cu): parameters and local controls,

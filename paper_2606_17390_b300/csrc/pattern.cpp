@@ -28,7 +28,7 @@ static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>&
   for (auto& x : th) x.join();
 }
 
-bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, int64_t slab_blocks, Pattern& P,
+bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, const SlabPlan& plan, Pattern& P,
                    std::string& err) {
   for (int64_t i = 0; i < n_el * 8; ++i) {
     if (conn[i] < 0 || conn[i] >= n_nodes) {
@@ -120,11 +120,35 @@ bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, int64_t s
   // The slab of an element is that of the first K block of its lowest-numbered node's row.
   std::vector<int64_t> slab(n_el, 0);
   P.n_slabs = 1;
-  if (slab_blocks > 0) {
+  P.slab_blocks = 0;
+  if (plan.max_blocks > 0 && n_el > 0) {
+    std::vector<int64_t> first(n_el);
     for (int64_t e = 0; e < n_el; ++e) {
       int32_t lo = conn[e * 8];
       for (int a = 1; a < 8; ++a) lo = std::min(lo, conn[e * 8 + a]);
-      slab[e] = P.rowptr[lo] / slab_blocks;
+      first[e] = P.rowptr[lo];
+    }
+    const int64_t lo_b = std::max<int64_t>(1, std::min(plan.min_blocks, plan.max_blocks));
+    const int64_t hi_b = std::max<int64_t>(lo_b, plan.max_blocks);
+    const int64_t res = std::max<int64_t>(1, plan.resident_ctas), epc = std::max<int64_t>(1, plan.el_per_cta);
+    int64_t best_sb = hi_b, best_w = -1;
+    const int n_cand = hi_b > lo_b ? 32 : 1;
+    std::vector<int64_t> cnt;
+    for (int k = n_cand - 1; k >= 0; --k) {   // largest first: a tie keeps the larger size
+      const int64_t sb = n_cand == 1 ? hi_b : lo_b + (hi_b - lo_b) * k / 31;
+      const int64_t ns = P.n_blocks / sb + 1;
+      cnt.assign(ns * ncol, 0);
+      for (int64_t e = 0; e < n_el; ++e) cnt[first[e] / sb * ncol + color[e]]++;
+      int64_t w = 0;
+      for (int64_t c : cnt) w += ((c + epc - 1) / epc + res - 1) / res;
+      if (best_w < 0 || w < best_w) {
+        best_w = w;
+        best_sb = sb;
+      }
+    }
+    P.slab_blocks = best_sb;
+    for (int64_t e = 0; e < n_el; ++e) {
+      slab[e] = first[e] / best_sb;
       P.n_slabs = std::max(P.n_slabs, slab[e] + 1);
     }
   }

@@ -18,13 +18,25 @@ struct Pattern {
   std::vector<int64_t> launch_off; // [n_launches + 1]: the conflict-free ranges of elems
   int64_t n_blocks = 0;
   int64_t n_slabs = 1;
+  int64_t slab_blocks = 0;         // the slab size chosen (0: one slab)
   int n_colors = 0;
 };
 
-// slab_blocks > 0: elements are grouped by the slab of slab_blocks consecutive K blocks (in
-// row order) that holds the first row they write, and by colour within a slab; one launch
-// per non-empty (slab, colour).  0: one slab, one launch per colour.
-bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, int64_t slab_blocks, Pattern& P,
+// Launch order.  Elements are grouped by the slab of slab_blocks consecutive K blocks (in row
+// order) that holds the first row they write, then by colour within a slab; one launch per
+// non-empty (slab, colour).  max_blocks == 0: one slab (one launch per colour).  min_blocks ==
+// max_blocks: that slab size.  Otherwise the size is chosen among the 32 sizes
+// min + (max - min) k / 31, k = 0..31, as the one whose launches take the fewest waves of
+// resident_ctas CTAs of el_per_cta elements (sum over launches of ceil(CTAs / resident_ctas)),
+// the larger size on a tie: a launch's partial last wave is time the next launch's assembly
+// waits for.
+struct SlabPlan {
+  int64_t min_blocks = 0, max_blocks = 0;
+  int64_t resident_ctas = 1;
+  int64_t el_per_cta = 16;
+};
+
+bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, const SlabPlan& plan, Pattern& P,
                    std::string& err);
 
 }  // namespace hfe

@@ -73,6 +73,43 @@ template <> struct V4<double> {
 
 using namespace gpm;
 
+// Streamed per-point data (the history and the slot map, each read or written once per
+// sweep) carries an L2 evict-first policy, so that it displaces the K rows the assembly adds
+// into last (createpolicy + .L2::cache_hint).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+template <typename T> struct Stream;
+template <> struct Stream<float> {
+  __device__ static float ld(const float* p, uint64_t pol) {
+    float v;
+    asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+  }
+  __device__ static void st(float* p, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+  }
+};
+template <> struct Stream<double> {
+  __device__ static double ld(const double* p, uint64_t pol) {
+    double v;
+    asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+  }
+  __device__ static void st(double* p, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+  }
+};
+template <> struct Stream<int32_t> {
+  __device__ static int32_t ld(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+  }
+};
+
 // Mixed path: sigma_y(alpha_n + da) = sigma_y(alpha_n) + inc(da) with the FP64 cache
 // sigma_y(alpha_n) and the increment in FP32 (relative error ~1e-7 of the increment only).
 // Swift: inc = sy_n (exp(n log1p(da / (eps0 + alpha_n))) - 1); Voce: inc = A (1 - exp(-b da))
@@ -193,7 +230,7 @@ constexpr int kStageEl = 584;   // staging words per element: 576 used; 584 = 8 
 
 template <typename R>
 __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le, int g, int e, unsigned lane,
-                                              bool valid, int node, unsigned cta, int64_t ccount) {
+                                              bool valid, int node, unsigned cta, int64_t ccount, uint64_t pol) {
   constexpr int kGpStride = Lay<false>::kGpStride;
   constexpr int kElStride = Lay<false>::kElStride;
   static_assert(4 * kStageEl <= 4 * kElStride, "staging must fit in the warp's records");
@@ -277,7 +314,7 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
     // before the first write so that their latencies overlap
     int32_t sv[18];
 #pragma unroll
-    for (int i = 0; i < 18; ++i) sv[i] = slj[((int)lane + 32 * i) / 9];
+    for (int i = 0; i < 18; ++i) sv[i] = Stream<int32_t>::ld(slj + ((int)lane + 32 * i) / 9, pol);
 #pragma unroll
     for (int i = 0; i < 18; ++i) {
       const int r = (int)lane + 32 * i;
@@ -290,7 +327,7 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
   }
   if (!valid) return;
   // node of row a = g is the node this thread gathered in phase 1
-  const bool store = a.slot[(int64_t)e * 64 + arow * 9] < 0;   // diagonal block (a, a)
+  const bool store = Stream<int32_t>::ld(a.slot + (int64_t)e * 64 + arow * 9, pol) < 0;   // diagonal block (a, a)
   double* Rg = a.R + 3 * (int64_t)node;
   if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
     atomicAdd(&a.status->nonfinite, 1);
@@ -329,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   const int e = valid ? a.elems[cbeg + li] : 0;
   const unsigned lane = tid & 31;
   const unsigned gmask = 0xffu << (lane & 24);
+  const uint64_t pol = l2_evict_first();
 
   using MR = typename MatOf<R>::T;
   const MR* matR = reinterpret_cast<const MR*>(a.mat);
@@ -346,9 +384,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   if (valid) {
     void* hb = const_cast<void*>(a.hist);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) epn[c] = Hist<R>::comp(hb, c, ng)[gpi];
-    alpn_r = Hist<R>::comp(hb, 6, ng)[gpi];
-    if (sizeof(R) == 4) syn_cache = Hist<R>::cache(hb, ng)[gpi];
+    for (int c = 0; c < 6; ++c) epn[c] = Stream<R>::ld(Hist<R>::comp(hb, c, ng) + gpi, pol);
+    alpn_r = Stream<R>::ld(Hist<R>::comp(hb, 6, ng) + gpi, pol);
+    if (sizeof(R) == 4) syn_cache = Stream<double>::ld(Hist<R>::cache(hb, ng) + gpi, pol);
   } else {
 #pragma unroll
     for (int c = 0; c < 6; ++c) epn[c] = R(0);
@@ -680,15 +718,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
           R s = R(0);
 #pragma unroll
           for (int j = 1; j < 6; ++j) s += m.QH[p * 6 + j] * neig[j];
-          Hist<R>::comp(hb, p, ng)[gpi] = epn[p] + dgR * s * (p < 3 ? R(1) : R(kISq2));
+          Stream<R>::st(Hist<R>::comp(hb, p, ng) + gpi, epn[p] + dgR * s * (p < 3 ? R(1) : R(kISq2)), pol);
         }
-        Hist<R>::comp(hb, 6, ng)[gpi] = (R)(alpn + kSq23 * rm.dgamma);
+        Stream<R>::st(Hist<R>::comp(hb, 6, ng) + gpi, (R)(alpn + kSq23 * rm.dgamma), pol);
       } else {
 #pragma unroll
-        for (int p = 0; p < 6; ++p) Hist<R>::comp(hb, p, ng)[gpi] = epn[p];
-        Hist<R>::comp(hb, 6, ng)[gpi] = alpn_r;
+        for (int p = 0; p < 6; ++p) Stream<R>::st(Hist<R>::comp(hb, p, ng) + gpi, epn[p], pol);
+        Stream<R>::st(Hist<R>::comp(hb, 6, ng) + gpi, alpn_r, pol);
       }
-      Hist<R>::cache(hb, ng)[gpi] = rm.syn1;
+      // the FP64 path keeps sigma_y(alpha_n+1) with the history; the mixed path's cache is
+      // recomputed from alpha when a step is committed, so the trial cache is not written
+      if constexpr (sizeof(R) == 8) Stream<double>::st(Hist<R>::cache(hb, ng) + gpi, rm.syn1, pol);
     }
     }   // MAT == 0
 
@@ -965,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     // staged row-major in shared memory and written out with consecutive lanes on consecutive
     // entries (a block's 9 values are contiguous in K), so that a warp store touches a few
     // 32-byte sectors instead of 32 scattered ones
-    phase2_staged<R>(a, sGp, le, g, e, lane, valid, node, blockIdx.x, ccount);
+    phase2_staged<R>(a, sGp, le, g, e, lane, valid, node, blockIdx.x, ccount, pol);
     return;
   }
   if (!valid) return;
@@ -1094,7 +1134,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
   }
   {
     // node of row a = g is the node this thread gathered in phase 1
-    const bool store = a.slot[(int64_t)e * 64 + arow * 9] < 0;   // diagonal block (a, a)
+    const bool store = Stream<int32_t>::ld(a.slot + (int64_t)e * 64 + arow * 9, pol) < 0;   // diagonal block (a, a)
     double* Rg = a.R + 3 * (int64_t)node;
     if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
       atomicAdd(&a.status->nonfinite, 1);
@@ -1337,6 +1377,26 @@ static void launch_typed(const SweepArgs& a, const std::vector<int64_t>& off, cu
     cudaLaunchKernelEx(&cfg, gp_sweep_kernel<R, TANGENT, UNIF, FBAR, MAT>, a, rec, off[c], cnt);
   }
 }
+
+template <typename R, bool FBAR>
+static int64_t resident_ctas() {
+  const size_t smem = sizeof(R) * (size_t)kElemsPerCta * Lay<FBAR>::kElStride;
+  auto* k = gp_sweep_kernel<R, true, true, FBAR, 0>;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem) != cudaSuccess)
+    return -1;
+  return (int64_t)per_sm * sms;
+}
+
+int64_t sweep_resident_ctas(bool fp64, bool fbar) {
+  if (fp64) return fbar ? resident_ctas<double, true>() : resident_ctas<double, false>();
+  return fbar ? resident_ctas<float, true>() : resident_ctas<float, false>();
+}
+
+int64_t sweep_elems_per_cta() { return kElemsPerCta; }
 
 template <typename R, bool FBAR>
 static void launch_mode(const SweepArgs& a, int mode, const std::vector<int64_t>& off, cudaStream_t s) {

@@ -27,9 +27,9 @@ def _oracle(mesh, u, hist, theta, hardening, Theta):
     return solver.assemble_R(prob, es["Re"]), solver.assemble_K(prob, es["Ke"]), es
 
 
-def _gpu(mesh, u, hist, theta, hardening, Theta, precision):
+def _gpu(mesh, u, hist, theta, hardening, Theta, precision, **opts):
     with hfe.Solver(mesh.X, mesh.conn, np.zeros(0, np.int64), np.zeros(0), theta, hardening, Theta,
-                    precision=precision) as s:
+                    precision=precision, **opts) as s:
         s.set_state(np.zeros(mesh.n_dof), hist_oracle_to_soa(hist))
         Ht = np.empty((7, mesh.n_gp if hasattr(mesh, "n_gp") else 8 * mesh.n_el))
         R, _, st = s.sweep(u, 1.0, tangent=True, hist_out=Ht)
@@ -86,6 +86,32 @@ def test_sweep_repeated_principal_stretches():
     u = np.stack([0.02 * X[:, 0], -0.006 * X[:, 1], -0.006 * X[:, 2]], 1).ravel()
     hist = np.zeros((mesh.n_el, 8, 7))
     _compare(mesh, u, hist, inputs.config0_material().theta_vector(), "swift", min_plastic=1.0, max_plastic=1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sweep_slab_launch_order(precision):
+    """Launches ordered by slabs of K rows (options.assembly_l2_bytes small enough for many
+    slabs on this mesh, each colour of a slab a launch of a few elements): K, R and the trial
+    history match the oracle as in colour order, and match the colour-order sweep up to the
+    order of the additions (the history bit for bit)."""
+    mesh = inputs.distorted_box_mesh(6, seed=12, amp=0.2)
+    mat = inputs.config1_material()
+    u, hist = mixed_state(mesh, 31)
+    Ro, Ko, es = _oracle(mesh, u, hist, mat.theta_vector(), "voce", None)
+    with hfe.Solver(mesh.X, mesh.conn, np.zeros(0, np.int64), np.zeros(0), mat.theta_vector(), "voce",
+                    precision=precision, assembly_l2_bytes=6000) as s:
+        info = s.info()
+    assert info["n_slabs"] > 10 and info["n_launches"] > info["n_slabs"]
+    runs = {b: _gpu(mesh, u, hist, mat.theta_vector(), "voce", None, precision, assembly_l2_bytes=b) for b in (0, 6000)}
+    tol = TOL[precision]
+    R, K, Ht, st = runs[6000]
+    assert st["local_fail"] == 0 and 0.05 < es["gp"]["plastic"].mean() < 0.95
+    assert rel_inf(R, Ro) < tol["R"]
+    assert np.abs((K - Ko).tocsr().data).max() / np.abs(Ko.data).max() < tol["K"]
+    R0, K0, Ht0, _ = runs[0]
+    assert np.array_equal(Ht, Ht0)
+    assert rel_inf(R, R0) < (1e-13 if precision == "fp64" else 1e-12)
+    assert np.abs((K - K0).tocsr().data).max() / np.abs(K0.data).max() < (1e-13 if precision == "fp64" else 2e-6)
 
 
 def test_sweep_zero_state_is_linear_elastic():

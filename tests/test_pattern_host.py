@@ -28,21 +28,23 @@ template <typename T> static void put(FILE* f, const std::vector<T>& v) {
 }
 int main(int argc, char** argv) {
   FILE* in = fopen(argv[1], "rb");
-  long long nn, ne, sb;
-  if (fread(&nn, 8, 1, in) != 1 || fread(&ne, 8, 1, in) != 1 || fread(&sb, 8, 1, in) != 1) return 3;
+  long long nn, ne, plan[4];
+  if (fread(&nn, 8, 1, in) != 1 || fread(&ne, 8, 1, in) != 1 || fread(plan, 8, 4, in) != 4) return 3;
   std::vector<int32_t> conn(ne * 8);
   if (fread(conn.data(), 4, conn.size(), in) != conn.size()) return 3;
   fclose(in);
   hfe::Pattern P;
   std::string err;
-  if (!hfe::build_pattern(nn, ne, conn.data(), sb, P, err)) {
+  hfe::SlabPlan sp;
+  sp.min_blocks = plan[0]; sp.max_blocks = plan[1]; sp.resident_ctas = plan[2]; sp.el_per_cta = plan[3];
+  if (!hfe::build_pattern(nn, ne, conn.data(), sp, P, err)) {
     fprintf(stderr, "%s\n", err.c_str());
     return 2;
   }
   FILE* out = fopen(argv[2], "wb");
   put(out, P.rowptr); put(out, P.cols); put(out, P.diag_slot); put(out, P.slot);
   put(out, P.elems); put(out, P.launch_off);
-  std::vector<long long> ns(1, (long long)P.n_slabs);
+  std::vector<long long> ns{(long long)P.n_slabs, (long long)P.slab_blocks};
   put(out, ns);
   fclose(out);
   return 0;
@@ -63,11 +65,14 @@ def driver(tmp_path_factory):
     return exe, d
 
 
-def _run(driver, n_nodes, conn, slab_blocks=0):
+def _run(driver, n_nodes, conn, slab_blocks=0, plan=None):
+    """plan = (min_blocks, max_blocks, resident_ctas, el_per_cta); slab_blocks > 0 fixes the size."""
     exe, d = driver
     inp, out = d / "conn.bin", d / "pattern.bin"
+    if plan is None:
+        plan = (slab_blocks, slab_blocks, 1, 16)
     with open(inp, "wb") as f:
-        np.array([n_nodes, conn.shape[0], slab_blocks], dtype=np.int64).tofile(f)
+        np.array([n_nodes, conn.shape[0], *plan], dtype=np.int64).tofile(f)
         np.ascontiguousarray(conn, dtype=np.int32).tofile(f)
     r = subprocess.run([str(exe), str(inp), str(out)], capture_output=True, text=True)
     if r.returncode != 0:
@@ -168,6 +173,7 @@ def test_slab_launch_order(driver, slab_blocks):
     colour = _colours(conn)
     slab = P["rowptr"][conn.min(axis=1)] // slab_blocks
     assert int(P["n_slabs"][0]) == slab.max() + 1
+    assert int(P["n_slabs"][1]) == (0 if slab_blocks == 0 else slab_blocks)
     elems, off = P["elems"], P["launch_off"]
     key = slab[elems] * 64 + colour[elems]
     assert np.all(np.diff(key) >= 0)                     # slabs in order, colours within a slab
@@ -182,6 +188,34 @@ def test_slab_launch_order(driver, slab_blocks):
     # within a launch the elements keep their id order
     for c in range(n_launch):
         assert np.all(np.diff(elems[off[c]:off[c + 1]]) > 0)
+
+
+def _waves(conn, rowptr, colour, sb, resident, epc):
+    first = rowptr[conn.min(axis=1)]
+    _, cnt = np.unique((first // sb) * 64 + colour, return_counts=True)
+    return int(np.sum(-(-(-(-cnt // epc)) // resident)))
+
+
+def test_slab_size_planner(driver):
+    """With a size range, the planner takes, among the 32 sizes min + (max - min) k / 31, one
+    with the fewest waves of resident CTAs (sum over launches of ceil(CTAs / resident)), the
+    largest such size; the launch order is then the fixed-size order of that size."""
+    mesh = inputs.box_mesh(9, 8, 7)
+    conn = np.asarray(mesh.conn, dtype=np.int64)
+    colour = _colours(conn)
+    lo, hi, res, epc = 300, 1200, 3, 4
+    P, err = _run(driver, mesh.n_nodes, mesh.conn, plan=(lo, hi, res, epc))
+    assert P is not None, err
+    sizes = [lo + (hi - lo) * k // 31 for k in range(32)]
+    waves = {sb: _waves(conn, P["rowptr"], colour, sb, res, epc) for sb in sizes}
+    best = min(waves.values())
+    chosen = int(P["n_slabs"][1])
+    assert chosen == max(sb for sb in sizes if waves[sb] == best)
+    assert len(set(waves.values())) > 1                     # the choice is not a trivial one
+    F, _ = _run(driver, mesh.n_nodes, mesh.conn, chosen)
+    for key in ("elems", "launch_off", "slot"):
+        assert np.array_equal(P[key], F[key]), key
+    _check(P, mesh.n_nodes, conn)
 
 
 def test_malformed_meshes_refused(driver):
