@@ -718,8 +718,11 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_persistent_kernel(const Pers
 
 // ---------------------------------------------------------------------------------------
 // One-launch CG with the streamed SpMV.  The iteration is that of pcg_persistent_kernel (same
-// fixed-order reductions, the same two barriers, p formed on the fly from z and p_prev); what
-// changes is how K reaches the SMs.  Each CTA owns a contiguous range of row chunks; a chunk's
+// fixed-order reductions, the same two barriers) except for how q = K p is formed: the SpMV
+// gathers z alone and q follows the recurrence q = K z + beta q_prev (K p = K z + beta K p_prev,
+// the recurrence of Chronopoulos and Gear's CG), so each column costs one gathered vector
+// instead of two; p = z + beta p_prev is formed on the own rows only.  The other change is how
+// K reaches the SMs.  Each CTA owns a contiguous range of row chunks; a chunk's
 // values and column indices are one contiguous range each in block-CSR order, and one thread
 // brings them into shared memory with bulk asynchronous copies (cp.async.bulk, completion on
 // an mbarrier), two stages deep, so that the HBM stream of K runs ahead of the arithmetic and
@@ -918,7 +921,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_stream_kernel(const PersistA
       const int64_t b = has ? a.rowptr[r] : 0, e = has ? a.rowptr[r + 1] : 0;
       R a0 = R(0), a1 = R(0), a2 = R(0);
       for (int64_t j0 = b; j0 < e; j0 += 32) {
-        // all column reads, then all gathers of p = z + beta p_prev, then the arithmetic
+        // all column reads, then all gathers of z, then the arithmetic
         int64_t col[kU];
         bool okj[kU];
 #pragma unroll
@@ -932,7 +935,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_stream_kernel(const PersistA
         for (int u = 0; u < kU; ++u)
 #pragma unroll
           for (int i = 0; i < 3; ++i)
-            x[u][i] = okj[u] ? a.z[3 * col[u] + i] + bt * pprev[3 * col[u] + i] : R(0);
+            x[u][i] = okj[u] ? a.z[3 * col[u] + i] : R(0);
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
           if (okj[u]) {
@@ -953,7 +956,7 @@ __global__ void __launch_bounds__(kBlock, MINB) pcg_stream_kernel(const PersistA
         const int64_t d = 3 * r + gl;
         const R o = gl == 0 ? a0 : (gl == 1 ? a1 : a2);
         const R pd = a.z[d] + bt * pprev[d];
-        const R qd = a.freem[d] ? o : R(0);
+        const R qd = (a.freem[d] ? o : R(0)) + (it > 0 ? bt * a.q[d] : R(0));
         pcur[d] = pd;
         a.q[d] = qd;
         dot += (double)pd * (double)qd;

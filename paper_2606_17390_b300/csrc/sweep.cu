@@ -174,23 +174,35 @@ __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv,
     if (fabsf(dgn - dg) <= 1e-7f * dg) { dg = dgn; ok = true; break; }
     dg = dgn;
   }
-  // FP64 polish: one Newton step on rt(dgamma) = phi^2 - phi_y^2 (derivative 2 phi_y r').
-  double dg64 = (double)dg;
+  // FP64 polish: one Newton step on rho(dgamma) = sum_i h_i (t_i / D_i)^2 - 1, the yield
+  // residual phi^2 - phi_y^2 divided by phi_y^2, with D_i = phi_y + 2 mu dgamma h_i (so that
+  // t_i / D_i = T_i / phi_y).  Each quotient is formed in FP32, q_i ~ t_i / D_i, and its FP64
+  // residual t_i - D_i q_i = D_i d_i gives the exact square (t_i / D_i)^2 = q_i^2 +
+  // d_i (2 q_i + d_i): q_i^2 is exact in FP64 and carries the sum, the correction (~1e-7 of
+  // it) needs FP32 only.  Four FP64 operations per component (the FP64 pipe of this part is
+  // 1/64 of its FP32 rate); the derivative 2 phi_y r' comes from the FP32 iteration.
   float incv, dsy;
   inc.eval(sq23 * dg, incv, dsy);
-  double sy64 = syn64 + (double)incv;
-  double phy = kSq23 * sy64;
-  double s = 2.0 * (double)mu * dg64 * rcp64(phy);
-  double phi2 = 0.0;
+  const double phy = kSq23 * (syn64 + (double)incv);
+  const float tmu = 2.0f * mu;                       // exact
+  const double k2 = (double)tmu * (double)dg;        // 2 mu dgamma, exact in FP64
+  const float phyf = (float)phy, k2f = tmu * dg;
+  double rho = -1.0;
+  float cor = 0.0f;
 #pragma unroll
   for (int i = 1; i < 6; ++i) {
-    double c = rcp64(fma(s, hv.v[i], 1.0));
-    double Ti = (double)t[i] * c;
-    phi2 = fma(hv.v[i] * Ti, Ti, phi2);
+    const float rD = __frcp_rn(fmaf(k2f, hfv.v[i], phyf));
+    const float qf = t[i] * rD;
+    const double qd = (double)qf;
+    const double Di = fma(k2, hv.v[i], phy);
+    const float del = (float)fma(-Di, qd, (double)t[i]) * rD;
+    rho = fma(hv.v[i], qd * qd, rho);
+    cor = fmaf(hfv.v[i] * del, fmaf(2.0f, qf, del), cor);
   }
-  double rt = phi2 - phy * phy;
-  float corr = __fdividef((float)rt, 2.0f * (float)phy * dr);
-  dg64 -= (double)corr;
+  rho += (double)cor;
+  // Newton: d(phi^2 - phi_y^2) / d dgamma = 2 phi_y r', so the step is phi_y rho / (2 r')
+  const float corr = __fdividef((float)rho * phyf, 2.0f * dr);
+  double dg64 = (double)dg - (double)corr;
   if (dg64 < 0.0) dg64 = 0.0;
   inc.eval(sq23 * (float)dg64, incv, dsy);
   out.dgamma = dg64;
