@@ -225,3 +225,29 @@ def test_voce_homogeneous_closed_form(precision):
         assert np.abs(u[k] - uex).max() < tol * np.abs(uex).max(), (k, precision)
     a = _uniaxial_closed_form(ts[-1], mesh, "voce")[1]
     assert np.abs(hist[6] - a).max() < (1e-12 if precision == "fp64" else 1e-6) * max(a, 1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plate_50x25x2_all_steps_vs_stored_oracle(precision):
+    """The perforated plate at 50 x 25 x 2 over all 20 Voce load steps against the oracle's
+    forward solve stored by tests/golden/make_plate_forward_50x25x2.py (per step: u at 600
+    seeded dofs and max |u|; after the last step von Mises at 1,000 seeded Gauss points and
+    the maximum).  FP64 1e-10 in displacement, mixed 1e-5 in displacement and 1e-4 in von
+    Mises stress, relative to the step's maximum."""
+    import os
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "plate_forward_50x25x2.npz"))
+    mesh, bc, mat, ts = inputs.config1_problem(nx=50, ny=25, nz=2, n_steps=20)
+    assert mesh.n_el == int(g["n_el"]) and mesh.n_dof == int(g["n_dof"])
+    assert np.array_equal(np.asarray(ts), g["ts"])
+    opts = dict(newton_rtol=1e-12, pcg_rtol=1e-13) if precision == "fp64" else {}
+    with hfe.from_inputs(mesh, bc, mat, precision=precision, **opts) as s:
+        sig = np.empty((mesh.n_el * 8, 6))
+        u, st = s.forward(ts, sigma_out=sig)
+    assert st["steps_done"] == 20
+    err_u = max(np.abs(u[n][g["dofs"]] - g["u_sample"][n]).max() / g["u_max"][n] for n in range(20))
+    err_umax = np.abs(np.abs(u).max(axis=1) - g["u_max"]).max() / g["u_max"].max()
+    vm = material.von_mises(_sym(sig))
+    err_vm = max(np.abs(vm[g["gps"]] - g["vm_sample"]).max(), abs(vm.max() - float(g["vm_max"]))) / float(g["vm_max"])
+    tol_u = 1e-10 if precision == "fp64" else 1e-5
+    assert err_u < tol_u and err_umax < tol_u, (err_u, err_umax)
+    assert err_vm < (1e-9 if precision == "fp64" else 1e-4), err_vm
