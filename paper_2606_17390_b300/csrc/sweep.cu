@@ -203,10 +203,16 @@ __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv,
   // Newton: d(phi^2 - phi_y^2) / d dgamma = 2 phi_y r', so the step is phi_y rho / (2 r')
   const float corr = __fdividef((float)rho * phyf, 2.0f * dr);
   double dg64 = (double)dg - (double)corr;
-  if (dg64 < 0.0) dg64 = 0.0;
-  inc.eval(sq23 * (float)dg64, incv, dsy);
+  float dgf = dg - corr;
+  if (corr > dg) {   // dgamma < 0: none
+    dg64 = 0.0;
+    dgf = 0.0f;
+  }
+  inc.eval(sq23 * dgf, incv, dsy);
   out.dgamma = dg64;
-  out.syn1 = syn64 + (double)incv;
+  out.dgf = dgf;
+  out.phyf = sq23 * (inc.syn + incv);   // the FP32 stress recovery's phi_y
+  out.syn1 = 0.0;
   out.dsy = dsy;
   out.iters = k + 1;
   out.ok = ok;
@@ -341,7 +347,7 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
   // node of row a = g is the node this thread gathered in phase 1
   const bool store = Stream<int32_t>::ld(a.slot + (int64_t)e * 64 + arow * 9, pol) < 0;   // diagonal block (a, a)
   double* Rg = a.R + 3 * (int64_t)node;
-  if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
+  if (!(isfinite(Ra[0]) && isfinite(Ra[1]) && isfinite(Ra[2])))
     atomicAdd(&a.status->nonfinite, 1);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -357,8 +363,11 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
 // MAT: 0 the Hill-48 update in the kernel; 1 the strain pass of an external material model
 // (the Mandel log strain of every Gauss point out, nothing assembled); 2 the external model's
 // stress, plastic flag and tangent dT/deps in (S4 and S5 replaced, S6-S8 as for Hill).
+// Occupancy: the mixed uniform-material tangent sweep runs five CTAs per SM (96 registers, a
+// few spilled values; measured 3.42 -> 3.33 ms at 100^3 against four CTAs at 128 registers),
+// the other mixed forms four, F-bar three.
 template <typename R, bool TANGENT, bool UNIF, bool FBAR, int MAT = 0>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGENT && UNIF ? 5 : 4)) : 1)
     gp_sweep_kernel(SweepArgs a, const typename MatOf<R>::T mrec, int64_t cbeg, int64_t ccount) {
   constexpr int kGpStride = Lay<FBAR>::kGpStride;
   constexpr int kElStride = Lay<FBAR>::kElStride;
@@ -603,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     const R lam = m.lam, mu = m.mu;
     bool plastic = false;
     RM rm;
-    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0;
+    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0; rm.dgf = 0.0f; rm.phyf = 1.0f;
     R Teig[6];
     R s_pl = R(0), phy = R(1);
     R TM[6];
@@ -663,7 +672,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       float phi2 = 0.0f;
 #pragma unroll
       for (int i = 1; i < 6; ++i) phi2 += mf.h[i] * (float)t[i] * (float)t[i];
-      float phyn2 = (float)((2.0 / 3.0) * syn64 * syn64);
+      const float synf = (float)syn64;
+      // the band below (1e-5) is far wider than the FP32 rounding of phi_y^2
+      const float phyn2 = (2.0f / 3.0f) * synf * synf;
       bool pl;
       if (phi2 > phyn2 * 1.00001f) pl = true;
       else if (phi2 < phyn2 * 0.99999f) pl = false;
@@ -675,9 +686,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       }
       HardInc inc;
       inc.type = a.hardening;
-      inc.p2 = (float)mf.hard64[2];
-      inc.syn = (float)syn64;
-      if (a.hardening == HFE_HARDENING_SWIFT) inc.z_or_A = (float)(mf.hard64[1] + alpn);
+      inc.p2 = mf.hard[2];
+      inc.syn = synf;
+      // Swift: eps0 + alpha_n (FP32 sum of FP32 values); Voce: Q exp(-b alpha_n) by a
+      // difference that cancels, in FP64
+      if (a.hardening == HFE_HARDENING_SWIFT) inc.z_or_A = mf.hard[1] + alpn_r;
       else inc.z_or_A = (float)(mf.hard64[0] + mf.hard64[1] - syn64);
       if (pl) {
         plastic = true;
@@ -703,9 +716,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     local_iters = rm.iters;
 
     // stress T and plastic update in the Hill eigenbasis, then back to Mandel components
+    // (the mixed path takes dgamma and phi_y rounded to FP32 from its return mapping)
+    const R dgR = sizeof(R) == 4 ? (R)rm.dgf : (R)rm.dgamma;
     if (plastic) {
-      phy = (R)(kSq23 * rm.syn1);
-      s_pl = Num<R>::div(R(2) * mu * (R)rm.dgamma, phy);
+      phy = sizeof(R) == 4 ? (R)rm.phyf : (R)(kSq23 * rm.syn1);
+      s_pl = Num<R>::div(R(2) * mu * dgR, phy);
     }
     Teig[0] = t[0];
 #pragma unroll
@@ -724,7 +739,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
         neig[0] = R(0);
 #pragma unroll
         for (int i = 1; i < 6; ++i) neig[i] = Num<R>::div((R)m.h[i] * Teig[i], phy);
-        const R dgR = (R)rm.dgamma;
 #pragma unroll
         for (int p = 0; p < 6; ++p) {
           R s = R(0);
@@ -857,9 +871,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
       } else {
         // implicit function theorem on Eq. local_cpp (App. D) in the Hill eigenbasis:
         // Xi^-1 = E^-1 + dgamma (H - N (x) N) / phi, D = Xi - (Xi N)(Xi N)^T / (N Xi N + 2/3 H')
-        const R dgR = (R)rm.dgamma;
         const R iphy = Num<R>::div(R(1), phy);
-        const R cph = dgR * iphy;
+        const R cph = (sizeof(R) == 4 ? (R)rm.dgf : (R)rm.dgamma) * iphy;
         R nv[6], iDd[6], pv[6];
         R npn = R(0);
 #pragma unroll
@@ -1148,7 +1161,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : 4) : 1)
     // node of row a = g is the node this thread gathered in phase 1
     const bool store = Stream<int32_t>::ld(a.slot + (int64_t)e * 64 + arow * 9, pol) < 0;   // diagonal block (a, a)
     double* Rg = a.R + 3 * (int64_t)node;
-    if (!(isfinite((double)Ra[0]) && isfinite((double)Ra[1]) && isfinite((double)Ra[2])))
+    if (!(isfinite(Ra[0]) && isfinite(Ra[1]) && isfinite(Ra[2])))
       atomicAdd(&a.status->nonfinite, 1);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
