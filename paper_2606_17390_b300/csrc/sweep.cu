@@ -130,14 +130,6 @@ struct HardInc {
   }
 };
 
-// FP64 reciprocal from the correctly rounded FP32 reciprocal and one Newton-Raphson step
-// for 1/d (x <- x (2 - d x)), relative error ~ (2^-24)^2.
-__device__ __forceinline__ double rcp64(double d) {
-  double r0 = (double)__frcp_rn((float)d);
-  double e = fma(-d, r0, 1.0);
-  return fma(r0, e, r0);
-}
-
 // Mixed form: the Newton iterations in FP32 to ~1e-6, then one FP64 Newton step on the yield
 // residual (written as phi^2 - phi_y^2 to avoid a square root) with FP64 reciprocals.
 __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv, const Vec6f hfv, float mu,
@@ -233,8 +225,7 @@ template <> struct MatOf<float> { using T = MatRecF; };
 template <> struct MatOf<double> { using T = MatRec; };
 
 // ----------------------------------------------------------------------------------------
-// Phase 2 of the symmetric tangent sweep (standard element): thread (element le, node row a =
-// g) contracts the eight Gauss-point records into the blocks (a, a + d mod 8), d = 0..3 (and
+// Phase 2 of the tangent sweep: thread (element le, node row a = g) contracts the eight Gauss-point records into the blocks (a, a + d mod 8), d = 0..3 (and
 // d = 4 for a < 4) — each unordered block pair once, as K^e is symmetric (A is stored with
 // its major symmetry) — and into R_a.  The blocks and their transposes are then staged in the
 // warp's own (already consumed) record area, row-major [a][b][3x3] per element, and the warp
@@ -242,16 +233,22 @@ template <> struct MatOf<double> { using T = MatRec; };
 // values are contiguous in K and an element row's blocks lie close together, so each warp
 // store covers a few 32-byte sectors.  The first launch that touches a block stores (bit 31 of
 // the slot), later launches add: one writer per block per launch, launches in a fixed order,
-// so the sums are deterministic.
+// so the sums are deterministic.  The F-bar element (FBAR) adds its non-symmetric rank-one part
+// K_ab += sum_q (M_q g_a,q) (x) v_b,q to the staged row a before the write-out; its staging
+// stays inside the element's own record area (words 0..71 of each Gauss-point record, entry r
+// at record r / 72), clear of the M and v_b sections the rank-one part reads afterwards.
 constexpr int kStageEl = 584;   // staging words per element: 576 used; 584 = 8 mod 32 spreads
                                 // the four elements of a warp over the banks
 
-template <typename R>
+template <typename R, bool FBAR>
 __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le, int g, int e, unsigned lane,
                                               bool valid, int node, unsigned cta, int64_t ccount, uint64_t pol) {
-  constexpr int kGpStride = Lay<false>::kGpStride;
-  constexpr int kElStride = Lay<false>::kElStride;
+  constexpr int kGpStride = Lay<FBAR>::kGpStride;
+  constexpr int kElStride = Lay<FBAR>::kElStride;
   static_assert(4 * kStageEl <= 4 * kElStride, "staging must fit in the warp's records");
+  static_assert(!FBAR || 72 <= kOffM, "F-bar staging must leave M and v_b in place");
+  // staging word of entry r ([a][b][3x3] row-major) relative to the element's staging base
+  auto sw = [](int r) { return FBAR ? (r / 72) * kGpStride + (r - 72 * (r / 72)) : r; };
   const int arow = g;
   // the element's slot-map row is read during the write-out: start bringing it into L1
   if (valid && g < 2) asm volatile("prefetch.global.L1 [%0];\n" ::"l"(a.slot + (int64_t)e * 64 + 32 * g));
@@ -300,11 +297,31 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
       for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
     }
   }
-  // every lane of the warp has read its records: the warp's four record areas become staging
+  // F-bar: M_q g_a,q for the eight points, read before the staging overwrites g
+  R ua[FBAR ? 8 : 1][3];
+  if constexpr (FBAR) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ua[q][0] = ua[q][1] = ua[q][2] = R(0);
+    if (valid) {
+      const R* G = sGp + (size_t)le * kElStride;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const R* Aq = G + q * kGpStride;
+        const R ga0 = Aq[kOffG + arow * 3], ga1 = Aq[kOffG + arow * 3 + 1], ga2 = Aq[kOffG + arow * 3 + 2];
+        R mv[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffM + 4 * k, mv + 4 * k);
+        ua[q][0] = mv[0] * ga0 + mv[1] * ga1 + mv[2] * ga2;
+        ua[q][1] = mv[3] * ga0 + mv[4] * ga1 + mv[5] * ga2;
+        ua[q][2] = mv[6] * ga0 + mv[7] * ga1 + mv[8] * ga2;
+      }
+    }
+  }
+  // every lane of the warp has read its records: the record areas become staging
   __syncwarp();
   R* stage = sGp + (size_t)(le & ~3) * kElStride;
+  R* se = FBAR ? sGp + (size_t)le * kElStride : stage + (le & 3) * kStageEl;
   if (valid) {
-    R* se = stage + (le & 3) * kStageEl;
 #pragma unroll
     for (int d = 0; d < kNb; ++d) {
       if (d < nb) {
@@ -313,20 +330,46 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
         for (int i = 0; i < 3; ++i)
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            se[(arow * 8 + b) * 9 + i * 3 + k] = Kr[d][i * 3 + k];
-            if (d != 0) se[(b * 8 + arow) * 9 + k * 3 + i] = Kr[d][i * 3 + k];
+            se[sw((arow * 8 + b) * 9 + i * 3 + k)] = Kr[d][i * 3 + k];
+            if (d != 0) se[sw((b * 8 + arow) * 9 + k * 3 + i)] = Kr[d][i * 3 + k];
           }
       }
     }
   }
   __syncwarp();
+  if constexpr (FBAR) {
+    // the rank-one part of row a (only this thread writes row a now)
+    if (valid) {
+      const R* G = sGp + (size_t)le * kElStride;
+#pragma unroll 1
+      for (int b = 0; b < 8; ++b) {
+        R C[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) C[c] = R(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const R* vb = G + q * kGpStride + kOffV + b * 3;
+          const R v0 = vb[0], v1 = vb[1], v2 = vb[2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            C[i * 3] += ua[q][i] * v0;
+            C[i * 3 + 1] += ua[q][i] * v1;
+            C[i * 3 + 2] += ua[q][i] * v2;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) se[sw((arow * 8 + b) * 9 + c)] += C[c];
+      }
+    }
+    __syncwarp();
+  }
   R* Kv = reinterpret_cast<R*>(a.K);
   const int w0 = le & ~3;
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
     const int ej = __shfl_sync(0xffffffffu, e, 8 * j);             // element of lanes 8j..8j+7
     if ((int64_t)cta * kElemsPerCta + w0 + j >= ccount) break;   // the same for every lane
-    const R* sej = stage + j * kStageEl;
+    const R* sej = FBAR ? sGp + (size_t)(w0 + j) * kElStride : stage + j * kStageEl;
     const int32_t* slj = a.slot + (int64_t)ej * 64;
     // lane l writes entries l + 32 i (i < 18) of the 576: all 18 slot loads are issued
     // before the first write so that their latencies overlap
@@ -338,7 +381,7 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
       const int r = (int)lane + 32 * i;
       const int c = r - 9 * (r / 9);
       R* dst = Kv + (int64_t)(sv[i] & 0x7fffffff) * 9 + c;
-      const R v = sej[r];
+      const R v = sej[sw(r)];
       if (sv[i] < 0) *dst = v;
       else atomicAdd(dst, v);
     }
@@ -363,11 +406,11 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
 // MAT: 0 the Hill-48 update in the kernel; 1 the strain pass of an external material model
 // (the Mandel log strain of every Gauss point out, nothing assembled); 2 the external model's
 // stress, plastic flag and tangent dT/deps in (S4 and S5 replaced, S6-S8 as for Hill).
-// Occupancy: the mixed uniform-material tangent sweep runs five CTAs per SM (96 registers, a
+// Occupancy: the mixed uniform-material Hill-48 tangent sweep runs five CTAs per SM (96 registers, a
 // few spilled values; measured 3.42 -> 3.33 ms at 100^3 against four CTAs at 128 registers),
 // the other mixed forms four, F-bar three.
 template <typename R, bool TANGENT, bool UNIF, bool FBAR, int MAT = 0>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGENT && UNIF ? 5 : 4)) : 1)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGENT && UNIF && MAT == 0 ? 5 : 4)) : 1)
     gp_sweep_kernel(SweepArgs a, const typename MatOf<R>::T mrec, int64_t cbeg, int64_t ccount) {
   constexpr int kGpStride = Lay<FBAR>::kGpStride;
   constexpr int kElStride = Lay<FBAR>::kElStride;
@@ -1025,126 +1068,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGEN
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
   // ---- S7/S8 phase 2: thread (element le, node row a = g)
-  if constexpr (TANGENT && !FBAR) {
-    // the symmetric element matrix: contraction as below, then the warp's four elements are
-    // staged row-major in shared memory and written out with consecutive lanes on consecutive
-    // entries (a block's 9 values are contiguous in K), so that a warp store touches a few
-    // 32-byte sectors instead of 32 scattered ones
-    phase2_staged<R>(a, sGp, le, g, e, lane, valid, node, blockIdx.x, ccount, pol);
+  if constexpr (TANGENT) {
+    // the element matrix: contraction, then the warp's four elements are staged row-major in
+    // shared memory and written out with consecutive lanes on consecutive entries (a block's 9
+    // values are contiguous in K), so that a warp store touches a few 32-byte sectors instead
+    // of 32 scattered ones
+    phase2_staged<R, FBAR>(a, sGp, le, g, e, lane, valid, node, blockIdx.x, ccount, pol);
     return;
   }
   if (!valid) return;
   const R* G = sGp + (size_t)le * kElStride;
   R Ra[3] = {R(0), R(0), R(0)};
   const int arow = g;
-  if constexpr (TANGENT) {
-    // K^e is symmetric (A is stored with its major symmetry), so row a computes the blocks
-    // (a, a + d mod 8) for d = 0..3 (d = 4 as well for a < 4): each unordered pair once, 4 or
-    // 5 blocks per thread, and writes every off-diagonal block together with its transpose.
-    constexpr int kNb = 5;
-    const int nb = (arow < 4) ? 5 : 4;
-    R Kr[kNb][9];
-#pragma unroll
-    for (int d = 0; d < kNb; ++d)
-#pragma unroll
-      for (int c = 0; c < 9; ++c) Kr[d][c] = R(0);
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-      const R* Aq = G + q * kGpStride;
-      const R* gt = Aq + kOffG;
-      const R ga0 = gt[arow * 3], ga1 = gt[arow * 3 + 1], ga2 = gt[arow * 3 + 2];
-      R A[48];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) V4<R>::ld(Aq + 4 * k, A + 4 * k);
-      R U[3][3][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int L = 0; L < 3; ++L)
-            U[i][k][L] = ga0 * A[asym(i * 3 + 0, k * 3 + L)] + ga1 * A[asym(i * 3 + 1, k * 3 + L)] +
-                         ga2 * A[asym(i * 3 + 2, k * 3 + L)];
-#pragma unroll
-      for (int d = 0; d < kNb; ++d) {
-        if (d < nb) {
-          const int b = (arow + d) & 7;
-          const R gb0 = gt[b * 3], gb1 = gt[b * 3 + 1], gb2 = gt[b * 3 + 2];
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) Kr[d][i * 3 + k] += U[i][k][0] * gb0 + U[i][k][1] * gb1 + U[i][k][2] * gb2;
-        }
-      }
-      R P[12];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffP + 4 * k, P + 4 * k);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) Ra[i] += P[i * 3] * ga0 + P[i * 3 + 1] * ga1 + P[i * 3 + 2] * ga2;
-    }
-    R* Kv = reinterpret_cast<R*>(a.K);
-    const int32_t* sl = a.slot + (int64_t)e * 64;
-#pragma unroll
-    for (int d = 0; d < kNb; ++d) {
-      if (d < nb) {
-        const int b = (arow + d) & 7;
-#pragma unroll
-        for (int tr = 0; tr < 2; ++tr) {
-          if (tr == 1 && d == 0) continue;
-          const int32_t sv = tr == 0 ? sl[arow * 8 + b] : sl[b * 8 + arow];
-          R* dst = Kv + (int64_t)(sv & 0x7fffffff) * 9;
-          if (sv < 0) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int k = 0; k < 3; ++k) dst[i * 3 + k] = tr == 0 ? Kr[d][i * 3 + k] : Kr[d][k * 3 + i];
-          } else {   // one writer per block per launch, launches in a fixed order: deterministic
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int k = 0; k < 3; ++k) atomicAdd(dst + i * 3 + k, tr == 0 ? Kr[d][i * 3 + k] : Kr[d][k * 3 + i]);
-          }
-        }
-      }
-    }
-    if constexpr (FBAR) {
-      // the non-symmetric part: K_ab += sum_q (M_q g_a,q) (x) v_b,q for all 8 b, added after the
-      // symmetric writes of every block of this element (its 8 threads share the warp)
-      __syncwarp(gmask);
-      R ua[8][3];   // M_q g_a,q for the 8 points
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const R* Aq = G + q * kGpStride;
-        const R ga0 = Aq[kOffG + arow * 3], ga1 = Aq[kOffG + arow * 3 + 1], ga2 = Aq[kOffG + arow * 3 + 2];
-        R mv[12];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) V4<R>::ld(Aq + kOffM + 4 * k, mv + 4 * k);
-        ua[q][0] = mv[0] * ga0 + mv[1] * ga1 + mv[2] * ga2;
-        ua[q][1] = mv[3] * ga0 + mv[4] * ga1 + mv[5] * ga2;
-        ua[q][2] = mv[6] * ga0 + mv[7] * ga1 + mv[8] * ga2;
-      }
-#pragma unroll 1
-      for (int b = 0; b < 8; ++b) {
-        R C[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) C[c] = R(0);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const R* vb = G + q * kGpStride + kOffV + b * 3;
-          const R v0 = vb[0], v1 = vb[1], v2 = vb[2];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            C[i * 3] += ua[q][i] * v0;
-            C[i * 3 + 1] += ua[q][i] * v1;
-            C[i * 3 + 2] += ua[q][i] * v2;
-          }
-        }
-        R* dst = Kv + (int64_t)(sl[arow * 8 + b] & 0x7fffffff) * 9;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) atomicAdd(dst + c, C[c]);
-      }
-    }
-  } else {
+  {
 #pragma unroll 1
     for (int q = 0; q < 8; ++q) {
       const R* Aq = G + q * kGpStride;
