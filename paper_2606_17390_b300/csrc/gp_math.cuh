@@ -181,10 +181,8 @@ __device__ __forceinline__ void sigy64(int type, Hard3 hp, double a, double& sy,
 // Safeguarded Newton: a step that leaves the bracket is replaced by bisection.
 struct RM {
   double dgamma;   // plastic multiplier
-  double syn1;     // sigma_y(alpha_{n+1}) (FP64 form)
+  double syn1;     // sigma_y(alpha_{n+1})
   float dsy;       // d sigma_y / d alpha at alpha_{n+1}
-  float dgf;       // mixed form: dgamma and sqrt(2/3) sigma_y(alpha_{n+1}) rounded to FP32, for
-  float phyf;      //   the FP32 stress recovery and tangent that follow
   int iters;
   bool ok;
 };

@@ -202,9 +202,7 @@ __device__ __forceinline__ RM return_map_mixed(const float t[6], const Vec6d hv,
   }
   inc.eval(sq23 * dgf, incv, dsy);
   out.dgamma = dg64;
-  out.dgf = dgf;
-  out.phyf = sq23 * (inc.syn + incv);   // the FP32 stress recovery's phi_y
-  out.syn1 = 0.0;
+  out.syn1 = syn64 + (double)incv;
   out.dsy = dsy;
   out.iters = k + 1;
   out.ok = ok;
@@ -655,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGEN
     const R lam = m.lam, mu = m.mu;
     bool plastic = false;
     RM rm;
-    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0; rm.dgf = 0.0f; rm.phyf = 1.0f;
+    rm.dgamma = 0.0; rm.dsy = 0.0f; rm.iters = 0; rm.ok = true; rm.syn1 = 0.0;
     R Teig[6];
     R s_pl = R(0), phy = R(1);
     R TM[6];
@@ -759,10 +757,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGEN
     local_iters = rm.iters;
 
     // stress T and plastic update in the Hill eigenbasis, then back to Mandel components
-    // (the mixed path takes dgamma and phi_y rounded to FP32 from its return mapping)
-    const R dgR = sizeof(R) == 4 ? (R)rm.dgf : (R)rm.dgamma;
+    const R dgR = (R)rm.dgamma;
     if (plastic) {
-      phy = sizeof(R) == 4 ? (R)rm.phyf : (R)(kSq23 * rm.syn1);
+      phy = (R)(kSq23 * rm.syn1);
       s_pl = Num<R>::div(R(2) * mu * dgR, phy);
     }
     Teig[0] = t[0];
@@ -915,7 +912,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGEN
         // implicit function theorem on Eq. local_cpp (App. D) in the Hill eigenbasis:
         // Xi^-1 = E^-1 + dgamma (H - N (x) N) / phi, D = Xi - (Xi N)(Xi N)^T / (N Xi N + 2/3 H')
         const R iphy = Num<R>::div(R(1), phy);
-        const R cph = (sizeof(R) == 4 ? (R)rm.dgf : (R)rm.dgamma) * iphy;
+        const R cph = (R)rm.dgamma * iphy;
         R nv[6], iDd[6], pv[6];
         R npn = R(0);
 #pragma unroll
