@@ -14,10 +14,11 @@
 // A = dP/dF (rotated into the eigenbasis of C), the rotated shape-function gradients and the
 // rotated first Piola-Kirchhoff stress in shared memory.  Phase 2: one thread per
 // (element, node row a) contracts the eight Gauss points into the 3x24 row block of K^e
-// and the 3 entries of R^e, and scatters them through the element-to-block slot map.
-// Elements of one launch share no node (one colour of one slab of the launch order), so
-// the scatter needs no atomics; the first launch that touches a block stores, later
-// launches add (bit 31 of the slot).
+// and the 3 entries of R^e; the warp stages its element matrices in shared memory and
+// writes them through the element-to-block slot map with consecutive lanes on consecutive
+// entries.  Elements of one launch share no node (one colour of one slab of the launch
+// order), so every block has one writer per launch: the first launch that touches a block
+// stores, later launches add (bit 31 of the slot), in a fixed order.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
