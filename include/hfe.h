@@ -111,7 +111,8 @@ typedef struct {
   double newton_atol;
   int newton_maxit;
   double newton_stag_tol; /* mixed only: stagnation accepted below this relative norm */
-  double pcg_rtol;        /* ||r|| <= pcg_rtol * ||b|| */
+  double pcg_rtol;        /* ||r|| <= pcg_rtol * ||b||; default 1e-12 (FP64), 1e-6 (mixed); the
+                             adjoint's reverse solves on the mixed path go to 0.3 pcg_rtol */
   int pcg_maxit;
   int pcg_check_every;    /* iterations per convergence read-back (one CUDA graph) */
   int precond;            /* HFE_PRECOND_JACOBI or HFE_PRECOND_BLOCK3 */
@@ -307,7 +308,9 @@ hfe_status hfe_set_barrier_spin_limit(hfe_handle* h, int64_t limit);
  * gradient by the discrete adjoint (Eq. dR_u, Eq. main_grad) with the per-Gauss-point
  * implicit-function derivative of the return mapping (App. D).  u_target [n_steps*n_dof]
  * host or device; grad_out [n_mat*11] host or device (same layout as theta); J_out host.
- * The forward runs in the handle's precision; the adjoint in FP64. */
+ * The forward runs in the handle's precision; the adjoint in FP64 (on the mixed path each
+ * step's state is first refined in FP64, and the reverse solves K^T lambda = rhs run FP32 CG
+ * inside FP64 iterative refinement until the FP64 residual is 0.3 pcg_rtol ||rhs||). */
 hfe_status hfe_adjoint(hfe_handle* h, int n_steps, const double* t, const double* u_target,
                        double w, double* J_out, double* grad_out, hfe_stats* stats);
 
