@@ -405,11 +405,11 @@ __device__ __forceinline__ void phase2_staged(const SweepArgs& a, R* sGp, int le
 // MAT: 0 the Hill-48 update in the kernel; 1 the strain pass of an external material model
 // (the Mandel log strain of every Gauss point out, nothing assembled); 2 the external model's
 // stress, plastic flag and tangent dT/deps in (S4 and S5 replaced, S6-S8 as for Hill).
-// Occupancy: the mixed uniform-material Hill-48 tangent sweep runs five CTAs per SM (96 registers, a
-// few spilled values; measured 3.42 -> 3.33 ms at 100^3 against four CTAs at 128 registers),
-// the other mixed forms four, F-bar three.
+// Occupancy: the mixed uniform-material Hill-48 sweeps run five CTAs per SM (96 registers; the
+// tangent form spills a few values, measured 3.42 -> 3.33 ms at 100^3 against four CTAs at
+// 128 registers; the residual form spills none), the other mixed forms four, F-bar three.
 template <typename R, bool TANGENT, bool UNIF, bool FBAR, int MAT = 0>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (TANGENT && UNIF && MAT == 0 ? 5 : 4)) : 1)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? (FBAR ? 3 : (UNIF && MAT == 0 ? 5 : 4)) : 1)
     gp_sweep_kernel(SweepArgs a, const typename MatOf<R>::T mrec, int64_t cbeg, int64_t ccount) {
   constexpr int kGpStride = Lay<FBAR>::kGpStride;
   constexpr int kElStride = Lay<FBAR>::kElStride;
