@@ -3,7 +3,8 @@
 // block slot map that replaces the paper's triplet -> COO -> CSR assembly (App. E,
 // Algorithm gpu_chunked_assembly): slot[e][a][b] is the index of block (conn[e][a],
 // conn[e][b]); bit 31 marks the first launch (in launch order) that writes the block, which
-// stores instead of adding, so K needs no clearing pass.
+// stores instead of adding, so K needs no clearing pass.  Also here: the cut of the rows into
+// the chunks that the streamed CG copies into shared memory.
 #include "pattern.h"
 
 #include <algorithm>
@@ -200,6 +201,21 @@ bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, const Sla
     }
   }
   return true;
+}
+
+void stream_chunks(const int64_t* rowptr, int64_t n_nodes, int max_rows, int max_blocks, std::vector<int32_t>& out) {
+  out.clear();
+  out.push_back(0);
+  int64_t r = 0;
+  while (r < n_nodes) {
+    const int64_t r0 = r;
+    while (r < n_nodes && r - r0 < max_rows && rowptr[r + 1] - rowptr[r0] <= max_blocks) ++r;
+    if (r == r0) {   // a row longer than a chunk: no streamed SpMV for this pattern
+      out.clear();
+      return;
+    }
+    out.push_back((int32_t)r);
+  }
 }
 
 }  // namespace hfe

@@ -39,4 +39,10 @@ struct SlabPlan {
 bool build_pattern(int64_t n_nodes, int64_t n_el, const int32_t* conn, const SlabPlan& plan, Pattern& P,
                    std::string& err);
 
+// Row chunks of the streamed CG SpMV: greedy runs of consecutive rows, each of at most
+// max_rows rows and max_blocks blocks (rowptr[end] - rowptr[start] <= max_blocks); out =
+// [0, end_0, end_1, ..., n_nodes].  out is empty when a single row has more than max_blocks
+// blocks (the CG then loads K directly).
+void stream_chunks(const int64_t* rowptr, int64_t n_nodes, int max_rows, int max_blocks, std::vector<int32_t>& out);
+
 }  // namespace hfe

@@ -1290,21 +1290,6 @@ void precond_setup(const Csr& K, const R* vals, const int64_t* diag_slot, const 
   precond_kernel<R><<<nblk(K.n_nodes, 128), 128, 0, s>>>(vals, diag_slot, freem, minv, block3, K.n_nodes, bad);
 }
 
-void stream_chunks(const int64_t* rowptr, int64_t n_nodes, int max_rows, int max_blocks, std::vector<int32_t>& out) {
-  out.clear();
-  out.push_back(0);
-  int64_t r = 0;
-  while (r < n_nodes) {
-    const int64_t r0 = r;
-    while (r < n_nodes && r - r0 < max_rows && rowptr[r + 1] - rowptr[r0] <= max_blocks) ++r;
-    if (r == r0) {   // a row longer than a chunk: no streamed SpMV for this pattern
-      out.clear();
-      return;
-    }
-    out.push_back((int32_t)r);
-  }
-}
-
 void free_norm(const double* R_, const uint8_t* freem, int64_t n_dof, PcgScalars* sc, double* part,
                cudaStream_t s, double* out) {
   free_norm_kernel<<<rblk(n_dof, kBlock), kBlock, 0, s>>>(R_, freem, n_dof, sc, part, out);

@@ -54,9 +54,7 @@ static_assert(stream_val_bytes<double>() + stream_col_bytes<double>() <= kStream
 // Elements of padding past the end of every K value and column array: the bulk copies round
 // their end up to 16 bytes.
 constexpr int kKPad = 16;
-// Host: greedy row chunks (at most max_rows rows and max_blocks blocks each); empty when a
-// single row has more than max_blocks blocks.
-void stream_chunks(const int64_t* rowptr, int64_t n_nodes, int max_rows, int max_blocks, std::vector<int32_t>& out);
+// stream_chunks (the host-side cut of the rows into chunks) is declared in pattern.h.
 
 // Grid-barrier words of the persistent solver, each in its own 128-byte line so that the
 // CTAs polling the generation do not contend with the arrivals.

@@ -4,7 +4,8 @@ block per pair of nodes sharing an element, sorted columns, the diagonal slot), 
 colouring (no two elements of a colour share a node; 8 colours on a structured hex mesh),
 the launch order (one colour of one slab of K rows per launch, slabs in row order), the
 element-to-block slot map, and the first-writer flags (exactly one per block, on its first
-touch in launch order); malformed meshes are refused with a message."""
+touch in launch order); malformed meshes are refused with a message.  Also the cut of the
+rows into the chunks that the streamed CG copies into shared memory (stream_chunks)."""
 import os
 import shutil
 import subprocess
@@ -229,3 +230,77 @@ def test_malformed_meshes_refused(driver):
     assert P is None and "repeats a node" in err
     P, err = _run(driver, mesh.n_nodes + 1, mesh.conn)
     assert P is None and err == f"node {mesh.n_nodes} belongs to no element"
+
+
+CHUNK_DRIVER = r"""
+#include <cstdio>
+#include <string>
+#include <vector>
+#include "pattern.h"
+int main(int argc, char** argv) {
+  FILE* in = fopen(argv[1], "rb");
+  long long nn, par[2];
+  if (fread(&nn, 8, 1, in) != 1 || fread(par, 8, 2, in) != 2) return 3;
+  std::vector<int64_t> rowptr(nn + 1);
+  if (fread(rowptr.data(), 8, rowptr.size(), in) != rowptr.size()) return 3;
+  fclose(in);
+  std::vector<int32_t> out;
+  hfe::stream_chunks(rowptr.data(), nn, (int)par[0], (int)par[1], out);
+  FILE* o = fopen(argv[2], "wb");
+  long long n = (long long)out.size();
+  fwrite(&n, 8, 1, o);
+  fwrite(out.data(), 4, out.size(), o);
+  fclose(o);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def chunk_driver(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("chunks")
+    (d / "driver.cpp").write_text(CHUNK_DRIVER)
+    exe = d / "driver"
+    subprocess.run([cxx, "-std=c++17", "-O1", "-pthread", "-I", CSRC, str(d / "driver.cpp"),
+                    os.path.join(CSRC, "pattern.cpp"), "-o", str(exe)], check=True)
+    return exe, d
+
+
+def _chunks(chunk_driver, rowptr, max_rows, max_blocks):
+    exe, d = chunk_driver
+    inp, out = d / "rowptr.bin", d / "chunks.bin"
+    with open(inp, "wb") as f:
+        np.array([len(rowptr) - 1, max_rows, max_blocks], dtype=np.int64).tofile(f)
+        np.asarray(rowptr, dtype=np.int64).tofile(f)
+    subprocess.run([str(exe), str(inp), str(out)], check=True)
+    buf = open(out, "rb").read()
+    n = int(np.frombuffer(buf, np.int64, 1, 0)[0])
+    return np.frombuffer(buf, np.int32, n, 8).copy()
+
+
+@pytest.mark.parametrize("max_rows,max_blocks", [(32, 764), (32, 100), (7, 60), (1, 27)])
+def test_stream_chunks_cover_rows_within_limits(chunk_driver, max_rows, max_blocks):
+    """The rows of the streamed CG cut into chunks: consecutive, covering every row once, each
+    within max_rows rows and max_blocks blocks, and greedy (one more row would break a limit)."""
+    mesh, _, _, _ = inputs.config1_problem(nx=24, ny=12, nz=2, n_steps=2)
+    conn = np.asarray(mesh.conn, dtype=np.int64)
+    pairs = np.unique(np.stack([np.repeat(conn, 8, axis=1).ravel(), np.tile(conn, (1, 8)).ravel()], 1), axis=0)
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(pairs[:, 0], minlength=mesh.n_nodes))])
+    c = _chunks(chunk_driver, rowptr, max_rows, max_blocks)
+    assert c[0] == 0 and c[-1] == mesh.n_nodes and np.all(np.diff(c) > 0)
+    rows = np.diff(c)
+    blocks = rowptr[c[1:]] - rowptr[c[:-1]]
+    assert rows.max() <= max_rows and blocks.max() <= max_blocks
+    for k in range(len(c) - 2):   # every chunk but the last stops because the next row breaks a limit
+        nxt_rows, nxt_blocks = rows[k] + 1, rowptr[c[k + 1] + 1] - rowptr[c[k]]
+        assert nxt_rows > max_rows or nxt_blocks > max_blocks
+
+
+def test_stream_chunks_empty_when_a_row_is_too_long(chunk_driver):
+    rowptr = np.array([0, 5, 40, 45])
+    assert _chunks(chunk_driver, rowptr, 32, 30).size == 0
+    assert np.array_equal(_chunks(chunk_driver, rowptr, 32, 45), [0, 3])
+    assert np.array_equal(_chunks(chunk_driver, rowptr, 2, 45), [0, 2, 3])
